@@ -1,0 +1,155 @@
+/*
+ * ttn.h -- C ABI of the GB300 tree-tensor-network trajectory simulator for
+ * color-code syndrome-extraction circuits (arXiv 2511.05719).
+ *
+ * Everything is plain C: integers, doubles, host or device pointers, sizes.
+ * No function throws; every call returns a ttn_status and leaves a message for
+ * ttn_last_error() (thread-local) when it fails.
+ *
+ * Ownership: the caller owns every input and output buffer.  The library owns
+ * the circuit handle and the device memory it allocates for a run (released
+ * when the call returns, except the per-handle cache freed by
+ * ttn_free_circuit).
+ *
+ * Pointers: when `cuda_stream` is NULL all buffers are host pointers and the
+ * call is synchronous; otherwise they are device pointers and the work is
+ * ordered on that stream (the call still synchronises before returning the
+ * status, so the outputs are ready when it returns).
+ */
+#ifndef TTN_H
+#define TTN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  TTN_OK = 0,
+  TTN_EINVAL = 1,       /* bad argument (message says which)                 */
+  TTN_ENOMEM = 2,       /* device or host allocation failed                  */
+  TTN_ECUDA = 3,        /* a CUDA call failed                                */
+  TTN_ETIMEOUT = 4,     /* a device-side bounded wait expired                */
+  TTN_EUNSUPPORTED = 5, /* valid request this build does not implement       */
+  TTN_EOVERFLOW = 6     /* a per-shot bound was exceeded (message says which)*/
+} ttn_status;
+
+/* Error channel after every layer on every qubit the layer does not measure
+ * (Sec. III.A, Fig. 1b-d).  SRX: exp(-i theta X) (Eq. 1).  AD: Kraus operators
+ * of Eqs. 2-3, unravelled exactly.  *_PTA: Pauli-twirled channel (Sec. IV.C):
+ * SRX -> X with prob. sin^2 theta; AD -> (I,X,Y,Z) with probabilities
+ * ((1+sqrt(1-g))^2/4, g/4, g/4, (1-sqrt(1-g))^2/4).  SRX_AD: SRX then AD. */
+typedef enum {
+  TTN_NOISE_NONE = 0,
+  TTN_NOISE_SRX = 1,
+  TTN_NOISE_AD = 2,
+  TTN_NOISE_SRX_PTA = 3,
+  TTN_NOISE_AD_PTA = 4,
+  TTN_NOISE_SRX_AD = 5
+} ttn_noise;
+
+/* Arithmetic of the tree tensors.  FP64: complex128 throughout.  FP32:
+ * complex64 tensors and singular value decompositions, with probabilities,
+ * log-probabilities and discarded weights accumulated in double. */
+typedef enum { TTN_PREC_FP64 = 0, TTN_PREC_FP32 = 1 } ttn_precision;
+
+/* Qubit -> TTN leaf assignment (App. B).  DEFAULT: qubit i on leaf i.
+ * OPTIMIZED: recursive spectral bisection of the gate-similarity graph
+ * (Eq. 9).  EXPLICIT: the caller's leaf_of_qubit array. */
+typedef enum { TTN_LAYOUT_DEFAULT = 0, TTN_LAYOUT_OPTIMIZED = 1, TTN_LAYOUT_EXPLICIT = 2 } ttn_layout;
+
+typedef struct {
+  int32_t distance;              /* code distance d: odd, 3..11          */
+  int32_t rounds;                /* C >= 1 syndrome-extraction cycles    */
+  int32_t layout;                /* ttn_layout                           */
+  const int32_t* leaf_of_qubit;  /* [n_qubits] distinct leaves in [0, 2^D),
+                                    EXPLICIT only; copied by the call     */
+} ttn_circuit_params;
+
+typedef struct {
+  int32_t noise;                 /* ttn_noise                            */
+  double theta;                  /* SRX angle of Eq. 1 (rad)             */
+  double gamma;                  /* AD probability of Eq. 2              */
+  int32_t chi;                   /* bond-dimension cap, >= 1             */
+  int32_t precision;             /* ttn_precision                        */
+  uint64_t seed;                 /* Philox key                           */
+  uint64_t first_traj;           /* index of the first trajectory        */
+  double svd_eps;                /* singular values <= svd_eps * s_max are
+                                    dropped; <= 0 selects 1e-13 (FP64) or
+                                    3e-7 (FP32)                           */
+  const double* theta_per_traj;  /* optional [n_traj], overrides theta    */
+  const double* gamma_per_traj;  /* optional [n_traj], overrides gamma    */
+} ttn_run_params;
+
+typedef struct ttn_circuit ttn_circuit;  /* opaque, library-owned */
+
+/* Builds the color code [[ (3d^2+1)/4, 1, d ]] (Sec. II.A), its C-cycle
+ * syndrome-extraction circuit with noise locations (Sec. III, Fig. 1a), the
+ * qubit-to-leaf layout (App. B) and the decoder graphs (App. A.2).
+ * EINVAL on a bad distance, rounds, layout or explicit leaf map. */
+ttn_status ttn_build_circuit(const ttn_circuit_params* params, ttn_circuit** out);
+void ttn_free_circuit(ttn_circuit* circuit);
+
+/* Sizes: qubits N = n + 2 * #plaquettes, data n, layers, record bits per
+ * trajectory (rounds * 2 * #plaquettes syndrome bits -- round, plaquette,
+ * Z before X -- then the n final data bits), stochastic events, ops, leaves. */
+ttn_status ttn_circuit_info(const ttn_circuit* circuit, int32_t* n_qubits, int32_t* n_data,
+                            int32_t* n_layers, int32_t* n_record_bits, int32_t* n_events,
+                            int32_t* n_ops, int32_t* n_leaves);
+
+/* The op list, 6 int32 per op: kind (PREP_Z 0, PREP_X 1, CNOT 2, MEAS_Z 3,
+ * MEAS_X 4, NOISE 5), a (qubit / control), b (target / location id), event id
+ * (-1 if none), record bit (-1 if none), layer.  ops: host [n_ops][6]. */
+ttn_status ttn_circuit_ops(const ttn_circuit* circuit, int32_t* ops);
+
+/* The qubit -> leaf map in use.  leaf_of_qubit: host [n_qubits]. */
+ttn_status ttn_circuit_layout(const ttn_circuit* circuit, int32_t* leaf_of_qubit);
+
+/* Runs trajectories first_traj .. first_traj + n_traj - 1 (Sec. III.C): the
+ * whole circuit on the TTN, Born-sampled measurements, Kraus-branch or Pauli
+ * draws from Philox4x32-10 keyed by (seed, trajectory, event), then decodes
+ * (App. A.2).  Outputs (any may be NULL): records [n_traj][n_record_bits]
+ * (u8 0/1), logical_fail [n_traj] (u8), log_prob [n_traj] (log p of the
+ * sampled record and branches), discarded [n_traj] (sum of discarded
+ * squared singular values), near_ties [n_traj] (draws with |u - p| < 1e-9
+ * (FP64) or 1e-5 (FP32)).  Results depend only on (seed, trajectory index),
+ * not on batching.  EOVERFLOW if a decoding instance exceeds the decoder's
+ * bound; ENOMEM if one trajectory does not fit on the device. */
+ttn_status ttn_run_trajectories(const ttn_circuit* circuit, const ttn_run_params* params,
+                                uint64_t n_traj, uint8_t* records, uint8_t* logical_fail,
+                                double* log_prob, double* discarded, int32_t* near_ties,
+                                void* cuda_stream);
+
+/* Monte Carlo p_L = failures / shots (App. A.3, steps i-iii) with its
+ * binomial standard error sigma = sqrt(p (1-p) / shots).  Host outputs. */
+ttn_status ttn_logical_error_rate(const ttn_circuit* circuit, const ttn_run_params* params,
+                                  uint64_t shots, double* p_L, double* sigma, uint64_t* n_fail);
+
+/* Decodes n records ([n][n_record_bits] u8) with the concatenated MWPM
+ * decoder (App. A.2) on the device.  fail [n] u8, color [n] int32 (winning
+ * colour), score [n] int64 (total matching weight).  color/score may be NULL. */
+ttn_status ttn_decode(const ttn_circuit* circuit, uint64_t n, const uint8_t* records,
+                      uint8_t* fail, int32_t* color, int64_t* score, void* cuda_stream);
+
+/* Runs one trajectory through the end of `layer` (0-based; -1 = before the
+ * first op) and writes its 2^N amplitudes, little-endian in the qubit index
+ * (qubit q = bit q), as interleaved (re, im) doubles.  N <= 24, at most 16
+ * leaves and chi <= 64.  Host buffer amps [2^N * 2]. */
+ttn_status ttn_debug_state(const ttn_circuit* circuit, const ttn_run_params* params,
+                           uint64_t traj, int32_t layer, double* amps);
+
+/* Philox4x32-10 uniform draws u(seed, traj_i, event_j) of the simulator, for
+ * n_traj x n_events pairs, computed on the device.  out: host [n_traj][n_events]. */
+ttn_status ttn_philox_uniforms(uint64_t seed, const uint64_t* trajs, uint64_t n_traj,
+                               const int32_t* events, int32_t n_events, double* out);
+
+const char* ttn_status_string(ttn_status status);
+const char* ttn_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TTN_H */

@@ -1,0 +1,232 @@
+"""ctypes marshalling for libttn.so (see include/ttn.h for the contract)."""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB = None
+
+NOISE = {"none": 0, "srx": 1, "ad": 2, "srx_pta": 3, "ad_pta": 4, "srx_ad": 5}
+PRECISION = {"fp64": 0, "fp32": 1}
+LAYOUT = {"default": 0, "optimized": 1, "explicit": 2}
+
+c_i32p = ctypes.POINTER(ctypes.c_int32)
+c_dblp = ctypes.POINTER(ctypes.c_double)
+c_u8p = ctypes.POINTER(ctypes.c_uint8)
+c_u64p = ctypes.POINTER(ctypes.c_uint64)
+c_i64p = ctypes.POINTER(ctypes.c_int64)
+
+
+class CircuitParams(ctypes.Structure):
+    _fields_ = [("distance", ctypes.c_int32), ("rounds", ctypes.c_int32),
+                ("layout", ctypes.c_int32), ("leaf_of_qubit", c_i32p)]
+
+
+class RunParams(ctypes.Structure):
+    _fields_ = [("noise", ctypes.c_int32), ("theta", ctypes.c_double), ("gamma", ctypes.c_double),
+                ("chi", ctypes.c_int32), ("precision", ctypes.c_int32), ("seed", ctypes.c_uint64),
+                ("first_traj", ctypes.c_uint64), ("svd_eps", ctypes.c_double),
+                ("theta_per_traj", c_dblp), ("gamma_per_traj", c_dblp)]
+
+
+class TTNError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__("ttn status %d: %s" % (status, message))
+        self.status = status
+
+
+EXPORTS = ["ttn_build_circuit", "ttn_free_circuit", "ttn_circuit_info", "ttn_circuit_ops",
+           "ttn_circuit_layout", "ttn_run_trajectories", "ttn_logical_error_rate", "ttn_decode",
+           "ttn_debug_state", "ttn_philox_uniforms", "ttn_status_string", "ttn_last_error"]
+
+
+def library_path():
+    return os.path.join(_HERE, "libttn.so")
+
+
+def load_library():
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = library_path()
+    if not os.path.exists(path):
+        raise TTNError(-1, "libttn.so is not built (run paper_2511_05719_gb300.build.build())")
+    lib = ctypes.CDLL(path)
+    vp = ctypes.c_void_p
+    lib.ttn_build_circuit.argtypes = [ctypes.POINTER(CircuitParams), ctypes.POINTER(vp)]
+    lib.ttn_free_circuit.argtypes = [vp]
+    lib.ttn_free_circuit.restype = None
+    lib.ttn_circuit_info.argtypes = [vp] + [c_i32p] * 7
+    lib.ttn_circuit_ops.argtypes = [vp, c_i32p]
+    lib.ttn_circuit_layout.argtypes = [vp, c_i32p]
+    lib.ttn_run_trajectories.argtypes = [vp, ctypes.POINTER(RunParams), ctypes.c_uint64, vp, vp, vp,
+                                         vp, vp, vp]
+    lib.ttn_logical_error_rate.argtypes = [vp, ctypes.POINTER(RunParams), ctypes.c_uint64, c_dblp,
+                                           c_dblp, c_u64p]
+    lib.ttn_decode.argtypes = [vp, ctypes.c_uint64, vp, vp, vp, vp, vp]
+    lib.ttn_debug_state.argtypes = [vp, ctypes.POINTER(RunParams), ctypes.c_uint64, ctypes.c_int32,
+                                    c_dblp]
+    lib.ttn_philox_uniforms.argtypes = [ctypes.c_uint64, c_u64p, ctypes.c_uint64, c_i32p,
+                                        ctypes.c_int32, c_dblp]
+    lib.ttn_status_string.restype = ctypes.c_char_p
+    lib.ttn_status_string.argtypes = [ctypes.c_int]
+    lib.ttn_last_error.restype = ctypes.c_char_p
+    for name in EXPORTS:
+        f = getattr(lib, name)
+        if name not in ("ttn_free_circuit", "ttn_status_string", "ttn_last_error"):
+            f.restype = ctypes.c_int
+    _LIB = lib
+    return lib
+
+
+def _check(status):
+    if status != 0:
+        lib = load_library()
+        raise TTNError(status, lib.ttn_last_error().decode())
+
+
+def _ptr(a, ctype=None):
+    """Data pointer of a numpy array or a torch tensor (None -> NULL)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return ctypes.c_void_p(a.data_ptr())
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+class Circuit:
+    """Color-code syndrome-extraction circuit (d, C) with its TTN layout."""
+
+    def __init__(self, distance, rounds, layout="optimized", leaf_of_qubit=None):
+        lib = load_library()
+        p = CircuitParams()
+        p.distance = distance
+        p.rounds = rounds
+        self._leaves = None
+        if leaf_of_qubit is not None:
+            layout = "explicit"
+            self._leaves = np.ascontiguousarray(leaf_of_qubit, dtype=np.int32)
+            p.leaf_of_qubit = self._leaves.ctypes.data_as(c_i32p)
+        p.layout = LAYOUT[layout]
+        h = ctypes.c_void_p()
+        _check(lib.ttn_build_circuit(ctypes.byref(p), ctypes.byref(h)))
+        self._h = h
+        vals = [ctypes.c_int32() for _ in range(7)]
+        _check(lib.ttn_circuit_info(h, *[ctypes.byref(v) for v in vals]))
+        (self.n_qubits, self.n_data, self.n_layers, self.n_record_bits, self.n_events,
+         self.n_ops, self.n_leaves) = [v.value for v in vals]
+        self.distance, self.rounds = distance, rounds
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and _LIB is not None:
+            _LIB.ttn_free_circuit(h)
+            self._h = None
+
+    @property
+    def handle(self):
+        return self._h
+
+    def ops(self):
+        out = np.zeros((self.n_ops, 6), dtype=np.int32)
+        _check(load_library().ttn_circuit_ops(self._h, out.ctypes.data_as(c_i32p)))
+        return out
+
+    def layout(self):
+        out = np.zeros(self.n_qubits, dtype=np.int32)
+        _check(load_library().ttn_circuit_layout(self._h, out.ctypes.data_as(c_i32p)))
+        return out
+
+
+def _run_params(noise, theta, gamma, chi, precision, seed, first_traj, svd_eps,
+                theta_per_traj=None, gamma_per_traj=None):
+    p = RunParams()
+    p.noise = NOISE[noise] if isinstance(noise, str) else int(noise)
+    p.theta = float(theta)
+    p.gamma = float(gamma)
+    p.chi = int(chi)
+    p.precision = PRECISION[precision] if isinstance(precision, str) else int(precision)
+    p.seed = int(seed)
+    p.first_traj = int(first_traj)
+    p.svd_eps = float(svd_eps)
+    keep = []
+    if theta_per_traj is not None:
+        a = np.ascontiguousarray(theta_per_traj, dtype=np.float64)
+        keep.append(a)
+        p.theta_per_traj = a.ctypes.data_as(c_dblp)
+    if gamma_per_traj is not None:
+        a = np.ascontiguousarray(gamma_per_traj, dtype=np.float64)
+        keep.append(a)
+        p.gamma_per_traj = a.ctypes.data_as(c_dblp)
+    return p, keep
+
+
+def run_trajectories(circuit, n_traj, noise="srx", theta=0.0, gamma=0.0, chi=16,
+                     precision="fp64", seed=0, first_traj=0, svd_eps=0.0,
+                     theta_per_traj=None, gamma_per_traj=None, out=None, stream=None):
+    """Runs n_traj trajectories.  With `out=None` returns host numpy arrays
+    {records, fail, log_prob, discarded, near_ties}.  With `out` a dict of
+    torch CUDA tensors (any subset of those keys) and `stream` a CUDA stream
+    handle (int), writes them on the device."""
+    lib = load_library()
+    p, keep = _run_params(noise, theta, gamma, chi, precision, seed, first_traj, svd_eps,
+                          theta_per_traj, gamma_per_traj)
+    if out is None:
+        out = dict(records=np.zeros((n_traj, circuit.n_record_bits), dtype=np.uint8),
+                   fail=np.zeros(n_traj, dtype=np.uint8),
+                   log_prob=np.zeros(n_traj), discarded=np.zeros(n_traj),
+                   near_ties=np.zeros(n_traj, dtype=np.int32))
+        st = None
+    else:
+        st = ctypes.c_void_p(int(stream)) if stream is not None else None
+        if st is None:
+            raise ValueError("device outputs need a CUDA stream handle")
+    _check(lib.ttn_run_trajectories(circuit.handle, ctypes.byref(p), n_traj,
+                                    _ptr(out.get("records")), _ptr(out.get("fail")),
+                                    _ptr(out.get("log_prob")), _ptr(out.get("discarded")),
+                                    _ptr(out.get("near_ties")), st))
+    del keep
+    return out
+
+
+def logical_error_rate(circuit, shots, noise="srx", theta=0.0, gamma=0.0, chi=16,
+                       precision="fp64", seed=0, first_traj=0, svd_eps=0.0):
+    lib = load_library()
+    p, keep = _run_params(noise, theta, gamma, chi, precision, seed, first_traj, svd_eps)
+    pl, sg, nf = ctypes.c_double(), ctypes.c_double(), ctypes.c_uint64()
+    _check(lib.ttn_logical_error_rate(circuit.handle, ctypes.byref(p), shots, ctypes.byref(pl),
+                                      ctypes.byref(sg), ctypes.byref(nf)))
+    return pl.value, sg.value, nf.value
+
+
+def decode(circuit, records):
+    """Decodes host records [n][n_record_bits] -> (fail u8, colour i32, score i64)."""
+    lib = load_library()
+    rec = np.ascontiguousarray(records, dtype=np.uint8)
+    n = rec.shape[0]
+    fail = np.zeros(n, dtype=np.uint8)
+    color = np.zeros(n, dtype=np.int32)
+    score = np.zeros(n, dtype=np.int64)
+    _check(lib.ttn_decode(circuit.handle, n, _ptr(rec), _ptr(fail), _ptr(color), _ptr(score), None))
+    return fail, color, score
+
+
+def debug_state(circuit, traj, layer, noise="srx", theta=0.0, gamma=0.0, chi=16,
+                precision="fp64", seed=0, svd_eps=0.0):
+    lib = load_library()
+    p, keep = _run_params(noise, theta, gamma, chi, precision, seed, 0, svd_eps)
+    amps = np.zeros(2 * (1 << circuit.n_qubits))
+    _check(lib.ttn_debug_state(circuit.handle, ctypes.byref(p), traj, layer,
+                               amps.ctypes.data_as(c_dblp)))
+    return amps[0::2] + 1j * amps[1::2]
+
+
+def philox_uniforms(seed, trajs, events):
+    lib = load_library()
+    t = np.ascontiguousarray(trajs, dtype=np.uint64)
+    e = np.ascontiguousarray(events, dtype=np.int32)
+    out = np.zeros((t.size, e.size))
+    _check(lib.ttn_philox_uniforms(seed, t.ctypes.data_as(c_u64p), t.size,
+                                   e.ctypes.data_as(c_i32p), e.size, out.ctypes.data_as(c_dblp)))
+    return out

@@ -1,0 +1,249 @@
+// extern "C" boundary of the library (declared in include/ttn.h).  Argument
+// checking, circuit handles and marshalling; all simulation work runs in the
+// CUDA engine and decoder.
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "engine.h"
+#include "internal.h"
+
+namespace ttn {
+static thread_local std::string g_last_error;
+void set_error(const std::string& msg) { g_last_error = msg; }
+}  // namespace ttn
+
+using namespace ttn;
+
+static ttn_status fail_with(ttn_status s, const std::string& msg) {
+  set_error(msg);
+  return s;
+}
+
+extern "C" {
+
+const char* ttn_status_string(ttn_status s) {
+  switch (s) {
+    case TTN_OK: return "ok";
+    case TTN_EINVAL: return "invalid argument";
+    case TTN_ENOMEM: return "out of memory";
+    case TTN_ECUDA: return "CUDA error";
+    case TTN_ETIMEOUT: return "device wait timed out";
+    case TTN_EUNSUPPORTED: return "unsupported";
+    case TTN_EOVERFLOW: return "per-shot bound exceeded";
+  }
+  return "unknown status";
+}
+
+const char* ttn_last_error(void) { return g_last_error.c_str(); }
+
+ttn_status ttn_build_circuit(const ttn_circuit_params* p, ttn_circuit** out) {
+  if (!p || !out) return fail_with(TTN_EINVAL, "null argument");
+  *out = nullptr;
+  if (p->distance < 3 || p->distance > 11 || p->distance % 2 == 0)
+    return fail_with(TTN_EINVAL, "distance must be odd and in [3, 11]");
+  if (p->rounds < 1 || p->rounds > 64) return fail_with(TTN_EINVAL, "rounds must be in [1, 64]");
+  if (p->layout < TTN_LAYOUT_DEFAULT || p->layout > TTN_LAYOUT_EXPLICIT)
+    return fail_with(TTN_EINVAL, "unknown layout");
+  ttn_circuit* c = new (std::nothrow) ttn_circuit();
+  if (!c) return fail_with(TTN_ENOMEM, "host allocation failed");
+  c->d = p->distance;
+  c->C = p->rounds;
+  c->code = build_code(c->d);
+  c->n = c->code.n;
+  c->P = c->code.P;
+  c->N = c->n + 2 * c->P;
+  c->ops = build_ops(c->code, c->C, &c->n_layers, &c->n_events, &c->n_locations);
+  c->n_rec = c->C * 2 * c->P + c->n;
+  c->D = 1;
+  while ((1 << c->D) < c->N) ++c->D;
+  c->L = 1 << c->D;
+  if (p->layout == TTN_LAYOUT_DEFAULT) {
+    c->leaf_of_qubit.resize(c->N);
+    for (int q = 0; q < c->N; ++q) c->leaf_of_qubit[q] = q;
+  } else if (p->layout == TTN_LAYOUT_OPTIMIZED) {
+    c->leaf_of_qubit = optimized_layout(c->code, c->ops, c->N, c->L);
+  } else {
+    if (!p->leaf_of_qubit) {
+      delete c;
+      return fail_with(TTN_EINVAL, "explicit layout needs leaf_of_qubit");
+    }
+    std::vector<int> seen(c->L, 0);
+    c->leaf_of_qubit.assign(p->leaf_of_qubit, p->leaf_of_qubit + c->N);
+    for (int q = 0; q < c->N; ++q) {
+      int l = c->leaf_of_qubit[q];
+      if (l < 0 || l >= c->L || seen[l]) {
+        delete c;
+        return fail_with(TTN_EINVAL, "leaf_of_qubit must hold distinct leaves in [0, 2^D)");
+      }
+      seen[l] = 1;
+    }
+  }
+  c->dec = build_decoder_tables(c->code, c->C);
+  *out = c;
+  return TTN_OK;
+}
+
+void ttn_free_circuit(ttn_circuit* c) { delete c; }
+
+ttn_status ttn_circuit_info(const ttn_circuit* c, int32_t* n_qubits, int32_t* n_data,
+                            int32_t* n_layers, int32_t* n_record_bits, int32_t* n_events,
+                            int32_t* n_ops, int32_t* n_leaves) {
+  if (!c) return fail_with(TTN_EINVAL, "null circuit");
+  if (n_qubits) *n_qubits = c->N;
+  if (n_data) *n_data = c->n;
+  if (n_layers) *n_layers = c->n_layers;
+  if (n_record_bits) *n_record_bits = c->n_rec;
+  if (n_events) *n_events = c->n_events;
+  if (n_ops) *n_ops = (int32_t)c->ops.size();
+  if (n_leaves) *n_leaves = c->L;
+  return TTN_OK;
+}
+
+ttn_status ttn_circuit_ops(const ttn_circuit* c, int32_t* ops) {
+  if (!c || !ops) return fail_with(TTN_EINVAL, "null argument");
+  for (size_t i = 0; i < c->ops.size(); ++i) {
+    const Op& o = c->ops[i];
+    int32_t* r = ops + 6 * i;
+    r[0] = o.kind;
+    r[1] = o.a;
+    r[2] = o.b;
+    r[3] = o.event;
+    r[4] = o.rec;
+    r[5] = o.layer;
+  }
+  return TTN_OK;
+}
+
+ttn_status ttn_circuit_layout(const ttn_circuit* c, int32_t* leaf_of_qubit) {
+  if (!c || !leaf_of_qubit) return fail_with(TTN_EINVAL, "null argument");
+  for (int q = 0; q < c->N; ++q) leaf_of_qubit[q] = c->leaf_of_qubit[q];
+  return TTN_OK;
+}
+
+static ttn_status check_params(const ttn_circuit* c, const ttn_run_params* p) {
+  if (!c || !p) return fail_with(TTN_EINVAL, "null argument");
+  if (p->noise < TTN_NOISE_NONE || p->noise > TTN_NOISE_SRX_AD) return fail_with(TTN_EINVAL, "unknown noise model");
+  if (p->precision != TTN_PREC_FP64 && p->precision != TTN_PREC_FP32)
+    return fail_with(TTN_EINVAL, "unknown precision");
+  if (p->chi < 1 || p->chi > 4096) return fail_with(TTN_EINVAL, "chi must be in [1, 4096]");
+  if (!std::isfinite(p->theta)) return fail_with(TTN_EINVAL, "theta must be finite");
+  if (!(p->gamma >= 0.0 && p->gamma <= 1.0)) return fail_with(TTN_EINVAL, "gamma must be in [0, 1]");
+  return TTN_OK;
+}
+
+static RunRequest make_request(const ttn_run_params* p, uint64_t n_traj, void* stream) {
+  RunRequest rq;
+  rq.noise = p->noise;
+  rq.chi = p->chi;
+  rq.precision = p->precision;
+  rq.theta = p->theta;
+  rq.gamma = p->gamma;
+  rq.svd_eps = p->svd_eps > 0 ? p->svd_eps : (p->precision == TTN_PREC_FP64 ? 1e-13 : 3e-7);
+  rq.seed = p->seed;
+  rq.first_traj = p->first_traj;
+  rq.n_traj = n_traj;
+  rq.theta_per_traj = p->theta_per_traj;
+  rq.gamma_per_traj = p->gamma_per_traj;
+  rq.stream = stream;
+  return rq;
+}
+
+ttn_status ttn_run_trajectories(const ttn_circuit* c, const ttn_run_params* p, uint64_t n_traj,
+                                uint8_t* records, uint8_t* logical_fail, double* log_prob,
+                                double* discarded, int32_t* near_ties, void* cuda_stream) {
+  ttn_status s = check_params(c, p);
+  if (s != TTN_OK) return s;
+  if (n_traj == 0) return TTN_OK;
+  RunRequest rq = make_request(p, n_traj, cuda_stream);
+  if (cuda_stream && (p->theta_per_traj || p->gamma_per_traj)) {
+    // per-trajectory strengths are read on the host
+    cudaPointerAttributes at{};
+    const double* probe = p->theta_per_traj ? p->theta_per_traj : p->gamma_per_traj;
+    if (cudaPointerGetAttributes(&at, probe) == cudaSuccess && at.type == cudaMemoryTypeDevice)
+      return fail_with(TTN_EINVAL, "theta_per_traj / gamma_per_traj must be host arrays");
+  }
+  RunOutputs out;
+  out.on_device = cuda_stream != nullptr;
+  out.fail_on_device = out.on_device;
+  out.records = records;
+  out.fail = logical_fail;
+  out.log_prob = log_prob;
+  out.discarded = discarded;
+  out.near_ties = near_ties;
+  s = run_trajectories_device(*c, rq, out);
+  if (s != TTN_OK) return s;
+  if (out.decode_overflow > 0) {
+    set_error("decoder: " + std::to_string(out.decode_overflow) +
+              " shot(s) exceeded the matching bound (fail byte 2)");
+    return TTN_EOVERFLOW;
+  }
+  return TTN_OK;
+}
+
+ttn_status ttn_logical_error_rate(const ttn_circuit* c, const ttn_run_params* p, uint64_t shots,
+                                  double* p_L, double* sigma, uint64_t* n_fail) {
+  ttn_status s = check_params(c, p);
+  if (s != TTN_OK) return s;
+  if (shots == 0) return fail_with(TTN_EINVAL, "shots must be > 0");
+  std::vector<uint8_t> fail(shots);
+  s = ttn_run_trajectories(c, p, shots, nullptr, fail.data(), nullptr, nullptr, nullptr, nullptr);
+  if (s != TTN_OK) return s;
+  uint64_t nf = 0;
+  for (uint8_t f : fail) nf += f == 1;
+  double pl = (double)nf / (double)shots;
+  if (p_L) *p_L = pl;
+  if (sigma) *sigma = std::sqrt(pl * (1.0 - pl) / (double)shots);
+  if (n_fail) *n_fail = nf;
+  return TTN_OK;
+}
+
+ttn_status ttn_decode(const ttn_circuit* c, uint64_t n, const uint8_t* records, uint8_t* fail,
+                      int32_t* color, int64_t* score, void* cuda_stream) {
+  if (!c || !records || !fail) return fail_with(TTN_EINVAL, "null argument");
+  if (n == 0) return TTN_OK;
+  if (cuda_stream) return decode_device(*c, (int)n, records, fail, color, score, cuda_stream, true);
+  uint8_t* d = nullptr;
+  if (cudaMalloc(&d, n * c->n_rec) != cudaSuccess) return fail_with(TTN_ENOMEM, "device allocation failed");
+  if (cudaMemcpy(d, records, n * c->n_rec, cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaFree(d);
+    return fail_with(TTN_ECUDA, "copy of records failed");
+  }
+  ttn_status s = decode_device(*c, (int)n, d, fail, color, score, nullptr, false);
+  cudaFree(d);
+  return s;
+}
+
+ttn_status ttn_debug_state(const ttn_circuit* c, const ttn_run_params* p, uint64_t traj,
+                           int32_t layer, double* amps) {
+  ttn_status s = check_params(c, p);
+  if (s != TTN_OK) return s;
+  if (!amps) return fail_with(TTN_EINVAL, "null amps");
+  if (c->N > 24 || c->L > 16) return fail_with(TTN_EUNSUPPORTED, "debug state needs N <= 24 and <= 16 leaves");
+  if (p->chi > 64) return fail_with(TTN_EUNSUPPORTED, "debug state needs chi <= 64");
+  if (layer < -1 || layer >= c->n_layers) return fail_with(TTN_EINVAL, "layer out of range");
+  ttn_run_params q = *p;
+  q.first_traj = traj;
+  q.theta_per_traj = nullptr;
+  q.gamma_per_traj = nullptr;
+  RunRequest rq = make_request(&q, 1, nullptr);
+  rq.last_layer = layer;
+  rq.debug_amps = amps;
+  if (p->theta_per_traj) rq.theta = p->theta_per_traj[0];
+  if (p->gamma_per_traj) rq.gamma = p->gamma_per_traj[0];
+  RunOutputs out;
+  return run_trajectories_device(*c, rq, out);
+}
+
+ttn_status ttn_philox_uniforms(uint64_t seed, const uint64_t* trajs, uint64_t n_traj,
+                               const int32_t* events, int32_t n_events, double* out) {
+  if (!trajs || !events || !out || n_events < 0) return fail_with(TTN_EINVAL, "bad argument");
+  if (n_traj == 0 || n_events == 0) return TTN_OK;
+  return philox_uniforms_device(seed, trajs, n_traj, events, n_events, out);
+}
+
+}  // extern "C"

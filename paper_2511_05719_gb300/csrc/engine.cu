@@ -1,0 +1,1180 @@
+// Batched tree-tensor-network trajectory engine (sm_103a).
+//
+// Every trajectory of a batch runs the same step program (compiled on the
+// host from the circuit and the tree layout); only bond dimensions, tensor
+// values and random draws differ.  Kernels take the whole batch (grid.z or
+// grid.x = trajectory), read each trajectory's bond dimensions from device
+// memory and skip the tiles outside them, so no host synchronisation is
+// needed between steps.
+//
+// Method (Sec. III.B-C): a binary TTN with the isometry centre moved by
+// singular value decompositions; a two-qubit gate is applied in
+// operator-Schmidt form along the tree path between its leaves and the path
+// bonds are re-truncated to chi; measurements and amplitude-damping branches
+// are sampled at the centre (Born rule / exact Kraus unravelling) with
+// Philox4x32-10 draws keyed by (seed, trajectory, event).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "engine.h"
+
+namespace ttn {
+
+// ------------------------------------------------------------------ complex
+template <typename R>
+struct alignas(2 * sizeof(R)) cx {
+  R x, y;
+};
+
+template <typename R>
+__device__ __forceinline__ cx<R> cmul(cx<R> a, cx<R> b) {
+  return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+template <typename R>
+__device__ __forceinline__ cx<R> cmulc(cx<R> a, cx<R> b) {  // conj(a) * b
+  return {a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x};
+}
+template <typename R>
+__device__ __forceinline__ cx<R> cadd(cx<R> a, cx<R> b) {
+  return {a.x + b.x, a.y + b.y};
+}
+template <typename R>
+__device__ __forceinline__ cx<R> cscale(cx<R> a, R s) {
+  return {a.x * s, a.y * s};
+}
+template <typename R>
+__device__ __forceinline__ R cabs2(cx<R> a) {
+  return a.x * a.x + a.y * a.y;
+}
+
+// ------------------------------------------------------------------ Philox
+// Philox4x32-10 (Salmon et al., SC'11): ten rounds of two 32x32->64 bit
+// products, key bumped by the Weyl constants between rounds.
+__device__ __forceinline__ uint4 philox10(uint4 c, uint2 k) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r) {
+      k.x += 0x9E3779B9u;
+      k.y += 0xBB67AE85u;
+    }
+    const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+  }
+  return c;
+}
+
+// Uniform in [0, 1) with 53 random bits: counter (traj_lo, traj_hi, event, 0).
+__device__ __forceinline__ double draw_uniform(uint64_t seed, uint64_t traj, uint32_t event) {
+  uint4 w = philox10(make_uint4((uint32_t)traj, (uint32_t)(traj >> 32), event, 0u),
+                     make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+  return ((double)(w.x >> 5) * 67108864.0 + (double)(w.y >> 6)) * (1.0 / 9007199254740992.0);
+}
+
+__global__ void k_philox_uniforms(uint64_t seed, const uint64_t* trajs, int n_traj,
+                                  const int32_t* events, int n_events, double* out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_traj * n_events) return;
+  int t = i / n_events, e = i % n_events;
+  out[i] = draw_uniform(seed, trajs[t], (uint32_t)events[e]);
+}
+
+// ------------------------------------------------------------------ batch state
+template <typename R>
+struct Dev {
+  cx<R>* T;              // node tensors, trajectory b at T + b * tstride + off[v]
+  const int64_t* off;    // [L]
+  int64_t tstride;
+  int32_t* dims;         // [B][2L] bond (x, parent(x)) dimension
+  int ds;                // 2L
+  cx<R>* W;              // [B][wstride] SVD / contraction workspace
+  int64_t wstride;
+  cx<R>* V;              // [B][vstride] right singular vectors (column-major n x n)
+  cx<R>* Rm;             // [B][vstride] factor absorbed by the neighbour (k x n)
+  int64_t vstride;
+  double* sv;            // [B][nmax]
+  int32_t* perm;         // [B][nmax]
+  int nmax;
+  int32_t* knew;         // [B] kept rank of the last move
+  int32_t* nold;         // [B] previous dimension of that bond
+  double* logp;          // [B]
+  double* disc;          // [B]
+  int32_t* ties;         // [B]
+  uint8_t* rec;          // [B][n_rec]
+  int n_rec;
+  uint8_t* last;         // [B][N] last measured value per qubit
+  int N;
+  const double* theta;   // [B]
+  const double* gamma;   // [B]
+  const uint64_t* traj;  // [B] trajectory index
+  uint64_t seed;
+  int L, chi, noise;
+  double eps, tie_eps, tol;
+  int max_sweeps;
+  int32_t* err;          // [B] error flags
+};
+
+enum : int32_t { ERR_ZERO_NORM = 1, ERR_NO_CONVERGE = 2, ERR_CAPACITY = 4, ERR_NAN = 8 };
+
+template <typename R>
+__device__ __forceinline__ cx<R>* node_ptr(const Dev<R>& d, int b, int v) {
+  return d.T + (int64_t)b * d.tstride + d.off[v];
+}
+
+// ------------------------------------------------------------------ init
+template <typename R>
+__global__ void k_init(Dev<R> d, const int32_t* leafdim, int B) {
+  int b = blockIdx.y;
+  if (b >= B) return;
+  for (int x = threadIdx.x + blockIdx.x * blockDim.x; x < d.ds; x += blockDim.x * gridDim.x) {
+    int val = 1;
+    if (x >= d.L) val = leafdim[x - d.L];
+    d.dims[b * d.ds + x] = val;
+  }
+  for (int v = 1 + threadIdx.x + blockIdx.x * blockDim.x; v < d.L; v += blockDim.x * gridDim.x) {
+    cx<R>* t = node_ptr(d, b, v);
+    int dl = (2 * v >= d.L) ? leafdim[2 * v - d.L] : 1;
+    int dr = (2 * v + 1 >= d.L) ? leafdim[2 * v + 1 - d.L] : 1;
+    for (int i = 0; i < dl * dr; ++i) t[i] = {R(i == 0), R(0)};
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    d.logp[b] = 0.0;
+    d.disc[b] = 0.0;
+    d.ties[b] = 0;
+    d.err[b] = 0;
+  }
+  for (int i = threadIdx.x + blockIdx.x * blockDim.x; i < d.N; i += blockDim.x * gridDim.x)
+    d.last[(int64_t)b * d.N + i] = 0;
+}
+
+// ------------------------------------------------------------------ SVD move
+// Centre move v -> w (neighbour) across their bond.  M = T_v with the bond as
+// column index (m x n).  One-sided Jacobi (Hestenes) orthogonalises the
+// columns of M V; s_j = |(M V)_j|; keep k singular triplets (s > eps s_max,
+// at most chi when capped); T_v <- U_k, R = S_k V_k^dag (renormalised after a
+// truncation) is left in d.Rm for the neighbour.
+template <typename R>
+__device__ __forceinline__ R warp_sum(R v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_svd_move(Dev<R> d, int v, int w, int capped) {
+  const int b = blockIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+  int* D = d.dims + b * d.ds;
+  const int dl = D[2 * v], dr = D[2 * v + 1], du = D[v];
+  const int leg = (w == 2 * v) ? 0 : ((w == 2 * v + 1) ? 1 : 2);
+  const int n = leg == 0 ? dl : (leg == 1 ? dr : du);
+  const int m = dl * dr * du / n;
+  cx<R>* T = node_ptr(d, b, v);
+  cx<R>* W = d.W + (int64_t)b * d.wstride;
+  cx<R>* V = d.V + (int64_t)b * d.vstride;
+  double* sv = d.sv + (int64_t)b * d.nmax;
+  int32_t* perm = d.perm + (int64_t)b * d.nmax;
+  __shared__ int s_k;
+  __shared__ double s_scale;
+  if ((int64_t)m * n > d.wstride || n > d.nmax || (int64_t)n * n > d.vstride) {
+    if (tid == 0) {
+      atomicOr(&d.err[b], ERR_CAPACITY);
+      d.knew[b] = 0;
+    }
+    return;
+  }
+
+  // gather M (column-major, m x n) and its squared Frobenius norm
+  __shared__ double s_part[32];
+  double fro_part = 0.0;
+  for (int idx = tid; idx < m * n; idx += blockDim.x) {
+    int j = idx / m, i = idx - j * m;
+    int src;
+    if (leg == 2) src = i * du + j;
+    else if (leg == 0) src = j * m + i;
+    else {
+      int l = i / du, u = i - l * du;
+      src = (l * dr + j) * du + u;
+    }
+    cx<R> val = T[src];
+    W[idx] = val;
+    fro_part += (double)cabs2(val);
+  }
+  fro_part = warp_sum(fro_part);
+  if (lane == 0) s_part[warp] = fro_part;
+  for (int idx = tid; idx < n * n; idx += blockDim.x) {
+    int j = idx / n, x = idx - j * n;
+    V[idx] = {R(j == x), R(0)};
+  }
+  __syncthreads();
+
+  double fro2 = 0.0;
+  for (int i = 0; i < nwarps; ++i) fro2 += s_part[i];
+  if (n > 1) {
+    const int ne = n + (n & 1);
+    const int M1 = ne - 1;
+    const R tolm = (R)d.tol * sqrt((R)(m > 1 ? m : 1));
+    // a column below eps |M|_F / sqrt(n) is always dropped (s_max^2 >=
+    // |M|_F^2 / n): it takes no part in rotations
+    const R skip2 = (R)(d.eps * d.eps * fro2 / (double)n);
+    int sweep = 0;
+    for (; sweep < d.max_sweeps; ++sweep) {
+      int rotated = 0;
+      for (int s = 0; s < M1; ++s) {
+        for (int pr = warp; pr < ne / 2; pr += nwarps) {
+          int p, q;
+          if (pr == 0) {
+            p = 0;
+            q = (s % M1) + 1;
+          } else {
+            p = ((pr + s) % M1) + 1;
+            q = ((M1 - pr + s) % M1) + 1;
+          }
+          if (p >= n || q >= n) continue;
+          cx<R>* wp = W + (int64_t)p * m;
+          cx<R>* wq = W + (int64_t)q * m;
+          R a = 0, bb = 0, gr = 0, gi = 0;
+          for (int i = lane; i < m; i += 32) {
+            cx<R> x = wp[i], y = wq[i];
+            a += cabs2(x);
+            bb += cabs2(y);
+            gr += x.x * y.x + x.y * y.y;
+            gi += x.x * y.y - x.y * y.x;
+          }
+          a = warp_sum(a);
+          bb = warp_sum(bb);
+          gr = warp_sum(gr);
+          gi = warp_sum(gi);
+          if (!(a > skip2) || !(bb > skip2)) continue;
+          // |g| and its phase without squaring tiny numbers
+          const R gm = fmax(fabs(gr), fabs(gi));
+          if (gm == R(0)) continue;
+          const R grs = gr / gm, gis = gi / gm;
+          const R hs = sqrt(grs * grs + gis * gis);
+          const R g = gm * hs;
+          if (!(g > tolm * sqrt(a) * sqrt(bb))) continue;
+          rotated = 1;
+          R zeta = (bb - a) / (R(2) * g);
+          R t = (zeta >= R(0) ? R(1) : R(-1)) / (fabs(zeta) + sqrt(R(1) + zeta * zeta));
+          R c = R(1) / sqrt(R(1) + t * t), sn = c * t;
+          cx<R> ec = {grs / hs, -gis / hs};  // conj(g / |g|), unit modulus
+          for (int i = lane; i < m; i += 32) {
+            cx<R> x = wp[i], y = cmul(ec, wq[i]);
+            wp[i] = {c * x.x - sn * y.x, c * x.y - sn * y.y};
+            wq[i] = {sn * x.x + c * y.x, sn * x.y + c * y.y};
+          }
+          cx<R>* vp = V + (int64_t)p * n;
+          cx<R>* vq = V + (int64_t)q * n;
+          for (int i = lane; i < n; i += 32) {
+            cx<R> x = vp[i], y = cmul(ec, vq[i]);
+            vp[i] = {c * x.x - sn * y.x, c * x.y - sn * y.y};
+            vq[i] = {sn * x.x + c * y.x, sn * x.y + c * y.y};
+          }
+        }
+        __syncthreads();
+      }
+      // every thread takes the same decision (a block-wide OR at one barrier)
+      if (!__syncthreads_or(rotated)) break;
+    }
+    if (sweep == d.max_sweeps && tid == 0) atomicOr(&d.err[b], ERR_NO_CONVERGE);
+  }
+
+  // singular values (double), sort descending, rank
+  for (int j = warp; j < n; j += nwarps) {
+    double acc = 0.0;
+    const cx<R>* wj = W + (int64_t)j * m;
+    for (int i = lane; i < m; i += 32) acc += (double)cabs2(wj[i]);
+    acc = warp_sum(acc);
+    if (lane == 0) {
+      double sj = sqrt(acc);
+      if (!(sj >= 0.0 && sj < 1e300)) {  // NaN / inf: flag, rank it last
+        atomicOr(&d.err[b], ERR_NAN);
+        sj = 0.0;
+      }
+      sv[j] = sj;
+    }
+  }
+  __syncthreads();
+  for (int j = tid; j < n; j += blockDim.x) {
+    double sj = sv[j];
+    int r = 0;
+    for (int i = 0; i < n; ++i) {
+      double si = sv[i];
+      r += (si > sj) || (si == sj && i < j);
+    }
+    perm[r] = j;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    for (int i = 0; i < n; ++i)
+      if (perm[i] < 0 || perm[i] >= n) atomicOr(&d.err[b], ERR_NAN);
+    double smax = sv[perm[0]];
+    int k = 0;
+    double tot = 0.0;
+    for (int i = 0; i < n; ++i) {
+      double s = sv[perm[i]];
+      tot += s * s;
+      if (s > d.eps * smax) ++k;
+    }
+    if (k < 1) k = 1;
+    double scale = 1.0;
+    if (smax == 0.0) atomicOr(&d.err[b], ERR_ZERO_NORM);
+    if (capped && k > d.chi) {
+      double dsc = 0.0;
+      for (int i = d.chi; i < n; ++i) dsc += sv[perm[i]] * sv[perm[i]];
+      dsc = tot > 0.0 ? dsc / tot : 0.0;
+      d.disc[b] += dsc;
+      scale = dsc < 1.0 ? 1.0 / sqrt(1.0 - dsc) : 1.0;
+      k = d.chi;
+    }
+    s_k = k;
+    s_scale = scale;
+    const int bond = (w == v / 2) ? v : w;
+    D[bond] = k;
+    d.knew[b] = k;
+    d.nold[b] = n;
+  }
+  __syncthreads();
+  const int k = s_k;
+  const R scale = (R)s_scale;
+  // T_v <- U_k with the bond dimension k
+  for (int idx = tid; idx < m * k; idx += blockDim.x) {
+    int c = idx / m, i = idx - c * m;
+    int j = perm[c];
+    if (j < 0 || j >= n) continue;
+    double s = sv[j];
+    R inv = s > 0.0 ? (R)(1.0 / s) : R(0);
+    cx<R> val = cscale(W[(int64_t)j * m + i], inv);
+    int dst;
+    if (leg == 2) dst = i * k + c;
+    else if (leg == 0) dst = c * m + i;
+    else {
+      int l = i / du, u = i - l * du;
+      dst = (l * k + c) * du + u;
+    }
+    T[dst] = val;
+  }
+  // R = S_k V_k^dag (k x n, row-major)
+  cx<R>* Rm = d.Rm + (int64_t)b * d.vstride;
+  for (int idx = tid; idx < k * n; idx += blockDim.x) {
+    int c = idx / n, x = idx - c * n;
+    int j = perm[c];
+    if (j < 0 || j >= n) continue;
+    cx<R> vv = V[(int64_t)j * n + x];
+    R s = (R)sv[j] * scale;
+    Rm[idx] = {s * vv.x, -s * vv.y};
+  }
+}
+
+// Neighbour w absorbs R (k x n) on its leg towards v:
+//   out[o][i][u] = sum_x R[i][x] in[o][x][u]   (o, u: the other legs)
+// written to the workspace W (then copied back).
+template <typename R>
+__global__ void __launch_bounds__(256) k_absorb(Dev<R> d, int w, int v) {
+  const int b = blockIdx.z;
+  const int* D = d.dims + b * d.ds;
+  const int lw = (v == 2 * w) ? 0 : ((v == 2 * w + 1) ? 1 : 2);
+  const int dl = D[2 * w], dr = D[2 * w + 1], du = D[w];
+  const int n = d.nold[b], k = d.knew[b];
+  int outer, inner;
+  if (lw == 0) {
+    outer = 1;
+    inner = dr * du;
+  } else if (lw == 1) {
+    outer = dl;
+    inner = du;
+  } else {
+    outer = dl * dr;
+    inner = 1;
+  }
+  const int J = outer * inner;
+  const int i0 = blockIdx.y * 64, j0 = blockIdx.x * 64;
+  if (k <= 0 || (int64_t)k * J > d.wstride || (int64_t)n * J > d.wstride) return;
+  if (i0 >= k || j0 >= J) return;
+  const cx<R>* Rm = d.Rm + (int64_t)b * d.vstride;
+  const cx<R>* in = node_ptr(d, b, w);
+  cx<R>* out = d.W + (int64_t)b * d.wstride;
+  __shared__ cx<R> As[16][64];
+  __shared__ cx<R> Bs[16][64];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  cx<R> acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[a][c] = {R(0), R(0)};
+  for (int x0 = 0; x0 < n; x0 += 16) {
+    for (int e = threadIdx.x; e < 16 * 64; e += 256) {
+      int xx = e / 64, ii = e % 64;
+      int i = i0 + ii, x = x0 + xx;
+      As[xx][ii] = (i < k && x < n) ? Rm[(int64_t)i * n + x] : cx<R>{R(0), R(0)};
+      int j = j0 + ii;
+      cx<R> bv = {R(0), R(0)};
+      if (j < J && x < n) {
+        int o = j / inner, u = j - o * inner;
+        bv = in[((int64_t)o * n + x) * inner + u];
+      }
+      Bs[xx][ii] = bv;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int xx = 0; xx < 16; ++xx) {
+      cx<R> av[4], bv[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) av[a] = As[xx][ty * 4 + a];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) bv[c] = Bs[xx][tx * 4 + c];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[a][c] = cadd(acc[a][c], cmul(av[a], bv[c]));
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    int i = i0 + ty * 4 + a;
+    if (i >= k) continue;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      int j = j0 + tx * 4 + c;
+      if (j >= J) continue;
+      int o = j / inner, u = j - o * inner;
+      out[((int64_t)o * k + i) * inner + u] = acc[a][c];
+    }
+  }
+}
+
+// Copy the workspace back into node v (count from its current dims).
+template <typename R>
+__global__ void k_copy_back(Dev<R> d, int v) {
+  const int b = blockIdx.y;
+  const int* D = d.dims + b * d.ds;
+  const int64_t cnt = (int64_t)D[2 * v] * D[2 * v + 1] * D[v];
+  if (cnt > d.wstride) return;
+  cx<R>* T = node_ptr(d, b, v);
+  const cx<R>* W = d.W + (int64_t)b * d.wstride;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < cnt;
+       i += (int64_t)gridDim.x * blockDim.x)
+    T[i] = W[i];
+}
+
+// ------------------------------------------------------------------ MPO threading
+// Operator-Schmidt factors of CNOT: control side {|0><0|, |1><1|}, target side
+// {I, X}.  A factor F_k applied on a leaf leg of node v; the up bond becomes
+// (k, u) with index k * du + u.
+template <typename R>
+__global__ void k_thread_leaf(Dev<R> d, int v, int leg, int side) {
+  const int b = blockIdx.y;
+  int* D = d.dims + b * d.ds;
+  const int dl = D[2 * v], dr = D[2 * v + 1], du = D[v];
+  const int cnt = dl * dr * 2 * du;
+  if (cnt > d.wstride) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&d.err[b], ERR_CAPACITY);
+    return;
+  }
+  const cx<R>* T = node_ptr(d, b, v);
+  cx<R>* out = d.W + (int64_t)b * d.wstride;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < cnt; idx += gridDim.x * blockDim.x) {
+    int u2 = idx % (2 * du);
+    int rest = idx / (2 * du);
+    int y = rest % dr, x = rest / dr;
+    int kk = u2 / du, u = u2 - kk * du;
+    int xo = leg == 0 ? x : y;   // output physical index on the gate leg
+    cx<R> val;
+    if (side == 0) {              // |k><k| on the control
+      val = (xo == kk) ? T[(x * dr + y) * du + u] : cx<R>{R(0), R(0)};
+    } else {                      // I (k=0) or X (k=1) on the target
+      int xi = kk ? 1 - xo : xo;
+      int xs = leg == 0 ? xi : x, ys = leg == 0 ? y : xi;
+      val = T[(xs * dr + ys) * du + u];
+    }
+    out[idx] = val;
+  }
+}
+
+template <typename R>
+__global__ void k_thread_dims_leaf(Dev<R> d, int v, int B) {
+  int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b < B) d.dims[b * d.ds + v] *= 2;
+}
+
+// Internal path node: its path-child leg and its up leg both carry k (block
+// diagonal).  The child leg's dimension in dims is already doubled.
+template <typename R>
+__global__ void k_thread_node(Dev<R> d, int v, int leg) {
+  const int b = blockIdx.y;
+  const int* D = d.dims + b * d.ds;
+  const int dl0 = D[2 * v], dr0 = D[2 * v + 1], du = D[v];
+  const int dl = leg == 0 ? dl0 / 2 : dl0, dr = leg == 1 ? dr0 / 2 : dr0;  // input dims
+  const int ol = leg == 0 ? 2 * dl : dl, orr = leg == 1 ? 2 * dr : dr, ou = 2 * du;
+  const int cnt = ol * orr * ou;
+  if (cnt > d.wstride) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&d.err[b], ERR_CAPACITY);
+    return;
+  }
+  const cx<R>* T = node_ptr(d, b, v);
+  cx<R>* out = d.W + (int64_t)b * d.wstride;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < cnt; idx += gridDim.x * blockDim.x) {
+    int u2 = idx % ou, rest = idx / ou;
+    int y2 = rest % orr, x2 = rest / orr;
+    int ku = u2 / du, u = u2 - ku * du;
+    int kc, x = x2, y = y2;
+    if (leg == 0) {
+      kc = x2 / dl;
+      x = x2 - kc * dl;
+    } else {
+      kc = y2 / dr;
+      y = y2 - kc * dr;
+    }
+    out[idx] = (kc == ku) ? T[(x * dr + y) * du + u] : cx<R>{R(0), R(0)};
+  }
+}
+
+// Lowest common ancestor: both child legs carry the same k.
+template <typename R>
+__global__ void k_thread_lca(Dev<R> d, int v) {
+  const int b = blockIdx.y;
+  const int* D = d.dims + b * d.ds;
+  const int ol = D[2 * v], orr = D[2 * v + 1], du = D[v];
+  const int dl = ol / 2, dr = orr / 2;
+  const int cnt = ol * orr * du;
+  if (cnt > d.wstride) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&d.err[b], ERR_CAPACITY);
+    return;
+  }
+  const cx<R>* T = node_ptr(d, b, v);
+  cx<R>* out = d.W + (int64_t)b * d.wstride;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < cnt; idx += gridDim.x * blockDim.x) {
+    int u = idx % du, rest = idx / du;
+    int y2 = rest % orr, x2 = rest / orr;
+    int k1 = x2 / dl, x = x2 - k1 * dl, k2 = y2 / dr, y = y2 - k2 * dr;
+    out[idx] = (k1 == k2) ? T[(x * dr + y) * du + u] : cx<R>{R(0), R(0)};
+  }
+}
+
+// Both qubits in one node: CNOT permutes the leaf indices in place.
+template <typename R>
+__global__ void k_gate_node(Dev<R> d, int v, int orient, int B) {
+  int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  int b = idx / 64, u = idx % 64;
+  if (b >= B) return;
+  const int* D = d.dims + b * d.ds;
+  const int du = D[v];
+  if (u >= du) return;
+  cx<R>* T = node_ptr(d, b, v);
+  // element (x, y, u) at (x * 2 + y) * du + u, both legs of dimension 2
+  int i1, i2;
+  if (orient == 0) {  // control on l: swap (1,0) <-> (1,1)
+    i1 = 2 * du + u;
+    i2 = 3 * du + u;
+  } else {            // control on r: swap (0,1) <-> (1,1)
+    i1 = du + u;
+    i2 = 3 * du + u;
+  }
+  cx<R> t = T[i1];
+  T[i1] = T[i2];
+  T[i2] = t;
+}
+
+// ------------------------------------------------------------------ single-qubit layer
+// One thread per (trajectory, level-1 node): applies the node's ops of this
+// layer in program order to every column u of T[x][y][u].
+template <typename R>
+__device__ void apply2x2(cx<R>* T, int dl, int dr, int du, int leg, const cx<R> U[4]) {
+  for (int u = 0; u < du; ++u) {
+    if (leg == 0) {
+      for (int y = 0; y < dr; ++y) {
+        cx<R> a0 = T[(0 * dr + y) * du + u], a1 = T[(1 * dr + y) * du + u];
+        T[(0 * dr + y) * du + u] = cadd(cmul(U[0], a0), cmul(U[1], a1));
+        T[(1 * dr + y) * du + u] = cadd(cmul(U[2], a0), cmul(U[3], a1));
+      }
+    } else {
+      for (int x = 0; x < dl; ++x) {
+        cx<R> a0 = T[(x * dr + 0) * du + u], a1 = T[(x * dr + 1) * du + u];
+        T[(x * dr + 0) * du + u] = cadd(cmul(U[0], a0), cmul(U[1], a1));
+        T[(x * dr + 1) * du + u] = cadd(cmul(U[2], a0), cmul(U[3], a1));
+      }
+    }
+  }
+}
+
+template <typename R>
+__global__ void k_layer1q(Dev<R> d, const Op1* ops, const Group1* groups, int g0, int ng, int B) {
+  int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  int b = idx / ng, g = idx % ng;
+  if (b >= B) return;
+  const Group1 G = groups[g0 + g];
+  const int v = G.node;
+  const int* D = d.dims + b * d.ds;
+  const int dl = D[2 * v], dr = D[2 * v + 1], du = D[v];
+  cx<R>* T = node_ptr(d, b, v);
+  const R rs2 = (R)0.70710678118654752440;
+  for (int e = G.begin; e < G.end; ++e) {
+    const Op1 o = ops[e];
+    cx<R> U[4];
+    if (o.kind == O1_RESET_Z || o.kind == O1_RESET_X) {
+      uint8_t* lq = d.last + (int64_t)b * d.N + o.qubit;
+      if (*lq) {
+        U[0] = {0, 0}; U[1] = {1, 0}; U[2] = {1, 0}; U[3] = {0, 0};
+        apply2x2(T, dl, dr, du, o.leg, U);
+        *lq = 0;
+      }
+      if (o.kind == O1_RESET_X) {
+        U[0] = {rs2, 0}; U[1] = {rs2, 0}; U[2] = {rs2, 0}; U[3] = {-rs2, 0};
+        apply2x2(T, dl, dr, du, o.leg, U);
+      }
+    } else if (o.kind == O1_SRX) {
+      double th = d.theta[b];
+      R c = (R)cos(th), s = (R)sin(th);
+      U[0] = {c, 0}; U[1] = {0, -s}; U[2] = {0, -s}; U[3] = {c, 0};
+      apply2x2(T, dl, dr, du, o.leg, U);
+    } else if (o.kind == O1_PTA) {
+      double p[4];
+      if (d.noise == TTN_NOISE_SRX_PTA) {
+        double c = cos(d.theta[b]), s = sin(d.theta[b]);
+        p[0] = c * c; p[1] = s * s; p[2] = 0.0; p[3] = 0.0;
+      } else {
+        double g = d.gamma[b], r = sqrt(1.0 - g);
+        p[0] = (1 + r) * (1 + r) / 4; p[1] = g / 4; p[2] = g / 4; p[3] = (1 - r) * (1 - r) / 4;
+      }
+      double uu = draw_uniform(d.seed, d.traj[b], (uint32_t)o.event);
+      double cum = 0.0;
+      int kk = 3;
+      double margin = 1e300;
+      for (int i = 0; i < 3; ++i) {
+        cum += p[i];
+        margin = fmin(margin, fabs(uu - cum));
+        if (kk == 3 && uu < cum) kk = i;
+      }
+      if (margin < d.tie_eps) atomicAdd(&d.ties[b], 1);
+      atomicAdd(&d.logp[b], log(p[kk]));
+      if (kk == 1) { U[0] = {0, 0}; U[1] = {1, 0}; U[2] = {1, 0}; U[3] = {0, 0}; }
+      if (kk == 2) { U[0] = {0, 0}; U[1] = {0, -1}; U[2] = {0, 1}; U[3] = {0, 0}; }
+      if (kk == 3) { U[0] = {1, 0}; U[1] = {0, 0}; U[2] = {0, 0}; U[3] = {-1, 0}; }
+      if (kk > 0) apply2x2(T, dl, dr, du, o.leg, U);
+    }
+  }
+}
+
+// ------------------------------------------------------------------ centre sampling
+// One warp per trajectory; the centre is at the level-1 node of the qubit.
+template <typename R>
+__global__ void k_measure(Dev<R> d, int q, int event, int recbit, int xbasis, int pos, int B) {
+  const int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (b >= B) return;
+  const int v = pos >> 1, leg = pos & 1;
+  const int* D = d.dims + b * d.ds;
+  const int dl = D[2 * v], dr = D[2 * v + 1], du = D[v];
+  cx<R>* T = node_ptr(d, b, v);
+  const int cnt = dl * dr * du;
+  const R rs2 = (R)0.70710678118654752440;
+  if (xbasis) {  // H on the qubit's leg, then Z measurement
+    const int half = cnt / 2;
+    for (int e = lane; e < half; e += 32) {
+      int i0, i1;
+      if (leg == 0) { i0 = e; i1 = e + dr * du; }
+      else { int x = e / du, u = e % du; i0 = (x * dr) * du + u; i1 = (x * dr + 1) * du + u; }
+      cx<R> a0 = T[i0], a1 = T[i1];
+      T[i0] = {rs2 * (a0.x + a1.x), rs2 * (a0.y + a1.y)};
+      T[i1] = {rs2 * (a0.x - a1.x), rs2 * (a0.y - a1.y)};
+    }
+    __syncwarp();
+  }
+  double n0 = 0.0, n1 = 0.0;
+  for (int e = lane; e < cnt; e += 32) {
+    int x = e / (dr * du), y = (e / du) % dr;
+    int bit = leg == 0 ? x : y;
+    double a = (double)cabs2(T[e]);
+    if (bit) n1 += a; else n0 += a;
+  }
+  n0 = warp_sum(n0);
+  n1 = warp_sum(n1);
+  double tot = n0 + n1;
+  double p1 = n1 / tot, p0 = 1.0 - p1;
+  double uu = draw_uniform(d.seed, d.traj[b], (uint32_t)event);
+  int mres = uu >= p0 ? 1 : 0;
+  double pm = mres ? p1 : p0;
+  R sc = (R)(1.0 / sqrt(mres ? n1 : n0));
+  for (int e = lane; e < cnt; e += 32) {
+    int x = e / (dr * du), y = (e / du) % dr;
+    int bit = leg == 0 ? x : y;
+    T[e] = bit == mres ? cscale(T[e], sc) : cx<R>{R(0), R(0)};
+  }
+  if (lane == 0) {
+    d.logp[b] += log(pm);
+    if (fabs(uu - p0) < d.tie_eps) d.ties[b] += 1;
+    d.rec[(int64_t)b * d.n_rec + recbit] = (uint8_t)mres;
+    d.last[(int64_t)b * d.N + q] = (uint8_t)mres;
+    if (!(tot > 0.0)) atomicOr(&d.err[b], ERR_ZERO_NORM);
+  }
+}
+
+// Amplitude damping at one location (Eqs. 2-3), exact Kraus unravelling:
+// jump with probability gamma * P(1).
+template <typename R>
+__global__ void k_ad(Dev<R> d, int q, int event, int pos, int B) {
+  const int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (b >= B) return;
+  const int v = pos >> 1, leg = pos & 1;
+  const int* D = d.dims + b * d.ds;
+  const int dl = D[2 * v], dr = D[2 * v + 1], du = D[v];
+  cx<R>* T = node_ptr(d, b, v);
+  const int cnt = dl * dr * du;
+  double n0 = 0.0, n1 = 0.0;
+  for (int e = lane; e < cnt; e += 32) {
+    int x = e / (dr * du), y = (e / du) % dr;
+    int bit = leg == 0 ? x : y;
+    double a = (double)cabs2(T[e]);
+    if (bit) n1 += a; else n0 += a;
+  }
+  n0 = warp_sum(n0);
+  n1 = warp_sum(n1);
+  const double g = d.gamma[b];
+  const double tot = n0 + n1;
+  const double P1 = n1 / tot;
+  const double p1 = g * P1;
+  const double uu = draw_uniform(d.seed, d.traj[b], (uint32_t)event);
+  const bool jump = uu < p1;
+  __syncwarp();
+  if (jump) {
+    // K1 = sqrt(g)|0><1|: the |1> slice moves to |0>, normalised by sqrt(n1)
+    R sc = (R)(1.0 / sqrt(n1));
+    const int half = cnt / 2;
+    for (int e = lane; e < half; e += 32) {
+      int i0, i1;
+      if (leg == 0) { i0 = e; i1 = e + dr * du; }
+      else { int x = e / du, u = e % du; i0 = (x * dr) * du + u; i1 = (x * dr + 1) * du + u; }
+      T[i0] = cscale(T[i1], sc);
+      T[i1] = {R(0), R(0)};
+    }
+  } else {
+    R s0 = (R)(1.0 / sqrt(n0 + (1.0 - g) * n1));
+    R s1 = (R)(sqrt(1.0 - g) / sqrt(n0 + (1.0 - g) * n1));
+    for (int e = lane; e < cnt; e += 32) {
+      int x = e / (dr * du), y = (e / du) % dr;
+      int bit = leg == 0 ? x : y;
+      T[e] = cscale(T[e], bit ? s1 : s0);
+    }
+  }
+  if (lane == 0) {
+    d.logp[b] += jump ? log(p1) : log1p(-p1);
+    if (fabs(uu - p1) < d.tie_eps) d.ties[b] += 1;
+  }
+}
+
+// ------------------------------------------------------------------ debug amplitudes
+// Contract the whole tree of trajectory b for every basis state (N <= 24,
+// bonds <= 64, leaves <= 16): one thread per amplitude, bottom-up.
+template <typename R>
+__global__ void k_amplitudes(Dev<R> d, int b, const int32_t* qubit_of_leaf, int nq,
+                             double* out) {
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= ((int64_t)1 << nq)) return;
+  const int L = d.L;
+  const int* D = d.dims + b * d.ds;
+  cx<double> vec[16][64];  // per node (v < L <= 16), bonds <= 64
+  for (int v = L - 1; v >= 1; --v) {
+    const int dl = D[2 * v], dr = D[2 * v + 1], du = D[v];
+    const cx<R>* T = node_ptr(d, b, v);
+    cx<double> acc[64];
+    for (int u = 0; u < du; ++u) acc[u] = {0.0, 0.0};
+    if (2 * v >= L) {
+      int ql = qubit_of_leaf[2 * v - L], qr = qubit_of_leaf[2 * v + 1 - L];
+      int x = ql >= 0 ? (int)((idx >> ql) & 1) : 0;
+      int y = qr >= 0 ? (int)((idx >> qr) & 1) : 0;
+      for (int u = 0; u < du; ++u) {
+        cx<R> t = T[(x * dr + y) * du + u];
+        acc[u] = {(double)t.x, (double)t.y};
+      }
+    } else {
+      for (int x = 0; x < dl; ++x)
+        for (int y = 0; y < dr; ++y) {
+          cx<double> a = vec[2 * v][x], bb = vec[2 * v + 1][y];
+          cx<double> ab = {a.x * bb.x - a.y * bb.y, a.x * bb.y + a.y * bb.x};
+          for (int u = 0; u < du; ++u) {
+            cx<R> t = T[(x * dr + y) * du + u];
+            acc[u].x += ab.x * (double)t.x - ab.y * (double)t.y;
+            acc[u].y += ab.x * (double)t.y + ab.y * (double)t.x;
+          }
+        }
+    }
+    for (int u = 0; u < du; ++u) vec[v][u] = acc[u];
+  }
+  out[2 * idx] = vec[1][0].x;
+  out[2 * idx + 1] = vec[1][0].y;
+}
+
+// ------------------------------------------------------------------ host driver
+#define CK(call)                                                                   \
+  do {                                                                             \
+    cudaError_t e_ = (call);                                                       \
+    if (e_ != cudaSuccess) {                                                       \
+      set_error(std::string("CUDA: ") + cudaGetErrorString(e_) + " at " #call);    \
+      return TTN_ECUDA;                                                            \
+    }                                                                              \
+  } while (0)
+
+static inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+ttn_status philox_uniforms_device(uint64_t seed, const uint64_t* trajs, uint64_t n_traj,
+                                  const int32_t* events, int32_t n_events, double* out) {
+  uint64_t* dt = nullptr;
+  int32_t* de = nullptr;
+  double* dout = nullptr;
+  const size_t cnt = (size_t)n_traj * n_events;
+  CK(cudaMalloc(&dt, n_traj * sizeof(uint64_t)));
+  CK(cudaMalloc(&de, n_events * sizeof(int32_t)));
+  CK(cudaMalloc(&dout, cnt * sizeof(double)));
+  CK(cudaMemcpy(dt, trajs, n_traj * sizeof(uint64_t), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(de, events, n_events * sizeof(int32_t), cudaMemcpyHostToDevice));
+  k_philox_uniforms<<<ceil_div(cnt, 256), 256>>>(seed, dt, (int)n_traj, de, n_events, dout);
+  CK(cudaGetLastError());
+  CK(cudaMemcpy(out, dout, cnt * sizeof(double), cudaMemcpyDeviceToHost));
+  cudaFree(dt);
+  cudaFree(de);
+  cudaFree(dout);
+  return TTN_OK;
+}
+
+// Bond capacity of bond (x, parent(x)) outside gates.
+static std::vector<int> bond_caps(const ttn_circuit& c, int chi) {
+  const int L = c.L;
+  std::vector<int> nq(2 * L, 0);
+  for (int q = 0; q < c.N; ++q) nq[L + c.leaf_of_qubit[q]] = 1;
+  for (int x = L - 1; x >= 1; --x) nq[x] = nq[2 * x] + nq[2 * x + 1];
+  std::vector<int> cap(2 * L, 1);
+  for (int x = 2; x < 2 * L; ++x) {
+    if (x >= L) {
+      cap[x] = nq[x] ? 2 : 1;
+      continue;
+    }
+    int a = nq[x], bq = c.N - nq[x];
+    int e = std::min(a, bq);
+    int64_t v = e >= 30 ? (int64_t)1 << 30 : ((int64_t)1 << e);
+    cap[x] = (int)std::min<int64_t>(v, chi);
+  }
+  return cap;
+}
+
+template <typename R>
+struct Engine {
+  const ttn_circuit& c;
+  const Program& prog;
+  int chi, noise, B;
+  cudaStream_t st;
+  std::vector<int> bcap;           // bond caps (outside gates)
+  std::vector<int64_t> ncap;       // node slot capacity (elements)
+  std::vector<int64_t> off;
+  int64_t tstride = 0, wstride = 0, vstride = 0;
+  int nmax = 0;
+  // device buffers
+  cx<R>* dT = nullptr;
+  cx<R>* dW = nullptr;
+  cx<R>* dV = nullptr;
+  cx<R>* dR = nullptr;
+  int64_t* dOff = nullptr;
+  int32_t* dDims = nullptr;
+  double* dSv = nullptr;
+  int32_t* dPerm = nullptr;
+  int32_t* dK = nullptr;
+  int32_t* dN = nullptr;
+  double* dLogp = nullptr;
+  double* dDisc = nullptr;
+  int32_t* dTies = nullptr;
+  uint8_t* dRec = nullptr;
+  uint8_t* dLast = nullptr;
+  double* dTheta = nullptr;
+  double* dGamma = nullptr;
+  uint64_t* dTraj = nullptr;
+  int32_t* dErr = nullptr;
+  int32_t* dLeafdim = nullptr;
+  Op1* dOp1 = nullptr;
+  Group1* dGroups = nullptr;
+  Dev<R> dev{};
+
+  Engine(const ttn_circuit& cc, const Program& p, int chi_, int noise_, cudaStream_t s)
+      : c(cc), prog(p), chi(chi_), noise(noise_), B(0), st(s) {
+    bcap = bond_caps(c, chi);
+    const int L = c.L;
+    ncap.assign(L, 0);
+    off.assign(L, 0);
+    int64_t acc = 0;
+    int maxb = 2;
+    for (int v = 1; v < L; ++v) {
+      int64_t cl = bcap[2 * v], cr = bcap[2 * v + 1], cu = v == 1 ? 1 : bcap[v];
+      ncap[v] = 4 * cl * cr * cu;
+      off[v] = acc;
+      acc += (ncap[v] + 31) / 32 * 32;
+      maxb = std::max<int>(maxb, (int)std::max(cl, std::max(cr, cu)));
+    }
+    tstride = acc;
+    int64_t wmax = 0;
+    for (int v = 1; v < L; ++v) wmax = std::max(wmax, ncap[v]);
+    wstride = (wmax + 31) / 32 * 32;
+    nmax = 2 * maxb;
+    vstride = (int64_t)nmax * nmax;
+  }
+
+  size_t bytes_per_traj() const {
+    return sizeof(cx<R>) * (size_t)(tstride + wstride + 2 * vstride) +
+           sizeof(int32_t) * (2 * c.L + 2 * nmax + 4) + sizeof(double) * (nmax + 5) + c.n_rec + c.N +
+           64;
+  }
+
+  ttn_status alloc(int Bmax) {
+    B = Bmax;
+    CK(cudaMalloc(&dT, sizeof(cx<R>) * (size_t)tstride * B));
+    CK(cudaMalloc(&dW, sizeof(cx<R>) * (size_t)wstride * B));
+    CK(cudaMalloc(&dV, sizeof(cx<R>) * (size_t)vstride * B));
+    CK(cudaMalloc(&dR, sizeof(cx<R>) * (size_t)vstride * B));
+    CK(cudaMalloc(&dOff, sizeof(int64_t) * c.L));
+    CK(cudaMalloc(&dDims, sizeof(int32_t) * 2 * c.L * B));
+    CK(cudaMalloc(&dSv, sizeof(double) * nmax * B));
+    CK(cudaMalloc(&dPerm, sizeof(int32_t) * nmax * B));
+    CK(cudaMalloc(&dK, sizeof(int32_t) * B));
+    CK(cudaMalloc(&dN, sizeof(int32_t) * B));
+    CK(cudaMalloc(&dLogp, sizeof(double) * B));
+    CK(cudaMalloc(&dDisc, sizeof(double) * B));
+    CK(cudaMalloc(&dTies, sizeof(int32_t) * B));
+    CK(cudaMalloc(&dRec, (size_t)c.n_rec * B));
+    CK(cudaMalloc(&dLast, (size_t)c.N * B));
+    CK(cudaMalloc(&dTheta, sizeof(double) * B));
+    CK(cudaMalloc(&dGamma, sizeof(double) * B));
+    CK(cudaMalloc(&dTraj, sizeof(uint64_t) * B));
+    CK(cudaMalloc(&dErr, sizeof(int32_t) * B));
+    CK(cudaMalloc(&dLeafdim, sizeof(int32_t) * c.L));
+    CK(cudaMalloc(&dOp1, sizeof(Op1) * std::max<size_t>(1, prog.op1.size())));
+    CK(cudaMalloc(&dGroups, sizeof(Group1) * std::max<size_t>(1, prog.groups.size())));
+    CK(cudaMemcpy(dOff, off.data(), sizeof(int64_t) * c.L, cudaMemcpyHostToDevice));
+    std::vector<int32_t> leafdim(c.L, 1);
+    for (int q = 0; q < c.N; ++q) leafdim[c.leaf_of_qubit[q]] = 2;
+    CK(cudaMemcpy(dLeafdim, leafdim.data(), sizeof(int32_t) * c.L, cudaMemcpyHostToDevice));
+    if (!prog.op1.empty())
+      CK(cudaMemcpy(dOp1, prog.op1.data(), sizeof(Op1) * prog.op1.size(), cudaMemcpyHostToDevice));
+    if (!prog.groups.empty())
+      CK(cudaMemcpy(dGroups, prog.groups.data(), sizeof(Group1) * prog.groups.size(),
+                    cudaMemcpyHostToDevice));
+    dev.T = dT;
+    dev.off = dOff;
+    dev.tstride = tstride;
+    dev.dims = dDims;
+    dev.ds = 2 * c.L;
+    dev.W = dW;
+    dev.wstride = wstride;
+    dev.V = dV;
+    dev.Rm = dR;
+    dev.vstride = vstride;
+    dev.sv = dSv;
+    dev.perm = dPerm;
+    dev.nmax = nmax;
+    dev.knew = dK;
+    dev.nold = dN;
+    dev.logp = dLogp;
+    dev.disc = dDisc;
+    dev.ties = dTies;
+    dev.rec = dRec;
+    dev.n_rec = c.n_rec;
+    dev.last = dLast;
+    dev.N = c.N;
+    dev.theta = dTheta;
+    dev.gamma = dGamma;
+    dev.traj = dTraj;
+    dev.L = c.L;
+    dev.chi = chi;
+    dev.noise = noise;
+    dev.err = dErr;
+    return TTN_OK;
+  }
+
+  void release() {
+    void* ptrs[] = {dT, dW, dV, dR, dOff, dDims, dSv, dPerm, dK, dN, dLogp, dDisc, dTies, dRec,
+                    dLast, dTheta, dGamma, dTraj, dErr, dLeafdim, dOp1, dGroups};
+    for (void* p : ptrs)
+      if (p) cudaFree(p);
+  }
+
+  // Launch the step program for trajectories [0, nb) of the batch.
+  ttn_status launch(int nb, int stop_step) {
+    const int L = c.L;
+    dim3 gi(1, nb);
+    k_init<R><<<dim3(std::max(1, ceil_div(2 * L, 256)), nb), 256, 0, st>>>(dev, dLeafdim, nb);
+    CK(cudaGetLastError());
+    (void)gi;
+    const int nsteps = stop_step < 0 ? (int)prog.steps.size() : stop_step;
+    for (int si = 0; si < nsteps; ++si) {
+      const Step& s = prog.steps[si];
+      switch (s.kind) {
+        case S_MOVE: {
+          const int v = s.a, w = s.b;
+          k_svd_move<R><<<nb, 256, 0, st>>>(dev, v, w, s.c);
+          // neighbour absorbs R: grid from capacities
+          const int lw = (v == 2 * w) ? 0 : ((v == 2 * w + 1) ? 1 : 2);
+          int64_t cl = 2 * (int64_t)bcap[2 * w], cr = 2 * (int64_t)bcap[2 * w + 1],
+                  cu = w == 1 ? 1 : 2 * (int64_t)bcap[w];
+          int64_t kmax = lw == 0 ? cl : (lw == 1 ? cr : cu);
+          int64_t Jmax = ncap[w] * 2 / std::max<int64_t>(1, kmax);
+          Jmax = std::min<int64_t>(Jmax, (lw == 0 ? cr * cu : (lw == 1 ? cl * cu : cl * cr)));
+          dim3 ga(std::max(1, ceil_div(Jmax, 64)), std::max(1, ceil_div(kmax, 64)), nb);
+          k_absorb<R><<<ga, 256, 0, st>>>(dev, w, v);
+          k_copy_back<R><<<dim3(std::max(1, ceil_div(ncap[w], 256 * 4)), nb), 256, 0, st>>>(dev, w);
+          break;
+        }
+        case S_THREAD_LEAF: {
+          k_thread_leaf<R><<<dim3(std::max(1, ceil_div(ncap[s.a], 256)), nb), 256, 0, st>>>(
+              dev, s.a, s.b, s.c);
+          k_thread_dims_leaf<R><<<ceil_div(nb, 128), 128, 0, st>>>(dev, s.a, nb);
+          k_copy_back<R><<<dim3(std::max(1, ceil_div(ncap[s.a], 256 * 4)), nb), 256, 0, st>>>(dev, s.a);
+          break;
+        }
+        case S_THREAD_NODE: {
+          k_thread_node<R><<<dim3(std::max(1, ceil_div(ncap[s.a], 256)), nb), 256, 0, st>>>(
+              dev, s.a, s.b);
+          k_thread_dims_leaf<R><<<ceil_div(nb, 128), 128, 0, st>>>(dev, s.a, nb);
+          k_copy_back<R><<<dim3(std::max(1, ceil_div(ncap[s.a], 256 * 4)), nb), 256, 0, st>>>(dev, s.a);
+          break;
+        }
+        case S_THREAD_LCA: {
+          k_thread_lca<R><<<dim3(std::max(1, ceil_div(ncap[s.a], 256)), nb), 256, 0, st>>>(dev, s.a);
+          k_copy_back<R><<<dim3(std::max(1, ceil_div(ncap[s.a], 256 * 4)), nb), 256, 0, st>>>(dev, s.a);
+          break;
+        }
+        case S_GATE_NODE:
+          k_gate_node<R><<<ceil_div((int64_t)nb * 64, 256), 256, 0, st>>>(dev, s.a, s.b, nb);
+          break;
+        case S_LAYER1Q: {
+          const int ng = s.d - s.c;
+          k_layer1q<R><<<ceil_div((int64_t)nb * ng, 128), 128, 0, st>>>(dev, dOp1, dGroups, s.c, ng, nb);
+          break;
+        }
+        case S_MEASURE:
+          k_measure<R><<<ceil_div(nb, 4), 128, 0, st>>>(dev, s.a, s.b, s.c, s.d,
+                                                        L + c.leaf_of_qubit[s.a], nb);
+          break;
+        case S_AD:
+          k_ad<R><<<ceil_div(nb, 4), 128, 0, st>>>(dev, s.a, s.b, L + c.leaf_of_qubit[s.a], nb);
+          break;
+      }
+    }
+    CK(cudaGetLastError());
+    return TTN_OK;
+  }
+};
+
+// Thread dims doubling for the node steps uses the same kernel as the leaf
+// (only the up bond of the node doubles; the child bond was doubled when the
+// child was threaded).
+
+template <typename R>
+static ttn_status run_impl(const ttn_circuit& c, const RunRequest& rq, RunOutputs& out) {
+  Program prog = compile_program(c, rq.noise, -1);
+  cudaStream_t st = (cudaStream_t)rq.stream;
+  Engine<R> eng(c, prog, rq.chi, rq.noise, st);
+  eng.dev.seed = rq.seed;
+  eng.dev.eps = rq.svd_eps;
+  eng.dev.tie_eps = sizeof(R) == 8 ? 1e-9 : 1e-5;
+  eng.dev.tol = sizeof(R) == 8 ? 1e-15 : 1e-7;
+  eng.dev.max_sweeps = sizeof(R) == 8 ? 40 : 30;
+  size_t freeb = 0, totb = 0;
+  CK(cudaMemGetInfo(&freeb, &totb));
+  const size_t per = eng.bytes_per_traj();
+  size_t budget = (size_t)((double)freeb * 0.80);
+  if (rq.max_device_bytes > 0) budget = std::min(budget, rq.max_device_bytes);
+  int64_t Bmax = (int64_t)(budget / per);
+  if (Bmax < 1) {
+    set_error("one trajectory needs " + std::to_string(per) + " device bytes; " +
+              std::to_string(budget) + " available");
+    return TTN_ENOMEM;
+  }
+  Bmax = std::min<int64_t>(Bmax, (int64_t)rq.n_traj);
+  if (rq.max_batch > 0) Bmax = std::min<int64_t>(Bmax, rq.max_batch);
+  Bmax = std::min<int64_t>(Bmax, 32768);
+  ttn_status stt = eng.alloc((int)Bmax);
+  if (stt != TTN_OK) {
+    eng.release();
+    return stt;
+  }
+  out.batch = (int)Bmax;
+  out.bytes_per_traj = per;
+  std::vector<double> th(Bmax), ga(Bmax);
+  std::vector<uint64_t> tj(Bmax);
+  std::vector<int32_t> err(Bmax);
+  int stop = -1;
+  if (rq.debug_amps) stop = rq.last_layer < 0 ? 0 : prog.stop_step_of_layer[rq.last_layer];
+  for (uint64_t t0 = 0; t0 < rq.n_traj; t0 += Bmax) {
+    const int nb = (int)std::min<uint64_t>(Bmax, rq.n_traj - t0);
+    for (int i = 0; i < nb; ++i) {
+      th[i] = rq.theta_per_traj ? rq.theta_per_traj[t0 + i] : rq.theta;
+      ga[i] = rq.gamma_per_traj ? rq.gamma_per_traj[t0 + i] : rq.gamma;
+      tj[i] = rq.first_traj + t0 + i;
+    }
+    CK(cudaMemcpyAsync(eng.dTheta, th.data(), sizeof(double) * nb, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(eng.dGamma, ga.data(), sizeof(double) * nb, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(eng.dTraj, tj.data(), sizeof(uint64_t) * nb, cudaMemcpyHostToDevice, st));
+    ttn_status s2 = eng.launch(nb, stop);
+    if (s2 != TTN_OK) {
+      eng.release();
+      return s2;
+    }
+    // decode on the device (full circuits only)
+    if (!rq.debug_amps && out.fail) {
+      s2 = decode_device(c, nb, eng.dRec, out.fail + t0, nullptr, nullptr, st, out.on_device);
+      if (s2 == TTN_EOVERFLOW) {
+        out.decode_overflow += 1;
+      } else if (s2 != TTN_OK) {
+        eng.release();
+        return s2;
+      }
+    }
+    auto cp = [&](void* dst, const void* src, size_t bytes) -> cudaError_t {
+      return cudaMemcpyAsync(dst, src, bytes,
+                             out.on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st);
+    };
+    if (out.records) CK(cp(out.records + t0 * c.n_rec, eng.dRec, (size_t)nb * c.n_rec));
+    if (out.log_prob) CK(cp(out.log_prob + t0, eng.dLogp, sizeof(double) * nb));
+    if (out.discarded) CK(cp(out.discarded + t0, eng.dDisc, sizeof(double) * nb));
+    if (out.near_ties) CK(cp(out.near_ties + t0, eng.dTies, sizeof(int32_t) * nb));
+    CK(cudaMemcpyAsync(err.data(), eng.dErr, sizeof(int32_t) * nb, cudaMemcpyDeviceToHost, st));
+    if (rq.debug_amps) {
+      std::vector<int32_t> qol(c.L, -1);
+      for (int q = 0; q < c.N; ++q) qol[c.leaf_of_qubit[q]] = q;
+      int32_t* dq = nullptr;
+      double* da = nullptr;
+      const size_t na = (size_t)1 << c.N;
+      CK(cudaMalloc(&dq, sizeof(int32_t) * c.L));
+      CK(cudaMalloc(&da, sizeof(double) * 2 * na));
+      CK(cudaMemcpyAsync(dq, qol.data(), sizeof(int32_t) * c.L, cudaMemcpyHostToDevice, st));
+      k_amplitudes<R><<<ceil_div(na, 64), 64, 0, st>>>(eng.dev, 0, dq, c.N, da);
+      CK(cudaGetLastError());
+      CK(cudaMemcpyAsync(rq.debug_amps, da, sizeof(double) * 2 * na, cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      cudaFree(dq);
+      cudaFree(da);
+    }
+    CK(cudaStreamSynchronize(st));
+    for (int i = 0; i < nb; ++i) out.err_flags |= err[i];
+    if (out.err_flags & (ERR_CAPACITY | ERR_ZERO_NORM | ERR_NAN)) {
+      eng.release();
+      set_error(std::string("engine: ") +
+                ((out.err_flags & ERR_CAPACITY) ? "tensor exceeded its slot capacity"
+                 : (out.err_flags & ERR_NAN) ? "non-finite singular value" : "zero-norm state"));
+      return TTN_ECUDA;
+    }
+  }
+  eng.release();
+  return TTN_OK;
+}
+
+ttn_status run_trajectories_device(const ttn_circuit& c, const RunRequest& rq, RunOutputs& out) {
+  if (rq.precision == TTN_PREC_FP64) return run_impl<double>(c, rq, out);
+  return run_impl<float>(c, rq, out);
+}
+
+}  // namespace ttn

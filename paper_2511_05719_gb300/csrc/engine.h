@@ -1,0 +1,48 @@
+// Host-facing entry points of the CUDA engine and decoder.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include "internal.h"
+
+namespace ttn {
+
+struct RunRequest {
+  int noise = 0, chi = 1, precision = 0;
+  double theta = 0.0, gamma = 0.0, svd_eps = 0.0;
+  uint64_t seed = 0, first_traj = 0, n_traj = 0;
+  const double* theta_per_traj = nullptr;  // host, [n_traj]
+  const double* gamma_per_traj = nullptr;
+  int last_layer = -1;           // >= 0: stop after this layer (debug)
+  double* debug_amps = nullptr;  // host [2^N * 2], with last_layer, one trajectory
+  void* stream = nullptr;
+  size_t max_device_bytes = 0;   // 0: 80% of free device memory
+  int max_batch = 0;             // 0: as many as fit
+};
+
+struct RunOutputs {
+  bool on_device = false;        // output pointers are device pointers
+  bool fail_on_device = false;
+  uint8_t* records = nullptr;
+  uint8_t* fail = nullptr;
+  double* log_prob = nullptr;
+  double* discarded = nullptr;
+  int32_t* near_ties = nullptr;
+  int err_flags = 0;
+  int batch = 0;
+  size_t bytes_per_traj = 0;
+  int decode_overflow = 0;
+};
+
+ttn_status run_trajectories_device(const ttn_circuit& c, const RunRequest& rq, RunOutputs& out);
+
+// Decodes nb records that live on the device; fail/color/score are device
+// pointers when on_device, else host pointers.
+ttn_status decode_device(const ttn_circuit& c, int nb, const uint8_t* d_records, uint8_t* fail,
+                         int32_t* color, int64_t* score, void* stream, bool on_device);
+
+ttn_status philox_uniforms_device(uint64_t seed, const uint64_t* trajs, uint64_t n_traj,
+                                  const int32_t* events, int32_t n_events, double* out);
+
+}  // namespace ttn

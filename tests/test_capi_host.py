@@ -1,0 +1,70 @@
+"""C-ABI checks that need no GPU: the library loads, exports every symbol
+include/ttn.h declares, and its host-side circuit logic equals the oracle's."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _lib_or_skip():
+    from paper_2511_05719_gb300 import _lib
+    if not os.path.exists(_lib.library_path()):
+        pytest.skip("libttn.so not built")
+    return _lib
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "ttn.h")).read()
+    return sorted(set(re.findall(r"\b(ttn_[a-z_]+)\s*\(", src)))
+
+
+def test_header_exports_every_symbol():
+    _lib = _lib_or_skip()
+    lib = ctypes.CDLL(_lib.library_path())
+    syms = declared_symbols()
+    assert len(syms) >= 12
+    for s in syms:
+        assert hasattr(lib, s), s
+
+
+@pytest.mark.parametrize("d,C", [(3, 1), (3, 3), (5, 5), (7, 7)])
+def test_circuit_ir_equals_oracle(d, C):
+    _lib_or_skip()
+    import paper_2511_05719_gb300 as P
+    from oracle.circuit import build_circuit
+    c = P.Circuit(d, C, layout="default")
+    oc = build_circuit(d, C)
+    assert (c.n_qubits, c.n_layers, c.n_events, c.n_record_bits) == \
+        (oc.n_qubits, oc.n_layers, oc.n_events, oc.n_record_bits)
+    assert np.array_equal(c.ops(), np.array(oc.ops, dtype=np.int32))
+
+
+@pytest.mark.parametrize("d,C", [(3, 3), (5, 5), (7, 7)])
+def test_layouts_valid(d, C):
+    _lib_or_skip()
+    import paper_2511_05719_gb300 as P
+    for lay in ("default", "optimized"):
+        c = P.Circuit(d, C, layout=lay)
+        lo = c.layout()
+        assert len(set(lo.tolist())) == c.n_qubits
+        assert lo.min() >= 0 and lo.max() < c.n_leaves
+        assert c.n_leaves == 1 << int(np.ceil(np.log2(c.n_qubits)))
+
+
+def test_invalid_arguments():
+    _lib_or_skip()
+    import paper_2511_05719_gb300 as P
+    for bad in [(4, 1), (1, 1), (3, 0), (13, 1)]:
+        with pytest.raises(P.TTNError) as e:
+            P.Circuit(*bad)
+        assert e.value.status == 1
+    with pytest.raises(P.TTNError):
+        P.Circuit(3, 1, leaf_of_qubit=[0] * 13)          # not injective
+    with pytest.raises(P.TTNError):
+        P.Circuit(3, 1, leaf_of_qubit=list(range(4, 17)))  # leaf 16 is outside 16 leaves
+    c = P.Circuit(3, 1, leaf_of_qubit=list(range(13)))
+    assert np.array_equal(c.layout(), np.arange(13))
