@@ -81,6 +81,10 @@ typedef struct {
                                     3e-7 (FP32)                           */
   const double* theta_per_traj;  /* optional [n_traj], overrides theta    */
   const double* gamma_per_traj;  /* optional [n_traj], overrides gamma    */
+  int32_t svd_mode;              /* factorisation of a centre move:
+                                    0 auto (FP32 bonds above 64: Gram),
+                                    1 one-sided Jacobi on the tensor,
+                                    2 Gram matrix + two-sided Jacobi       */
 } ttn_run_params;
 
 typedef struct ttn_circuit ttn_circuit;  /* opaque, library-owned */
@@ -144,6 +148,18 @@ ttn_status ttn_debug_state(const ttn_circuit* circuit, const ttn_run_params* par
  * n_traj x n_events pairs, computed on the device.  out: host [n_traj][n_events]. */
 ttn_status ttn_philox_uniforms(uint64_t seed, const uint64_t* trajs, uint64_t n_traj,
                                const int32_t* events, int32_t n_events, double* out);
+
+/* Profiling ledger.  Kernel classes: 0 one-sided Jacobi SVD move, 1 Gram
+ * GEMM, 2 Gram eigendecomposition, 3 U = M V GEMM, 4 bond absorption GEMM,
+ * 5 tensor copies, 6 other.  Between ttn_profile_begin(c) and
+ * ttn_profile_end, every run adds each class's algorithmic flops and bytes
+ * (counted from the live bond dimensions: complex GEMM 8mnk, eigensolver
+ * 36n^3, thin SVD 24mn^2 + 44n^3, bytes = operands read + written) and the
+ * device time of every launch of class c (CUDA events on the launch stream;
+ * c = -1 times nothing).  flops, bytes, launches: host [7] or NULL. */
+ttn_status ttn_profile_begin(int32_t timed_class);
+ttn_status ttn_profile_end(double* timed_ms, uint64_t* timed_launches, double* flops,
+                           double* bytes, uint64_t* launches);
 
 const char* ttn_status_string(ttn_status status);
 const char* ttn_last_error(void);

@@ -27,7 +27,8 @@ class RunParams(ctypes.Structure):
     _fields_ = [("noise", ctypes.c_int32), ("theta", ctypes.c_double), ("gamma", ctypes.c_double),
                 ("chi", ctypes.c_int32), ("precision", ctypes.c_int32), ("seed", ctypes.c_uint64),
                 ("first_traj", ctypes.c_uint64), ("svd_eps", ctypes.c_double),
-                ("theta_per_traj", c_dblp), ("gamma_per_traj", c_dblp)]
+                ("theta_per_traj", c_dblp), ("gamma_per_traj", c_dblp),
+                ("svd_mode", ctypes.c_int32)]
 
 
 class TTNError(RuntimeError):
@@ -38,7 +39,8 @@ class TTNError(RuntimeError):
 
 EXPORTS = ["ttn_build_circuit", "ttn_free_circuit", "ttn_circuit_info", "ttn_circuit_ops",
            "ttn_circuit_layout", "ttn_run_trajectories", "ttn_logical_error_rate", "ttn_decode",
-           "ttn_debug_state", "ttn_philox_uniforms", "ttn_status_string", "ttn_last_error"]
+           "ttn_debug_state", "ttn_philox_uniforms", "ttn_profile_begin", "ttn_profile_end",
+           "ttn_status_string", "ttn_last_error"]
 
 
 def library_path():
@@ -69,6 +71,8 @@ def load_library():
                                     c_dblp]
     lib.ttn_philox_uniforms.argtypes = [ctypes.c_uint64, c_u64p, ctypes.c_uint64, c_i32p,
                                         ctypes.c_int32, c_dblp]
+    lib.ttn_profile_begin.argtypes = [ctypes.c_int32]
+    lib.ttn_profile_end.argtypes = [c_dblp, c_u64p, c_dblp, c_dblp, c_u64p]
     lib.ttn_status_string.restype = ctypes.c_char_p
     lib.ttn_status_string.argtypes = [ctypes.c_int]
     lib.ttn_last_error.restype = ctypes.c_char_p
@@ -139,8 +143,11 @@ class Circuit:
         return out
 
 
+SVD_MODE = {"auto": 0, "jacobi": 1, "gram": 2}
+
+
 def _run_params(noise, theta, gamma, chi, precision, seed, first_traj, svd_eps,
-                theta_per_traj=None, gamma_per_traj=None):
+                theta_per_traj=None, gamma_per_traj=None, svd_mode="auto"):
     p = RunParams()
     p.noise = NOISE[noise] if isinstance(noise, str) else int(noise)
     p.theta = float(theta)
@@ -150,6 +157,7 @@ def _run_params(noise, theta, gamma, chi, precision, seed, first_traj, svd_eps,
     p.seed = int(seed)
     p.first_traj = int(first_traj)
     p.svd_eps = float(svd_eps)
+    p.svd_mode = SVD_MODE[svd_mode] if isinstance(svd_mode, str) else int(svd_mode)
     keep = []
     if theta_per_traj is not None:
         a = np.ascontiguousarray(theta_per_traj, dtype=np.float64)
@@ -164,14 +172,15 @@ def _run_params(noise, theta, gamma, chi, precision, seed, first_traj, svd_eps,
 
 def run_trajectories(circuit, n_traj, noise="srx", theta=0.0, gamma=0.0, chi=16,
                      precision="fp64", seed=0, first_traj=0, svd_eps=0.0,
-                     theta_per_traj=None, gamma_per_traj=None, out=None, stream=None):
+                     theta_per_traj=None, gamma_per_traj=None, out=None, stream=None,
+                     svd_mode="auto"):
     """Runs n_traj trajectories.  With `out=None` returns host numpy arrays
     {records, fail, log_prob, discarded, near_ties}.  With `out` a dict of
     torch CUDA tensors (any subset of those keys) and `stream` a CUDA stream
     handle (int), writes them on the device."""
     lib = load_library()
     p, keep = _run_params(noise, theta, gamma, chi, precision, seed, first_traj, svd_eps,
-                          theta_per_traj, gamma_per_traj)
+                          theta_per_traj, gamma_per_traj, svd_mode)
     if out is None:
         out = dict(records=np.zeros((n_traj, circuit.n_record_bits), dtype=np.uint8),
                    fail=np.zeros(n_traj, dtype=np.uint8),
@@ -191,9 +200,10 @@ def run_trajectories(circuit, n_traj, noise="srx", theta=0.0, gamma=0.0, chi=16,
 
 
 def logical_error_rate(circuit, shots, noise="srx", theta=0.0, gamma=0.0, chi=16,
-                       precision="fp64", seed=0, first_traj=0, svd_eps=0.0):
+                       precision="fp64", seed=0, first_traj=0, svd_eps=0.0, svd_mode="auto"):
     lib = load_library()
-    p, keep = _run_params(noise, theta, gamma, chi, precision, seed, first_traj, svd_eps)
+    p, keep = _run_params(noise, theta, gamma, chi, precision, seed, first_traj, svd_eps,
+                          svd_mode=svd_mode)
     pl, sg, nf = ctypes.c_double(), ctypes.c_double(), ctypes.c_uint64()
     _check(lib.ttn_logical_error_rate(circuit.handle, ctypes.byref(p), shots, ctypes.byref(pl),
                                       ctypes.byref(sg), ctypes.byref(nf)))
@@ -213,9 +223,10 @@ def decode(circuit, records):
 
 
 def debug_state(circuit, traj, layer, noise="srx", theta=0.0, gamma=0.0, chi=16,
-                precision="fp64", seed=0, svd_eps=0.0):
+                precision="fp64", seed=0, svd_eps=0.0, svd_mode="auto"):
     lib = load_library()
-    p, keep = _run_params(noise, theta, gamma, chi, precision, seed, 0, svd_eps)
+    p, keep = _run_params(noise, theta, gamma, chi, precision, seed, 0, svd_eps,
+                          svd_mode=svd_mode)
     amps = np.zeros(2 * (1 << circuit.n_qubits))
     _check(lib.ttn_debug_state(circuit.handle, ctypes.byref(p), traj, layer,
                                amps.ctypes.data_as(c_dblp)))
@@ -230,3 +241,24 @@ def philox_uniforms(seed, trajs, events):
     _check(lib.ttn_philox_uniforms(seed, t.ctypes.data_as(c_u64p), t.size,
                                    e.ctypes.data_as(c_i32p), e.size, out.ctypes.data_as(c_dblp)))
     return out
+
+
+KERNEL_CLASSES = ["svd_jacobi", "gram", "eig", "form_u", "absorb", "copy", "other"]
+
+
+def profile_begin(timed_class=-1):
+    """Starts the profiling ledger; launches of `timed_class` are timed."""
+    if isinstance(timed_class, str):
+        timed_class = KERNEL_CLASSES.index(timed_class)
+    _check(load_library().ttn_profile_begin(int(timed_class)))
+
+
+def profile_end():
+    ms, nl = ctypes.c_double(), ctypes.c_uint64()
+    fl = (ctypes.c_double * 7)()
+    by = (ctypes.c_double * 7)()
+    la = (ctypes.c_uint64 * 7)()
+    _check(load_library().ttn_profile_end(ctypes.byref(ms), ctypes.byref(nl), fl, by, la))
+    return dict(timed_ms=ms.value, timed_launches=nl.value,
+                flops=dict(zip(KERNEL_CLASSES, list(fl))), bytes=dict(zip(KERNEL_CLASSES, list(by))),
+                launches=dict(zip(KERNEL_CLASSES, list(la))))

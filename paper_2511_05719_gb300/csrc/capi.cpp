@@ -133,6 +133,7 @@ static ttn_status check_params(const ttn_circuit* c, const ttn_run_params* p) {
   if (p->chi < 1 || p->chi > 4096) return fail_with(TTN_EINVAL, "chi must be in [1, 4096]");
   if (!std::isfinite(p->theta)) return fail_with(TTN_EINVAL, "theta must be finite");
   if (!(p->gamma >= 0.0 && p->gamma <= 1.0)) return fail_with(TTN_EINVAL, "gamma must be in [0, 1]");
+  if (p->svd_mode < 0 || p->svd_mode > 2) return fail_with(TTN_EINVAL, "svd_mode must be 0, 1 or 2");
   return TTN_OK;
 }
 
@@ -150,6 +151,7 @@ static RunRequest make_request(const ttn_run_params* p, uint64_t n_traj, void* s
   rq.theta_per_traj = p->theta_per_traj;
   rq.gamma_per_traj = p->gamma_per_traj;
   rq.stream = stream;
+  rq.svd_mode = p->svd_mode;
   return rq;
 }
 
@@ -237,6 +239,30 @@ ttn_status ttn_debug_state(const ttn_circuit* c, const ttn_run_params* p, uint64
   if (p->gamma_per_traj) rq.gamma = p->gamma_per_traj[0];
   RunOutputs out;
   return run_trajectories_device(*c, rq, out);
+}
+
+ttn_status ttn_profile_begin(int32_t timed_class) {
+  if (timed_class < -1 || timed_class >= NCLASS) return fail_with(TTN_EINVAL, "unknown kernel class");
+  Profile& p = profile();
+  p = Profile();
+  p.active = true;
+  p.timed_class = timed_class;
+  return TTN_OK;
+}
+
+ttn_status ttn_profile_end(double* timed_ms, uint64_t* timed_launches, double* flops, double* bytes,
+                           uint64_t* launches) {
+  Profile& p = profile();
+  if (!p.active) return fail_with(TTN_EINVAL, "profiling was not started");
+  if (timed_ms) *timed_ms = p.ms;
+  if (timed_launches) *timed_launches = p.launches;
+  for (int c = 0; c < NCLASS; ++c) {
+    if (flops) flops[c] = p.flops[c];
+    if (bytes) bytes[c] = p.bytes[c];
+    if (launches) launches[c] = p.class_launches[c];
+  }
+  p.active = false;
+  return TTN_OK;
 }
 
 ttn_status ttn_philox_uniforms(uint64_t seed, const uint64_t* trajs, uint64_t n_traj,

@@ -97,6 +97,7 @@ struct Dev {
   int64_t wstride;
   cx<R>* V;              // [B][vstride] right singular vectors (column-major n x n)
   cx<R>* Rm;             // [B][vstride] factor absorbed by the neighbour (k x n)
+  cx<R>* G;              // [B][vstride] Gram matrix / V_k S_k^-1 (Gram path)
   int64_t vstride;
   double* sv;            // [B][nmax]
   int32_t* perm;         // [B][nmax]
@@ -116,6 +117,11 @@ struct Dev {
   uint64_t seed;
   int L, chi, noise;
   double eps, tie_eps, tol;
+  double eps_gram, tol_gram, tol_abs_gram;
+  int svd_mode;
+  unsigned long long* ledger;  // [2 * NCLASS] algorithmic flops, bytes (or null)
+  double* frob;          // [B] |M|_F^2 of the current Gram-path move
+  int32_t* trunc;        // [B] 1 if that move truncated
   int max_sweeps;
   int32_t* err;          // [B] error flags
 };
@@ -125,6 +131,13 @@ enum : int32_t { ERR_ZERO_NORM = 1, ERR_NO_CONVERGE = 2, ERR_CAPACITY = 4, ERR_N
 template <typename R>
 __device__ __forceinline__ cx<R>* node_ptr(const Dev<R>& d, int b, int v) {
   return d.T + (int64_t)b * d.tstride + d.off[v];
+}
+
+// Algorithmic work of one launch, added once per trajectory by its first block.
+__device__ __forceinline__ void ledger_add(unsigned long long* L, int cls, double flops, double bytes) {
+  if (!L) return;
+  atomicAdd(&L[2 * cls], (unsigned long long)flops);
+  atomicAdd(&L[2 * cls + 1], (unsigned long long)bytes);
 }
 
 // ------------------------------------------------------------------ init
@@ -190,6 +203,9 @@ __global__ void __launch_bounds__(256) k_svd_move(Dev<R> d, int v, int w, int ca
     return;
   }
 
+  if (tid == 0)
+    ledger_add(d.ledger, KC_SVD, 24.0 * m * (double)n * n + 44.0 * (double)n * n * n,
+               2.0 * sizeof(cx<R>) * m * (double)n);
   // gather M (column-major, m x n) and its squared Frobenius norm
   __shared__ double s_part[32];
   double fro_part = 0.0;
@@ -396,6 +412,9 @@ __global__ void __launch_bounds__(256) k_absorb(Dev<R> d, int w, int v) {
   const int J = outer * inner;
   const int i0 = blockIdx.y * 64, j0 = blockIdx.x * 64;
   if (k <= 0 || (int64_t)k * J > d.wstride || (int64_t)n * J > d.wstride) return;
+  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0)
+    ledger_add(d.ledger, KC_ABSORB, 8.0 * k * (double)n * J,
+               sizeof(cx<R>) * ((double)n * J + (double)k * n + (double)k * J));
   if (i0 >= k || j0 >= J) return;
   const cx<R>* Rm = d.Rm + (int64_t)b * d.vstride;
   const cx<R>* in = node_ptr(d, b, w);
@@ -457,11 +476,391 @@ __global__ void k_copy_back(Dev<R> d, int v) {
   const int* D = d.dims + b * d.ds;
   const int64_t cnt = (int64_t)D[2 * v] * D[2 * v + 1] * D[v];
   if (cnt > d.wstride) return;
+  if (blockIdx.x == 0 && threadIdx.x == 0) ledger_add(d.ledger, KC_COPY, 0.0, 2.0 * sizeof(cx<R>) * cnt);
   cx<R>* T = node_ptr(d, b, v);
   const cx<R>* W = d.W + (int64_t)b * d.wstride;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < cnt;
        i += (int64_t)gridDim.x * blockDim.x)
     T[i] = W[i];
+}
+
+// ------------------------------------------------------------------ Gram-path move
+// For large matrices the move factorises M through its Gram matrix:
+// G = M^H M (tiled GEMM), G = V L V^H by cyclic two-sided Jacobi (one CTA per
+// trajectory, the same rotation as the one-sided kernel), Y = M V_k (tiled
+// GEMM), s_c = |Y_c| exactly, U = Y S^-1, R = S V_k^H.  The reconstruction
+// M V_k V_k^H and the discarded weight are exact; the Gram matrix only limits
+// the orthogonality of U (to about eps s_max / s_c) and the choice of the kept
+// space among directions with eigenvalues below eps_gram^2 lambda_max.
+template <typename R>
+__device__ __forceinline__ int m_addr(int leg, int i, int j, int m, int dr, int du) {
+  if (leg == 2) return i * du + j;
+  if (leg == 0) return j * m + i;
+  int l = i / du, u = i - l * du;
+  return (l * dr + j) * du + u;
+}
+
+// 64 x 64 output tile of C = A B (complex), K-loop in chunks of 16.
+// fa(i, k), fb(k, j) load operands; fc(i, j, v) stores.  A_KFAST: the A
+// loader walks k fastest (contiguous when A is row-major).
+template <typename R, bool A_KFAST, typename FA, typename FB, typename FC>
+__device__ __forceinline__ void tile_gemm64(int Mr, int Nc, int K, int i0, int j0, FA fa, FB fb,
+                                            FC fc) {
+  __shared__ cx<R> As[16][64];
+  __shared__ cx<R> Bs[16][64];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  cx<R> acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[a][c] = {R(0), R(0)};
+  for (int k0 = 0; k0 < K; k0 += 16) {
+    for (int e = threadIdx.x; e < 16 * 64; e += 256) {
+      int kk, ii;
+      if (A_KFAST) {
+        kk = e & 15;
+        ii = e >> 4;
+      } else {
+        kk = e >> 6;
+        ii = e & 63;
+      }
+      const int i = i0 + ii, k = k0 + kk;
+      As[kk][ii] = (i < Mr && k < K) ? fa(i, k) : cx<R>{R(0), R(0)};
+      const int kb = e >> 6, jb = e & 63;
+      const int j = j0 + jb, k2 = k0 + kb;
+      Bs[kb][jb] = (j < Nc && k2 < K) ? fb(k2, j) : cx<R>{R(0), R(0)};
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) {
+      cx<R> av[4], bv[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) av[a] = As[kk][ty * 4 + a];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) bv[c] = Bs[kk][tx * 4 + c];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[a][c] = cadd(acc[a][c], cmul(av[a], bv[c]));
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const int i = i0 + ty * 4 + a;
+    if (i >= Mr) continue;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int j = j0 + tx * 4 + c;
+      if (j < Nc) fc(i, j, acc[a][c]);
+    }
+  }
+}
+
+// M (m x n, row-major) into the workspace.
+template <typename R>
+__global__ void k_gather_rows(Dev<R> d, int v, int w) {
+  const int b = blockIdx.y;
+  const int* D = d.dims + b * d.ds;
+  const int dl = D[2 * v], dr = D[2 * v + 1], du = D[v];
+  const int leg = (w == 2 * v) ? 0 : ((w == 2 * v + 1) ? 1 : 2);
+  const int n = leg == 0 ? dl : (leg == 1 ? dr : du);
+  const int m = dl * dr * du / n;
+  if ((int64_t)m * n > d.wstride) return;
+  const cx<R>* T = node_ptr(d, b, v);
+  cx<R>* W = d.W + (int64_t)b * d.wstride;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < m * n; idx += gridDim.x * blockDim.x) {
+    int i = idx / n, j = idx - i * n;
+    W[idx] = T[m_addr<R>(leg, i, j, m, dr, du)];
+  }
+}
+
+// G = M^H M (n x n)
+template <typename R>
+__global__ void __launch_bounds__(256) k_gram(Dev<R> d, int v, int w) {
+  const int b = blockIdx.z;
+  const int* D = d.dims + b * d.ds;
+  const int dl = D[2 * v], dr = D[2 * v + 1], du = D[v];
+  const int leg = (w == 2 * v) ? 0 : ((w == 2 * v + 1) ? 1 : 2);
+  const int n = leg == 0 ? dl : (leg == 1 ? dr : du);
+  const int m = dl * dr * du / n;
+  if ((int64_t)n * n > d.vstride || (int64_t)m * n > d.wstride) return;
+  const int i0 = blockIdx.y * 64, j0 = blockIdx.x * 64;
+  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0)
+    ledger_add(d.ledger, KC_GRAM, 8.0 * m * (double)n * n,
+               sizeof(cx<R>) * ((double)m * n + (double)n * n));
+  if (i0 >= n || j0 >= n) return;
+  const cx<R>* Mw = d.W + (int64_t)b * d.wstride;
+  cx<R>* G = d.G + (int64_t)b * d.vstride;
+  tile_gemm64<R, false>(
+      n, n, m, i0, j0,
+      [&](int i, int k) {
+        cx<R> x = Mw[(int64_t)k * n + i];
+        return cx<R>{x.x, -x.y};
+      },
+      [&](int k, int j) { return Mw[(int64_t)k * n + j]; },
+      [&](int i, int j, cx<R> val) { G[(int64_t)i * n + j] = val; });
+}
+
+// Eigen-decomposition of G by cyclic two-sided Jacobi; then the kept rank,
+// V_k S_k^-1 (into G) and R = S_k V_k^H (into Rm).
+template <typename R>
+__global__ void __launch_bounds__(512) k_eig(Dev<R> d, int v, int w, int capped) {
+  const int b = blockIdx.x;
+  const int tid = threadIdx.x, nth = blockDim.x;
+  int* D = d.dims + b * d.ds;
+  const int dl = D[2 * v], dr = D[2 * v + 1], du = D[v];
+  const int leg = (w == 2 * v) ? 0 : ((w == 2 * v + 1) ? 1 : 2);
+  const int n = leg == 0 ? dl : (leg == 1 ? dr : du);
+  cx<R>* G = d.G + (int64_t)b * d.vstride;
+  cx<R>* V = d.V + (int64_t)b * d.vstride;
+  double* sv = d.sv + (int64_t)b * d.nmax;
+  int32_t* perm = d.perm + (int64_t)b * d.nmax;
+  __shared__ R pc[256], ps[256];
+  __shared__ cx<R> pe[256];
+  __shared__ int pp[256], pq[256];
+  __shared__ int s_k;
+  __shared__ double s_scale, s_tr;
+  if ((int64_t)n * n > d.vstride || n > d.nmax || n > 512) {
+    if (tid == 0) {
+      atomicOr(&d.err[b], ERR_CAPACITY);
+      d.knew[b] = 0;
+    }
+    return;
+  }
+  for (int idx = tid; idx < n * n; idx += nth) {
+    int x = idx / n, j = idx - x * n;
+    V[idx] = {R(x == j), R(0)};
+  }
+  if (tid == 0) ledger_add(d.ledger, KC_EIG, 36.0 * (double)n * n * n, 3.0 * sizeof(cx<R>) * n * (double)n);
+  if (tid == 0) {
+    double tr = 0.0;
+    for (int j = 0; j < n; ++j) tr += (double)G[(int64_t)j * n + j].x;
+    s_tr = tr;
+  }
+  __syncthreads();
+  const R skip2 = (R)(d.eps_gram * d.eps_gram * s_tr / (double)n);
+  const R tol = (R)d.tol_gram;
+  const R tol_abs = (R)(d.tol_abs_gram * s_tr);  // below rounding of G
+  if (n > 1) {
+    const int ne = n + (n & 1), M1 = ne - 1, np2 = ne / 2;
+    int sweep = 0;
+    for (; sweep < d.max_sweeps; ++sweep) {
+      int rotated = 0;
+      for (int s = 0; s < M1; ++s) {
+        for (int pr = tid; pr < np2; pr += nth) {
+          int p, q;
+          if (pr == 0) {
+            p = 0;
+            q = (s % M1) + 1;
+          } else {
+            p = ((pr + s) % M1) + 1;
+            q = ((M1 - pr + s) % M1) + 1;
+          }
+          pp[pr] = -1;
+          if (p >= n || q >= n) continue;
+          const R a = G[(int64_t)p * n + p].x, bb = G[(int64_t)q * n + q].x;
+          const cx<R> g = G[(int64_t)p * n + q];
+          if (!(a > skip2) || !(bb > skip2)) continue;
+          const R gm = fmax(fabs(g.x), fabs(g.y));
+          if (gm == R(0)) continue;
+          const R grs = g.x / gm, gis = g.y / gm, hs = sqrt(grs * grs + gis * gis), ga = gm * hs;
+          if (!(ga > tol * sqrt(a) * sqrt(bb)) || !(ga > tol_abs)) continue;
+          rotated = 1;
+          const R zeta = (bb - a) / (R(2) * ga);
+          const R t = (zeta >= R(0) ? R(1) : R(-1)) / (fabs(zeta) + sqrt(R(1) + zeta * zeta));
+          const R c = R(1) / sqrt(R(1) + t * t);
+          pp[pr] = p;
+          pq[pr] = q;
+          pc[pr] = c;
+          ps[pr] = c * t;
+          pe[pr] = {grs / hs, -gis / hs};
+        }
+        __syncthreads();
+        // rows: G <- J^H G, J = [[c, s], [-s e, c e]], e = pe
+        for (int idx = tid; idx < np2 * n; idx += nth) {
+          const int pr = idx / n, col = idx - pr * n;
+          const int p = pp[pr];
+          if (p < 0) continue;
+          const int q = pq[pr];
+          const R c = pc[pr], sn = ps[pr];
+          const cx<R> e = pe[pr];
+          const cx<R> gp = G[(int64_t)p * n + col], gq = G[(int64_t)q * n + col];
+          // conj(Jqp) = -s conj(e), conj(Jqq) = c conj(e)
+          const cx<R> ceq = cmulc(e, gq);  // conj(e) * gq
+          G[(int64_t)p * n + col] = {c * gp.x - sn * ceq.x, c * gp.y - sn * ceq.y};
+          G[(int64_t)q * n + col] = {sn * gp.x + c * ceq.x, sn * gp.y + c * ceq.y};
+        }
+        __syncthreads();
+        // columns: G <- G J, V <- V J
+        for (int idx = tid; idx < np2 * n; idx += nth) {
+          const int pr = idx / n, row = idx - pr * n;
+          const int p = pp[pr];
+          if (p < 0) continue;
+          const int q = pq[pr];
+          const R c = pc[pr], sn = ps[pr];
+          const cx<R> e = pe[pr];
+          {
+            const cx<R> gp = G[(int64_t)row * n + p], gq = cmul(e, G[(int64_t)row * n + q]);
+            G[(int64_t)row * n + p] = {c * gp.x - sn * gq.x, c * gp.y - sn * gq.y};
+            G[(int64_t)row * n + q] = {sn * gp.x + c * gq.x, sn * gp.y + c * gq.y};
+          }
+          {
+            const cx<R> vp = V[(int64_t)row * n + p], vq = cmul(e, V[(int64_t)row * n + q]);
+            V[(int64_t)row * n + p] = {c * vp.x - sn * vq.x, c * vp.y - sn * vq.y};
+            V[(int64_t)row * n + q] = {sn * vp.x + c * vq.x, sn * vp.y + c * vq.y};
+          }
+        }
+        __syncthreads();
+      }
+      if (!__syncthreads_or(rotated)) break;
+    }
+    if (sweep == d.max_sweeps && tid == 0) atomicOr(&d.err[b], ERR_NO_CONVERGE);
+  }
+  for (int j = tid; j < n; j += nth) {
+    double lam = (double)G[(int64_t)j * n + j].x;
+    double sj = lam > 0.0 ? sqrt(lam) : 0.0;
+    if (!(sj < 1e300)) {
+      atomicOr(&d.err[b], ERR_NAN);
+      sj = 0.0;
+    }
+    sv[j] = sj;
+  }
+  __syncthreads();
+  for (int j = tid; j < n; j += nth) {
+    double sj = sv[j];
+    int r = 0;
+    for (int i = 0; i < n; ++i) {
+      double si = sv[i];
+      r += (si > sj) || (si == sj && i < j);
+    }
+    perm[r] = j;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double smax = sv[perm[0]];
+    int k = 0;
+    for (int i = 0; i < n; ++i)
+      if (sv[perm[i]] > d.eps_gram * smax) ++k;
+    if (k < 1) k = 1;
+    if (smax == 0.0) atomicOr(&d.err[b], ERR_ZERO_NORM);
+    int trunc = 0;
+    if (capped && k > d.chi) {
+      k = d.chi;
+      trunc = 1;
+    }
+    s_k = k;
+    const int bond = (w == v / 2) ? v : w;
+    D[bond] = k;
+    d.knew[b] = k;
+    d.nold[b] = n;
+    d.frob[b] = s_tr;
+    d.trunc[b] = trunc;
+  }
+  __syncthreads();
+  const int k = s_k;
+  // V_k (n x k, row-major, columns in descending eigenvalue order) into G
+  for (int idx = tid; idx < n * k; idx += nth) {
+    const int x = idx / k, c = idx - x * k;
+    G[idx] = V[(int64_t)x * n + perm[c]];
+  }
+}
+
+// Exact singular values of the kept columns: Y = M V_k was written into T_v;
+// s_c = |Y_c|, U_c = Y_c / s_c, R_c = s_c V_c^H (renormalised after a
+// truncation, the discarded weight 1 - sum s_c^2 / |M|_F^2 recorded).
+template <typename R>
+__global__ void __launch_bounds__(256) k_unorm(Dev<R> d, int v, int w) {
+  const int b = blockIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+  const int* D = d.dims + b * d.ds;
+  const int leg = (w == 2 * v) ? 0 : ((w == 2 * v + 1) ? 1 : 2);
+  const int n = d.nold[b], k = d.knew[b];
+  if (k <= 0) return;
+  const int dl0 = D[2 * v], dr0 = D[2 * v + 1], du0 = D[v];
+  const int dl = leg == 0 ? n : dl0, dr = leg == 1 ? n : dr0, du = leg == 2 ? n : du0;
+  const int m = dl * dr * du / n;
+  cx<R>* T = node_ptr(d, b, v);
+  double* sv = d.sv + (int64_t)b * d.nmax;
+  __shared__ double s_scale;
+  auto addr = [&](int i, int c) {
+    if (leg == 2) return i * k + c;
+    if (leg == 0) return c * m + i;
+    int l = i / du, u = i - l * du;
+    return (l * k + c) * du + u;
+  };
+  for (int c = warp; c < k; c += nwarps) {
+    double acc = 0.0;
+    for (int i = lane; i < m; i += 32) acc += (double)cabs2(T[addr(i, c)]);
+    acc = warp_sum(acc);
+    if (lane == 0) sv[c] = sqrt(acc);
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double kept = 0.0;
+    for (int c = 0; c < k; ++c) kept += sv[c] * sv[c];
+    const double fro2 = d.frob[b];
+    double scale = 1.0;
+    if (d.trunc[b] && fro2 > 0.0 && kept > 0.0) {
+      const double dsc = fmax(0.0, 1.0 - kept / fro2);
+      d.disc[b] += dsc;
+      scale = sqrt(fro2 / kept);
+    }
+    if (!(kept > 0.0)) atomicOr(&d.err[b], ERR_ZERO_NORM);
+    s_scale = scale;
+  }
+  __syncthreads();
+  for (int idx = tid; idx < m * k; idx += blockDim.x) {
+    const int c = idx / m, i = idx - c * m;
+    const double s = sv[c];
+    const int a = addr(i, c);
+    T[a] = cscale(T[a], s > 0.0 ? (R)(1.0 / s) : R(0));
+  }
+  const cx<R>* Vk = d.G + (int64_t)b * d.vstride;
+  cx<R>* Rm = d.Rm + (int64_t)b * d.vstride;
+  const R sc = (R)s_scale;
+  for (int idx = tid; idx < k * n; idx += blockDim.x) {
+    const int c = idx / n, x = idx - c * n;
+    const cx<R> vv = Vk[(int64_t)x * k + c];
+    const R s = (R)sv[c] * sc;
+    Rm[idx] = {s * vv.x, -s * vv.y};
+  }
+}
+
+// Y = M V_k: m x k, written into T_v with bond dimension k.
+template <typename R>
+__global__ void __launch_bounds__(256) k_form_u(Dev<R> d, int v, int w) {
+  const int b = blockIdx.z;
+  const int* D = d.dims + b * d.ds;
+  const int leg = (w == 2 * v) ? 0 : ((w == 2 * v + 1) ? 1 : 2);
+  // dims already hold k on the bond; n is the previous dimension
+  const int n = d.nold[b], k = d.knew[b];
+  if (k <= 0) return;
+  const int dl0 = D[2 * v], dr0 = D[2 * v + 1], du0 = D[v];
+  const int dl = leg == 0 ? n : dl0, dr = leg == 1 ? n : dr0, du = leg == 2 ? n : du0;
+  const int m = dl * dr * du / n;
+  if ((int64_t)m * n > d.wstride) return;
+  const int i0 = blockIdx.x * 64, j0 = blockIdx.y * 64;
+  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0)
+    ledger_add(d.ledger, KC_FORMU, 8.0 * m * (double)n * k,
+               sizeof(cx<R>) * ((double)m * n + (double)n * k + (double)m * k));
+  if (i0 >= m || j0 >= k) return;
+  const cx<R>* Mw = d.W + (int64_t)b * d.wstride;
+  const cx<R>* Vs = d.G + (int64_t)b * d.vstride;  // V_k
+  cx<R>* T = node_ptr(d, b, v);
+  tile_gemm64<R, true>(
+      m, k, n, i0, j0, [&](int i, int kk) { return Mw[(int64_t)i * n + kk]; },
+      [&](int kk, int j) { return Vs[(int64_t)kk * k + j]; },
+      [&](int i, int c, cx<R> val) {
+        int dst;
+        if (leg == 2) dst = i * k + c;
+        else if (leg == 0) dst = c * m + i;
+        else {
+          int l = i / du, u = i - l * du;
+          dst = (l * k + c) * du + u;
+        }
+        T[dst] = val;
+      });
 }
 
 // ------------------------------------------------------------------ MPO threading
@@ -824,6 +1223,11 @@ __global__ void k_amplitudes(Dev<R> d, int b, const int32_t* qubit_of_leaf, int 
 
 static inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 
+Profile& profile() {
+  static Profile p;
+  return p;
+}
+
 ttn_status philox_uniforms_device(uint64_t seed, const uint64_t* trajs, uint64_t n_traj,
                                   const int32_t* events, int32_t n_events, double* out) {
   uint64_t* dt = nullptr;
@@ -880,6 +1284,7 @@ struct Engine {
   cx<R>* dW = nullptr;
   cx<R>* dV = nullptr;
   cx<R>* dR = nullptr;
+  cx<R>* dG = nullptr;
   int64_t* dOff = nullptr;
   int32_t* dDims = nullptr;
   double* dSv = nullptr;
@@ -895,10 +1300,58 @@ struct Engine {
   double* dGamma = nullptr;
   uint64_t* dTraj = nullptr;
   int32_t* dErr = nullptr;
+  double* dFrob = nullptr;
+  int32_t* dTrunc = nullptr;
   int32_t* dLeafdim = nullptr;
   Op1* dOp1 = nullptr;
   Group1* dGroups = nullptr;
+  unsigned long long* dLedger = nullptr;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> events;
+  uint64_t class_launches[NCLASS] = {0};
   Dev<R> dev{};
+
+  // Launch wrapper: counts launches per class and, when profiling that
+  // class, brackets the launch with events on the launch stream.
+  template <typename F>
+  void timed(int cls, F&& fn) {
+    Profile& pf = profile();
+    class_launches[cls]++;
+    if (pf.active && pf.timed_class == cls) {
+      cudaEvent_t a, b;
+      cudaEventCreate(&a);
+      cudaEventCreate(&b);
+      cudaEventRecord(a, st);
+      fn();
+      cudaEventRecord(b, st);
+      events.push_back({a, b});
+    } else {
+      fn();
+    }
+  }
+
+  void collect_profile() {
+    Profile& pf = profile();
+    if (!pf.active) return;
+    for (auto& e : events) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, e.first, e.second) == cudaSuccess) pf.ms += ms;
+      pf.launches++;
+      cudaEventDestroy(e.first);
+      cudaEventDestroy(e.second);
+    }
+    events.clear();
+    unsigned long long h[2 * NCLASS] = {0};
+    if (dLedger && cudaMemcpy(h, dLedger, sizeof(h), cudaMemcpyDeviceToHost) == cudaSuccess)
+      for (int c = 0; c < NCLASS; ++c) {
+        pf.flops[c] += (double)h[2 * c];
+        pf.bytes[c] += (double)h[2 * c + 1];
+      }
+    for (int c = 0; c < NCLASS; ++c) {
+      pf.class_launches[c] += class_launches[c];
+      class_launches[c] = 0;
+    }
+    if (dLedger) cudaMemset(dLedger, 0, sizeof(h));
+  }
 
   Engine(const ttn_circuit& cc, const Program& p, int chi_, int noise_, cudaStream_t s)
       : c(cc), prog(p), chi(chi_), noise(noise_), B(0), st(s) {
@@ -924,7 +1377,7 @@ struct Engine {
   }
 
   size_t bytes_per_traj() const {
-    return sizeof(cx<R>) * (size_t)(tstride + wstride + 2 * vstride) +
+    return sizeof(cx<R>) * (size_t)(tstride + wstride + 3 * vstride) +
            sizeof(int32_t) * (2 * c.L + 2 * nmax + 4) + sizeof(double) * (nmax + 5) + c.n_rec + c.N +
            64;
   }
@@ -935,6 +1388,7 @@ struct Engine {
     CK(cudaMalloc(&dW, sizeof(cx<R>) * (size_t)wstride * B));
     CK(cudaMalloc(&dV, sizeof(cx<R>) * (size_t)vstride * B));
     CK(cudaMalloc(&dR, sizeof(cx<R>) * (size_t)vstride * B));
+    CK(cudaMalloc(&dG, sizeof(cx<R>) * (size_t)vstride * B));
     CK(cudaMalloc(&dOff, sizeof(int64_t) * c.L));
     CK(cudaMalloc(&dDims, sizeof(int32_t) * 2 * c.L * B));
     CK(cudaMalloc(&dSv, sizeof(double) * nmax * B));
@@ -950,6 +1404,12 @@ struct Engine {
     CK(cudaMalloc(&dGamma, sizeof(double) * B));
     CK(cudaMalloc(&dTraj, sizeof(uint64_t) * B));
     CK(cudaMalloc(&dErr, sizeof(int32_t) * B));
+    CK(cudaMalloc(&dFrob, sizeof(double) * B));
+    CK(cudaMalloc(&dTrunc, sizeof(int32_t) * B));
+    if (profile().active) {
+      CK(cudaMalloc(&dLedger, sizeof(unsigned long long) * 2 * NCLASS));
+      CK(cudaMemset(dLedger, 0, sizeof(unsigned long long) * 2 * NCLASS));
+    }
     CK(cudaMalloc(&dLeafdim, sizeof(int32_t) * c.L));
     CK(cudaMalloc(&dOp1, sizeof(Op1) * std::max<size_t>(1, prog.op1.size())));
     CK(cudaMalloc(&dGroups, sizeof(Group1) * std::max<size_t>(1, prog.groups.size())));
@@ -971,6 +1431,7 @@ struct Engine {
     dev.wstride = wstride;
     dev.V = dV;
     dev.Rm = dR;
+    dev.G = dG;
     dev.vstride = vstride;
     dev.sv = dSv;
     dev.perm = dPerm;
@@ -991,12 +1452,16 @@ struct Engine {
     dev.chi = chi;
     dev.noise = noise;
     dev.err = dErr;
+    dev.frob = dFrob;
+    dev.trunc = dTrunc;
+    dev.ledger = dLedger;
     return TTN_OK;
   }
 
   void release() {
-    void* ptrs[] = {dT, dW, dV, dR, dOff, dDims, dSv, dPerm, dK, dN, dLogp, dDisc, dTies, dRec,
-                    dLast, dTheta, dGamma, dTraj, dErr, dLeafdim, dOp1, dGroups};
+    void* ptrs[] = {dT, dW, dV, dR, dG, dOff, dDims, dSv, dPerm, dK, dN, dLogp, dDisc, dTies, dRec,
+                    dLast, dTheta, dGamma, dTraj, dErr, dFrob, dTrunc, dLeafdim, dOp1, dGroups,
+                    dLedger};
     for (void* p : ptrs)
       if (p) cudaFree(p);
   }
@@ -1014,7 +1479,25 @@ struct Engine {
       switch (s.kind) {
         case S_MOVE: {
           const int v = s.a, w = s.b;
-          k_svd_move<R><<<nb, 256, 0, st>>>(dev, v, w, s.c);
+          const int bond = (w == v / 2) ? v : w;
+          const int64_t nmv = 2 * (int64_t)bcap[bond];
+          const bool gram = dev.svd_mode == 2 || (dev.svd_mode == 0 && sizeof(R) == 4 && nmv > 64);
+          if (gram) {
+            const int lv = (w == 2 * v) ? 0 : ((w == 2 * v + 1) ? 1 : 2);
+            int64_t c3[3] = {2 * (int64_t)bcap[2 * v], 2 * (int64_t)bcap[2 * v + 1],
+                             v == 1 ? 1 : 2 * (int64_t)bcap[v]};
+            int64_t mmax = 1;
+            for (int t = 0; t < 3; ++t)
+              if (t != lv) mmax *= c3[t];
+            timed(KC_COPY, [&] { k_gather_rows<R><<<dim3(std::max(1, ceil_div(ncap[v], 1024)), nb), 256, 0, st>>>(dev, v, w); });
+            const int tn = std::max(1, ceil_div(nmv, 64));
+            timed(KC_GRAM, [&] { k_gram<R><<<dim3(tn, tn, nb), 256, 0, st>>>(dev, v, w); });
+            timed(KC_EIG, [&] { k_eig<R><<<nb, 512, 0, st>>>(dev, v, w, s.c); });
+            timed(KC_FORMU, [&] { k_form_u<R><<<dim3(std::max(1, ceil_div(mmax, 64)), tn, nb), 256, 0, st>>>(dev, v, w); });
+            timed(KC_OTHER, [&] { k_unorm<R><<<nb, 256, 0, st>>>(dev, v, w); });
+          } else {
+            timed(KC_SVD, [&] { k_svd_move<R><<<nb, 256, 0, st>>>(dev, v, w, s.c); });
+          }
           // neighbour absorbs R: grid from capacities
           const int lw = (v == 2 * w) ? 0 : ((v == 2 * w + 1) ? 1 : 2);
           int64_t cl = 2 * (int64_t)bcap[2 * w], cr = 2 * (int64_t)bcap[2 * w + 1],
@@ -1023,8 +1506,8 @@ struct Engine {
           int64_t Jmax = ncap[w] * 2 / std::max<int64_t>(1, kmax);
           Jmax = std::min<int64_t>(Jmax, (lw == 0 ? cr * cu : (lw == 1 ? cl * cu : cl * cr)));
           dim3 ga(std::max(1, ceil_div(Jmax, 64)), std::max(1, ceil_div(kmax, 64)), nb);
-          k_absorb<R><<<ga, 256, 0, st>>>(dev, w, v);
-          k_copy_back<R><<<dim3(std::max(1, ceil_div(ncap[w], 256 * 4)), nb), 256, 0, st>>>(dev, w);
+          timed(KC_ABSORB, [&] { k_absorb<R><<<ga, 256, 0, st>>>(dev, w, v); });
+          timed(KC_COPY, [&] { k_copy_back<R><<<dim3(std::max(1, ceil_div(ncap[w], 256 * 4)), nb), 256, 0, st>>>(dev, w); });
           break;
         }
         case S_THREAD_LEAF: {
@@ -1082,6 +1565,10 @@ static ttn_status run_impl(const ttn_circuit& c, const RunRequest& rq, RunOutput
   eng.dev.tie_eps = sizeof(R) == 8 ? 1e-9 : 1e-5;
   eng.dev.tol = sizeof(R) == 8 ? 1e-15 : 1e-7;
   eng.dev.max_sweeps = sizeof(R) == 8 ? 40 : 30;
+  eng.dev.svd_mode = rq.svd_mode;
+  eng.dev.eps_gram = sizeof(R) == 8 ? 1e-7 : 1e-4;
+  eng.dev.tol_gram = sizeof(R) == 8 ? 1e-13 : 3e-6;
+  eng.dev.tol_abs_gram = sizeof(R) == 8 ? 1e-15 : 2e-7;
   size_t freeb = 0, totb = 0;
   CK(cudaMemGetInfo(&freeb, &totb));
   const size_t per = eng.bytes_per_traj();
@@ -1159,6 +1646,7 @@ static ttn_status run_impl(const ttn_circuit& c, const RunRequest& rq, RunOutput
       cudaFree(da);
     }
     CK(cudaStreamSynchronize(st));
+    eng.collect_profile();
     for (int i = 0; i < nb; ++i) out.err_flags |= err[i];
     if (out.err_flags & (ERR_CAPACITY | ERR_ZERO_NORM | ERR_NAN)) {
       eng.release();

@@ -19,6 +19,7 @@ struct RunRequest {
   void* stream = nullptr;
   size_t max_device_bytes = 0;   // 0: 80% of free device memory
   int max_batch = 0;             // 0: as many as fit
+  int svd_mode = 0;              // 0 auto, 1 one-sided Jacobi on M, 2 Gram matrix
 };
 
 struct RunOutputs {
@@ -34,6 +35,24 @@ struct RunOutputs {
   size_t bytes_per_traj = 0;
   int decode_overflow = 0;
 };
+
+// Kernel classes of the profiling ledger.
+enum KernelClass { KC_SVD = 0, KC_GRAM = 1, KC_EIG = 2, KC_FORMU = 3, KC_ABSORB = 4, KC_COPY = 5,
+                   KC_OTHER = 6, NCLASS = 7 };
+
+// Process-wide profiling state: while active, every run adds algorithmic
+// flops/bytes per class to `ledger`, and launches of class `timed_class` are
+// bracketed by CUDA events whose elapsed times accumulate in `ms`.
+struct Profile {
+  bool active = false;
+  int timed_class = -1;
+  double ms = 0.0;
+  uint64_t launches = 0;
+  double flops[NCLASS] = {0};
+  double bytes[NCLASS] = {0};
+  uint64_t class_launches[NCLASS] = {0};
+};
+Profile& profile();
 
 ttn_status run_trajectories_device(const ttn_circuit& c, const RunRequest& rq, RunOutputs& out);
 

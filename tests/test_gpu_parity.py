@@ -156,3 +156,41 @@ def test_batching_does_not_change_results():
                             first_traj=17, precision="fp64")
     assert np.array_equal(a["records"], np.vstack([b1["records"], b2["records"]]))
     assert np.allclose(a["log_prob"], np.concatenate([b1["log_prob"], b2["log_prob"]]), atol=1e-12)
+
+
+# Gram-matrix path (large bonds): the kept space is chosen from eigenvalues of
+# M^H M above eps_gram^2 lambda_max (FP64 1e-7, FP32 1e-4 in singular values),
+# so each move may drop a component of relative amplitude up to eps_gram; the
+# snapshots below are a few tens of moves apart.  Tolerances: FP64 1e-5,
+# FP32 3e-3 (2-norm, relative).
+GRAM_TOL = {"fp64": 1e-5, "fp32": 3e-3}
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("noise", ["srx", "ad", "srx_ad"])
+def test_gram_path_amplitudes(noise, precision):
+    circ = build_circuit(3, 2)
+    th, ga = STRENGTH[noise]
+    c = P.Circuit(3, 2, layout="optimized")
+    for traj in (1, 4):
+        layers = [4, 13, 20, circ.n_layers - 1]
+        ref = SV.run_trajectory(circ, MODELS[noise], th, ga, W.BASE_SEED, traj, snapshot_layers=layers)
+        if ref["margin"] < 1e-3:
+            continue
+        for L in layers:
+            amp = P.debug_state(c, traj, L, noise=noise, theta=th, gamma=ga, chi=64,
+                                precision=precision, seed=W.BASE_SEED, svd_mode="gram")
+            want = ref["states"][L]
+            err = np.linalg.norm(amp - want) / np.linalg.norm(want)
+            assert err < GRAM_TOL[precision], (noise, traj, L, err)
+
+
+def test_profile_ledger_counts_work():
+    c = P.Circuit(3, 1)
+    P.profile_begin("svd_jacobi")
+    P.run_trajectories(c, 8, noise="srx", theta=0.05, chi=64, precision="fp64", seed=1,
+                       svd_mode="jacobi")
+    prof = P.profile_end()
+    assert prof["timed_launches"] > 0 and prof["timed_ms"] > 0
+    assert prof["flops"]["svd_jacobi"] > 0 and prof["flops"]["absorb"] > 0
+    assert prof["flops"]["gram"] == 0
