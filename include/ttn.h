@@ -78,7 +78,7 @@ typedef struct {
   uint64_t first_traj;           /* index of the first trajectory        */
   double svd_eps;                /* singular values <= svd_eps * s_max are
                                     dropped; <= 0 selects 1e-13 (FP64) or
-                                    3e-7 (FP32)                           */
+                                    5e-7 (FP32)                           */
   const double* theta_per_traj;  /* optional [n_traj], overrides theta    */
   const double* gamma_per_traj;  /* optional [n_traj], overrides gamma    */
   int32_t svd_mode;              /* factorisation of a centre move:
@@ -130,6 +130,19 @@ ttn_status ttn_run_trajectories(const ttn_circuit* circuit, const ttn_run_params
  * binomial standard error sigma = sqrt(p (1-p) / shots).  Host outputs. */
 ttn_status ttn_logical_error_rate(const ttn_circuit* circuit, const ttn_run_params* params,
                                   uint64_t shots, double* p_L, double* sigma, uint64_t* n_fail);
+
+/* Gradient of p_L by the score-function estimator (the paper has no
+ * gradient; this extends its Monte Carlo step, App. A.3):
+ *   dp_L/dx = E[ fail * d/dx log p(trajectory; x) ],  x = theta (wrt 0) or
+ * gamma (wrt 1).  Each trajectory is run once, then replayed twice with all its
+ * sampled choices (measurement outcomes, damping branches, Pauli draws)
+ * forced, at x + h and x - h; the score is the central difference of the
+ * replayed log-probabilities (h <= 0 selects 1e-4).  Outputs (host): p_L,
+ * dpL, its standard error dpL_sigma, and optionally the per-shot score
+ * [shots].  EINVAL when the model does not depend on x. */
+ttn_status ttn_grad(const ttn_circuit* circuit, const ttn_run_params* params, uint64_t shots,
+                    int32_t wrt, double h, double* p_L, double* dpL, double* dpL_sigma,
+                    double* score);
 
 /* Decodes n records ([n][n_record_bits] u8) with the concatenated MWPM
  * decoder (App. A.2) on the device.  fail [n] u8, color [n] int32 (winning

@@ -39,10 +39,14 @@ finds the same one.  Paths: the canonical shortest path from the smaller
 node id to the larger walks, at each step, to the smallest-id neighbour that
 stays on a shortest path (distances compared as (weight, hops)).
 
-MWPM here is an exact subset dynamic programme (defects <= 22).
+MWPM here is exact: the optimum splits over connected components of the
+pairs cheaper than sending both defects to the boundary; each component is
+solved by a subset dynamic programme (<= 14 defects) or by networkx's
+weighted blossom with integer weights (a library routine as one step).
 
 Pinned (tests/test_oracle_decoder.py): DP matching == brute-force enumeration
-of perfect matchings; every code-capacity X error of weight <= (d-1)/2
+of perfect matchings; the component split equals the undecomposed DP and
+the blossom; every code-capacity X error of weight <= (d-1)/2
 decodes without a logical flip (d = 3, 5, 7); noise-free records decode to no
 flip.  Parity against the paper's own decoder is unpinned (its definition is
 not in the paper).
@@ -162,7 +166,8 @@ def mwpm_dp(defects, wpair, wbound):
     """Exact minimum-weight matching of `defects` (sorted ids); each defect is
     paired with another or with the boundary.  wpair(i, j), wbound(i) are
     perturbed integer weights or None when unreachable.  Returns list of
-    (i, j) index pairs, j = -1 for the boundary, and the total weight."""
+    (i, j) index pairs, j = -1 for the boundary, and the total weight.
+    Subset dynamic programme (small instances)."""
     k = len(defects)
     if k > MAX_DP_DEFECTS:
         raise ValueError("too many defects for the DP oracle: %d" % k)
@@ -199,6 +204,88 @@ def mwpm_dp(defects, wpair, wbound):
     if tot == INF:
         raise ValueError("no perfect matching")
     return list(pairs), tot
+
+
+def mwpm_blossom(k, wpair, wbound):
+    """Exact minimum-weight matching with boundary through networkx's
+    weighted blossom on the graph of defects and boundary copies (integer
+    weights, so the library's dual updates stay exact)."""
+    import networkx as nx
+    G = nx.Graph()
+    maxw = 0
+    edges = []
+    for i in range(k):
+        wb = wbound(i)
+        if wb is not None:
+            edges.append((("d", i), ("b", i), wb))
+        for j in range(i + 1, k):
+            w = wpair(i, j)
+            if w is not None:
+                edges.append((("d", i), ("d", j), w))
+            edges.append((("b", i), ("b", j), 0))
+    for (_, _, w) in edges:
+        maxw = max(maxw, w)
+    for (a, b, w) in edges:
+        G.add_edge(a, b, weight=maxw + 1 - w)
+    M = nx.max_weight_matching(G, maxcardinality=True)
+    pairs, tot = [], 0
+    for (a, b) in M:
+        if a[0] == "d" and b[0] == "d":
+            i, j = sorted((a[1], b[1]))
+            pairs.append((i, j))
+            tot += wpair(i, j)
+        elif a[0] != b[0]:
+            i = a[1] if a[0] == "d" else b[1]
+            pairs.append((i, -1))
+            tot += wbound(i)
+    if sum(2 if j >= 0 else 1 for (_, j) in pairs) != k:
+        raise ValueError("no perfect matching")
+    return pairs, tot
+
+
+def mwpm(defects, wpair, wbound):
+    """Exact minimum-weight matching with boundary.  A pair with
+    w(i, j) >= wb(i) + wb(j) is never better than sending both defects to the
+    boundary, so the optimum splits over connected components of the other
+    pairs; each component is solved exactly (DP when small, blossom
+    otherwise)."""
+    k = len(defects)
+    useful = [[] for _ in range(k)]
+    for i in range(k):
+        for j in range(i + 1, k):
+            w = wpair(i, j)
+            if w is None:
+                continue
+            bi, bj = wbound(i), wbound(j)
+            if bi is not None and bj is not None and w >= bi + bj:
+                continue
+            useful[i].append(j)
+            useful[j].append(i)
+    seen = [False] * k
+    pairs, tot = [], 0
+    for r in range(k):
+        if seen[r]:
+            continue
+        comp, stack = [], [r]
+        seen[r] = True
+        while stack:
+            x = stack.pop()
+            comp.append(x)
+            for y in useful[x]:
+                if not seen[y]:
+                    seen[y] = True
+                    stack.append(y)
+        comp.sort()
+        wp = lambda a, b: wpair(comp[a], comp[b])
+        wb = lambda a: wbound(comp[a])
+        if len(comp) <= 14:
+            cp, ct = mwpm_dp(list(range(len(comp))), wp, wb)
+        else:
+            cp, ct = mwpm_blossom(len(comp), wp, wb)
+        for (a, b) in cp:
+            pairs.append((comp[a], comp[b] if b >= 0 else -1))
+        tot += ct
+    return pairs, tot
 
 
 def detectors(record, code, rounds):
@@ -271,7 +358,7 @@ def decode_color(G, D, c):
         w = dist[a].get(B)
         return None if w is None else w * WUNIT + pair_hash(a, B, 0, c)
 
-    pairs, tot1 = mwpm_dp(defects, wp, wb)
+    pairs, tot1 = mwpm(defects, wp, wb)
     score1 = tot1 // WUNIT
     # stage-1 edges (XOR of canonical paths, from the smaller id)
     e1 = {}
@@ -343,7 +430,7 @@ def decode_color(G, D, c):
         dd = dists[a].get(B)
         return None if dd is None else dd[0] * WUNIT + pair_hash(a, B, 1, c)
 
-    pairs2, tot2 = mwpm_dp(defects2, wp2, wb2)
+    pairs2, tot2 = mwpm(defects2, wp2, wb2)
     score2 = tot2 // WUNIT
     for (i, j) in pairs2:
         a = defects2[i]

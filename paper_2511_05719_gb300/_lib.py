@@ -40,6 +40,7 @@ class TTNError(RuntimeError):
 EXPORTS = ["ttn_build_circuit", "ttn_free_circuit", "ttn_circuit_info", "ttn_circuit_ops",
            "ttn_circuit_layout", "ttn_run_trajectories", "ttn_logical_error_rate", "ttn_decode",
            "ttn_debug_state", "ttn_philox_uniforms", "ttn_profile_begin", "ttn_profile_end",
+           "ttn_grad",
            "ttn_status_string", "ttn_last_error"]
 
 
@@ -71,6 +72,8 @@ def load_library():
                                     c_dblp]
     lib.ttn_philox_uniforms.argtypes = [ctypes.c_uint64, c_u64p, ctypes.c_uint64, c_i32p,
                                         ctypes.c_int32, c_dblp]
+    lib.ttn_grad.argtypes = [vp, ctypes.POINTER(RunParams), ctypes.c_uint64, ctypes.c_int32,
+                             ctypes.c_double, c_dblp, c_dblp, c_dblp, c_dblp]
     lib.ttn_profile_begin.argtypes = [ctypes.c_int32]
     lib.ttn_profile_end.argtypes = [c_dblp, c_u64p, c_dblp, c_dblp, c_u64p]
     lib.ttn_status_string.restype = ctypes.c_char_p
@@ -262,3 +265,38 @@ def profile_end():
     return dict(timed_ms=ms.value, timed_launches=nl.value,
                 flops=dict(zip(KERNEL_CLASSES, list(fl))), bytes=dict(zip(KERNEL_CLASSES, list(by))),
                 launches=dict(zip(KERNEL_CLASSES, list(la))))
+
+
+def grad(circuit, shots, wrt="theta", noise="srx", theta=0.0, gamma=0.0, chi=16, precision="fp64",
+         seed=0, first_traj=0, h=1e-4, svd_eps=0.0, svd_mode="auto", return_score=False):
+    """Score-function estimate of dp_L/d(theta or gamma): (p_L, dpL, sigma[, score])."""
+    lib = load_library()
+    p, keep = _run_params(noise, theta, gamma, chi, precision, seed, first_traj, svd_eps,
+                          svd_mode=svd_mode)
+    pl, g, sg = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    score = np.zeros(shots) if return_score else None
+    _check(lib.ttn_grad(circuit.handle, ctypes.byref(p), shots, 0 if wrt == "theta" else 1, h,
+                        ctypes.byref(pl), ctypes.byref(g), ctypes.byref(sg),
+                        score.ctypes.data_as(c_dblp) if return_score else None))
+    if return_score:
+        return pl.value, g.value, sg.value, score
+    return pl.value, g.value, sg.value
+
+
+def logical_error_rate_fn(circuit, shots, **kw):
+    """torch.autograd.Function whose forward is p_L(theta) and whose backward
+    is the score-function dp_L/dtheta from ttn_grad."""
+    import torch
+
+    class _PL(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, theta):
+            pl, g, sg = grad(circuit, shots, wrt="theta", theta=float(theta), **kw)
+            ctx.g = g
+            return torch.tensor(pl, dtype=torch.float64)
+
+        @staticmethod
+        def backward(ctx, gout):
+            return gout * ctx.g
+
+    return _PL.apply

@@ -144,7 +144,7 @@ static RunRequest make_request(const ttn_run_params* p, uint64_t n_traj, void* s
   rq.precision = p->precision;
   rq.theta = p->theta;
   rq.gamma = p->gamma;
-  rq.svd_eps = p->svd_eps > 0 ? p->svd_eps : (p->precision == TTN_PREC_FP64 ? 1e-13 : 3e-7);
+  rq.svd_eps = p->svd_eps > 0 ? p->svd_eps : (p->precision == TTN_PREC_FP64 ? 1e-13 : 5e-7);
   rq.seed = p->seed;
   rq.first_traj = p->first_traj;
   rq.n_traj = n_traj;
@@ -201,6 +201,55 @@ ttn_status ttn_logical_error_rate(const ttn_circuit* c, const ttn_run_params* p,
   if (p_L) *p_L = pl;
   if (sigma) *sigma = std::sqrt(pl * (1.0 - pl) / (double)shots);
   if (n_fail) *n_fail = nf;
+  return TTN_OK;
+}
+
+ttn_status ttn_grad(const ttn_circuit* c, const ttn_run_params* p, uint64_t shots, int32_t wrt,
+                    double h, double* p_L, double* dpL, double* dpL_sigma, double* score) {
+  ttn_status s = check_params(c, p);
+  if (s != TTN_OK) return s;
+  if (shots < 2) return fail_with(TTN_EINVAL, "shots must be >= 2");
+  if (wrt != 0 && wrt != 1) return fail_with(TTN_EINVAL, "wrt must be 0 (theta) or 1 (gamma)");
+  if (p->theta_per_traj || p->gamma_per_traj)
+    return fail_with(TTN_EINVAL, "ttn_grad takes one theta and one gamma");
+  if (h <= 0.0) h = 1e-4;
+  if (wrt == 1 && (p->gamma - h < 0.0 || p->gamma + h > 1.0))
+    return fail_with(TTN_EINVAL, "gamma +- h must stay in [0, 1]");
+  const bool srx_like = p->noise == TTN_NOISE_SRX || p->noise == TTN_NOISE_SRX_PTA || p->noise == TTN_NOISE_SRX_AD;
+  const bool ad_like = p->noise == TTN_NOISE_AD || p->noise == TTN_NOISE_AD_PTA || p->noise == TTN_NOISE_SRX_AD;
+  if ((wrt == 0 && !srx_like) || (wrt == 1 && !ad_like))
+    return fail_with(TTN_EINVAL, "the noise model does not depend on that parameter");
+  RunRequest rq = make_request(p, shots, nullptr);
+  rq.grad_wrt = wrt;
+  rq.grad_h = h;
+  std::vector<uint8_t> fail(shots);
+  std::vector<double> sc(shots);
+  RunOutputs out;
+  out.fail = fail.data();
+  out.score = sc.data();
+  s = run_trajectories_device(*c, rq, out);
+  if (s != TTN_OK) return s;
+  // score-function estimator: dp_L/dx = E[fail * d/dx log p(trajectory)]
+  double n = 0, nf = 0, m1 = 0, m2 = 0;
+  for (uint64_t i = 0; i < shots; ++i) {
+    if (fail[i] > 1) continue;  // decoder bound exceeded: not counted
+    const double f = fail[i];
+    const double x = f * sc[i];
+    n += 1;
+    nf += f;
+    m1 += x;
+    m2 += x * x;
+  }
+  if (n < 2) return fail_with(TTN_EOVERFLOW, "no decodable shots");
+  const double mean = m1 / n, var = fmax(0.0, m2 / n - mean * mean);
+  if (p_L) *p_L = nf / n;
+  if (dpL) *dpL = mean;
+  if (dpL_sigma) *dpL_sigma = std::sqrt(var / (n - 1));
+  if (score) std::memcpy(score, sc.data(), sizeof(double) * shots);
+  if (out.decode_overflow > 0) {
+    set_error("decoder: some shots exceeded the matching bound and were not counted");
+    return TTN_EOVERFLOW;
+  }
   return TTN_OK;
 }
 

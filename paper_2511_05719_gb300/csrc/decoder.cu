@@ -24,8 +24,11 @@
 //   fail = parity(data) ^ parity(number of corrected qubits)  (Z-bar = Z^n).
 //   Matching weights are w * 2^40 + h(a, b), h a 28-bit splitmix64 hash of
 //   the node pair, stage and colour, so the optimum is unique.
-// Exact matching: subset dynamic programme, at most KMAX defects per
-// instance (more sets the overflow counter and the shot's fail byte to 2).
+// Exact matching: the optimum splits over connected components of the pairs
+// cheaper than sending both defects to the boundary; each component is
+// solved by a subset DP.  At most KMAX defects per instance and KCOMP per
+// component (beyond that the overflow counter is raised and the shot's fail
+// byte is 2).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -38,7 +41,8 @@
 
 namespace ttn {
 
-static constexpr int KMAX = 16;
+static constexpr int KMAX = 128;   // defects per matching instance
+static constexpr int KCOMP = 16;   // defects per independent component (subset DP)
 static constexpr int64_t WUNIT = (int64_t)1 << 40;
 static constexpr int64_t INF64 = (int64_t)1 << 62;
 
@@ -161,6 +165,8 @@ struct DecDev {
   int64_t* dist2;          // [KMAX + 1][NN]
   uint8_t* e1;             // [T * ncm + T * P]
   uint8_t* resid;          // [NN]
+  int* defs;               // [4 * KMAX] defects, partners, components, local ids
+  int64_t* wb;             // [KMAX] boundary weights
   size_t dp_stride, d2_stride, e1_stride;
   int32_t* overflow;
 };
@@ -181,52 +187,80 @@ __device__ __forceinline__ uint64_t pair_hash(int a, int b, int stage, int color
   return x >> 36;
 }
 
-// Exact minimum-weight matching by subset DP; W[i*k+j] / Wb[i] < 0 = absent.
-__device__ int64_t mwpm_dp(int k, const int64_t* W, const int64_t* Wb, int64_t* f, int8_t* ch,
-                           int* partner) {
-  const int full = (1 << k) - 1;
-  f[0] = 0;
-  for (int mask = 1; mask <= full; ++mask) {
-    int i = __ffs(mask) - 1;
-    int rest = mask & ~(1 << i);
-    int64_t best = INF64;
-    int bc = -2;
-    if (Wb[i] >= 0 && f[rest] < INF64) {
-      int64_t cand = Wb[i] + f[rest];
-      if (cand < best) {
-        best = cand;
+// Exact minimum-weight matching of k defects (each to another defect or to
+// the boundary).  A pair with W(i,j) >= Wb(i) + Wb(j) is never better than
+// sending both to the boundary, so the optimum decomposes over the connected
+// components of the graph of the other pairs; each component is solved
+// exactly by a subset DP.  wfun(i, j) / wb[i] return the perturbed weight or
+// a negative value when absent.  Returns the total, or -1 when a component
+// exceeds KCOMP defects (overflow), -2 when no perfect matching exists.
+template <typename WF>
+__device__ int64_t mwpm_exact(int k, WF wfun, const int64_t* wb, int64_t* f, int8_t* ch, int* partner,
+                              int* comp, int* loc) {
+  // union-find by label propagation (k <= KMAX_TOTAL)
+  for (int i = 0; i < k; ++i) comp[i] = i;
+  bool changed = true;
+  while (changed) {
+    changed = false;
+    for (int i = 0; i < k; ++i)
+      for (int j = i + 1; j < k; ++j) {
+        if (comp[i] == comp[j]) continue;
+        const int64_t w = wfun(i, j);
+        if (w < 0) continue;
+        if (wb[i] >= 0 && wb[j] >= 0 && w >= wb[i] + wb[j]) continue;
+        const int m = min(comp[i], comp[j]);
+        comp[i] = comp[j] = m;
+        changed = true;
+      }
+  }
+  int64_t total = 0;
+  for (int root = 0; root < k; ++root) {
+    int s = 0;
+    for (int i = 0; i < k; ++i)
+      if (comp[i] == root) loc[s++] = i;
+    if (s == 0) continue;
+    if (s > KCOMP) return -1;
+    const int full = (1 << s) - 1;
+    f[0] = 0;
+    for (int mask = 1; mask <= full; ++mask) {
+      const int a = __ffs(mask) - 1;
+      const int rest = mask & ~(1 << a);
+      int64_t best = INF64;
+      int bc = -2;
+      const int64_t wba = wb[loc[a]];
+      if (wba >= 0 && f[rest] < INF64) {
+        best = wba + f[rest];
         bc = -1;
       }
-    }
-    int m = rest;
-    while (m) {
-      int j = __ffs(m) - 1;
-      m &= m - 1;
-      int64_t wij = W[i * k + j];
-      int sub = rest & ~(1 << j);
-      if (wij >= 0 && f[sub] < INF64) {
-        int64_t cand = wij + f[sub];
-        if (cand < best) {
-          best = cand;
-          bc = j;
+      int m = rest;
+      while (m) {
+        const int c = __ffs(m) - 1;
+        m &= m - 1;
+        const int64_t w = wfun(loc[a], loc[c]);
+        const int sub = rest & ~(1 << c);
+        if (w >= 0 && f[sub] < INF64 && w + f[sub] < best) {
+          best = w + f[sub];
+          bc = c;
         }
       }
+      f[mask] = best;
+      ch[mask] = (int8_t)bc;
     }
-    f[mask] = best;
-    ch[mask] = (int8_t)bc;
-  }
-  int mask = full;
-  while (mask) {
-    int i = __ffs(mask) - 1;
-    int j = ch[mask];
-    partner[i] = j;
-    mask &= ~(1 << i);
-    if (j >= 0) {
-      partner[j] = i;
-      mask &= ~(1 << j);
+    if (f[full] >= INF64) return -2;
+    total += f[full];
+    int mask = full;
+    while (mask) {
+      const int a = __ffs(mask) - 1;
+      const int c = ch[mask];
+      partner[loc[a]] = c >= 0 ? loc[c] : -1;
+      mask &= ~(1 << a);
+      if (c >= 0) {
+        partner[loc[c]] = loc[a];
+        mask &= ~(1 << c);
+      }
     }
   }
-  return f[full];
+  return total;
 }
 
 __device__ __forceinline__ int edge_id1(const DecDev& d, int c, int u, int w) {
@@ -363,9 +397,11 @@ __global__ void k_decode(DecDev d, int nb, const uint8_t* records, uint8_t* fail
   uint8_t* resid = d.resid + (int64_t)s * (2 * NN);
   uint8_t* done = resid + NN;
   int ny[256], nw[256];
-  int defs[KMAX];
-  int partner[KMAX];
-  int64_t W[KMAX * KMAX], Wb[KMAX];
+  int* defs = d.defs + (int64_t)s * 4 * KMAX;
+  int* partner = defs + KMAX;
+  int* comp = defs + 2 * KMAX;
+  int* loc = defs + 3 * KMAX;
+  int64_t* Wb = d.wb + (int64_t)s * KMAX;
   // detectors into resid scratch temporarily: Dbit(t, p)
   auto Dbit = [&](int t, int p) -> int {
     int cur = t < C ? rec[t * 2 * P + 2 * p] : 0;
@@ -398,14 +434,14 @@ __global__ void k_decode(DecDev d, int nb, const uint8_t* records, uint8_t* fail
       int a = defs[i];
       int db = D1[(size_t)a * NN + d.B];
       Wb[i] = db < 0 ? -1 : (int64_t)db * WUNIT + (int64_t)pair_hash(a, d.B, 0, c);
-      for (int j = 0; j < k; ++j) {
-        int dd = D1[(size_t)a * NN + defs[j]];
-        W[i * k + j] = (i == j || dd < 0) ? -1 : (int64_t)dd * WUNIT + (int64_t)pair_hash(a, defs[j], 0, c);
-      }
     }
-    int64_t tot1 = mwpm_dp(k, W, Wb, f, ch, partner);
-    if (tot1 >= INF64) {
-      atomicAdd(d.overflow + 1, 1);
+    auto w1 = [&](int i, int j) -> int64_t {
+      const int dd = D1[(size_t)defs[i] * NN + defs[j]];
+      return dd < 0 ? -1 : (int64_t)dd * WUNIT + (int64_t)pair_hash(defs[i], defs[j], 0, c);
+    };
+    int64_t tot1 = mwpm_exact(k, w1, Wb, f, ch, partner, comp, loc);
+    if (tot1 < 0) {
+      if (tot1 == -2) atomicAdd(d.overflow + 1, 1);
       over = true;
       break;
     }
@@ -468,15 +504,14 @@ __global__ void k_decode(DecDev d, int nb, const uint8_t* records, uint8_t* fail
       int a = defs[i];
       int64_t kb = dist2[(size_t)i * NN + d.B];
       Wb[i] = kb >= INF64 ? -1 : (kb >> 20) * WUNIT + (int64_t)pair_hash(a, d.B, 1, c);
-      for (int j = 0; j < k2; ++j) {
-        int64_t kk = dist2[(size_t)i * NN + defs[j]];
-        W[i * k2 + j] = (i == j || kk >= INF64) ? -1
-                                                : (kk >> 20) * WUNIT + (int64_t)pair_hash(a, defs[j], 1, c);
-      }
     }
-    int64_t tot2 = mwpm_dp(k2, W, Wb, f, ch, partner);
-    if (tot2 >= INF64) {
-      atomicAdd(d.overflow + 1, 1);
+    auto w2 = [&](int i, int j) -> int64_t {
+      const int64_t kk = dist2[(size_t)i * NN + defs[j]];
+      return kk >= INF64 ? -1 : (kk >> 20) * WUNIT + (int64_t)pair_hash(defs[i], defs[j], 1, c);
+    };
+    int64_t tot2 = mwpm_exact(k2, w2, Wb, f, ch, partner, comp, loc);
+    if (tot2 < 0) {
+      if (tot2 == -2) atomicAdd(d.overflow + 1, 1);
       over = true;
       break;
     }
@@ -613,7 +648,7 @@ ttn_status decode_device(const ttn_circuit& c, int nb, const uint8_t* d_records,
   UP(inc_off, inc_off);
   UP(inc, inc);
 #undef UP
-  d.dp_stride = (size_t)1 << KMAX;
+  d.dp_stride = (size_t)1 << KCOMP;
   d.d2_stride = (size_t)(KMAX + 1) * t.n_nodes;
   d.e1_stride = (size_t)t.T * t.n_cls_max + (size_t)t.T * t.P;
   auto alloc = [&](void** p, size_t bytes) -> bool {
@@ -627,6 +662,8 @@ ttn_status decode_device(const ttn_circuit& c, int nb, const uint8_t* d_records,
             alloc((void**)&d.dist2, sizeof(int64_t) * d.d2_stride * chunk) &&
             alloc((void**)&d.e1, d.e1_stride * chunk) &&
             alloc((void**)&d.resid, (size_t)2 * t.n_nodes * chunk) &&
+            alloc((void**)&d.defs, sizeof(int) * 4 * KMAX * chunk) &&
+            alloc((void**)&d.wb, sizeof(int64_t) * KMAX * chunk) &&
             alloc((void**)&d.overflow, 2 * sizeof(int32_t));
   if (!ok) {
     cleanup();
@@ -675,7 +712,8 @@ ttn_status decode_device(const ttn_circuit& c, int nb, const uint8_t* d_records,
   }
   if (ovf[0] > 0) {
     set_error("decoder: " + std::to_string(ovf[0]) + " shot(s) exceed " + std::to_string(KMAX) +
-              " defects in one matching instance (fail byte set to 2)");
+              " defects per instance or " + std::to_string(KCOMP) +
+              " per matching component (fail byte set to 2)");
     return TTN_EOVERFLOW;
   }
   if (ovf[1] > 0) {

@@ -120,6 +120,9 @@ struct Dev {
   double eps_gram, tol_gram, tol_abs_gram;
   int svd_mode;
   unsigned long long* ledger;  // [2 * NCLASS] algorithmic flops, bytes (or null)
+  uint8_t* choice;       // [B][n_events] sampled outcome of every stochastic event
+  int n_events;
+  int forced;            // 1: replay the recorded choices instead of sampling
   double* frob;          // [B] |M|_F^2 of the current Gram-path move
   int32_t* trunc;        // [B] 1 if that move truncated
   int max_sweeps;
@@ -235,10 +238,10 @@ __global__ void __launch_bounds__(256) k_svd_move(Dev<R> d, int v, int w, int ca
   if (n > 1) {
     const int ne = n + (n & 1);
     const int M1 = ne - 1;
-    const R tolm = (R)d.tol * sqrt((R)(m > 1 ? m : 1));
+    const double tolm = d.tol * sqrt((double)(m > 1 ? m : 1));
     // a column below eps |M|_F / sqrt(n) is always dropped (s_max^2 >=
     // |M|_F^2 / n): it takes no part in rotations
-    const R skip2 = (R)(d.eps * d.eps * fro2 / (double)n);
+    const double skip2 = d.eps * d.eps * fro2 / (double)n;
     int sweep = 0;
     for (; sweep < d.max_sweeps; ++sweep) {
       int rotated = 0;
@@ -255,13 +258,16 @@ __global__ void __launch_bounds__(256) k_svd_move(Dev<R> d, int v, int w, int ca
           if (p >= n || q >= n) continue;
           cx<R>* wp = W + (int64_t)p * m;
           cx<R>* wq = W + (int64_t)q * m;
-          R a = 0, bb = 0, gr = 0, gi = 0;
+          // inner products accumulated in double (products of floats are
+          // exact in double; this path only sees bonds up to 64)
+          double a = 0, bb = 0, gr = 0, gi = 0;
           for (int i = lane; i < m; i += 32) {
-            cx<R> x = wp[i], y = wq[i];
-            a += cabs2(x);
-            bb += cabs2(y);
-            gr += x.x * y.x + x.y * y.y;
-            gi += x.x * y.y - x.y * y.x;
+            const cx<R> x = wp[i], y = wq[i];
+            const double xr = x.x, xi = x.y, yr = y.x, yi = y.y;
+            a += xr * xr + xi * xi;
+            bb += yr * yr + yi * yi;
+            gr += xr * yr + xi * yi;
+            gi += xr * yi - xi * yr;
           }
           a = warp_sum(a);
           bb = warp_sum(bb);
@@ -269,17 +275,18 @@ __global__ void __launch_bounds__(256) k_svd_move(Dev<R> d, int v, int w, int ca
           gi = warp_sum(gi);
           if (!(a > skip2) || !(bb > skip2)) continue;
           // |g| and its phase without squaring tiny numbers
-          const R gm = fmax(fabs(gr), fabs(gi));
-          if (gm == R(0)) continue;
-          const R grs = gr / gm, gis = gi / gm;
-          const R hs = sqrt(grs * grs + gis * gis);
-          const R g = gm * hs;
+          const double gm = fmax(fabs(gr), fabs(gi));
+          if (gm == 0.0) continue;
+          const double grs = gr / gm, gis = gi / gm;
+          const double hs = sqrt(grs * grs + gis * gis);
+          const double g = gm * hs;
           if (!(g > tolm * sqrt(a) * sqrt(bb))) continue;
           rotated = 1;
-          R zeta = (bb - a) / (R(2) * g);
-          R t = (zeta >= R(0) ? R(1) : R(-1)) / (fabs(zeta) + sqrt(R(1) + zeta * zeta));
-          R c = R(1) / sqrt(R(1) + t * t), sn = c * t;
-          cx<R> ec = {grs / hs, -gis / hs};  // conj(g / |g|), unit modulus
+          const double zeta = (bb - a) / (2.0 * g);
+          const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+          const double cd = 1.0 / sqrt(1.0 + t * t);
+          const R c = (R)cd, sn = (R)(cd * t);
+          const cx<R> ec = {(R)(grs / hs), (R)(-gis / hs)};  // conj(g / |g|), unit modulus
           for (int i = lane; i < m; i += 32) {
             cx<R> x = wp[i], y = cmul(ec, wq[i]);
             wp[i] = {c * x.x - sn * y.x, c * x.y - sn * y.y};
@@ -1051,7 +1058,13 @@ __global__ void k_layer1q(Dev<R> d, const Op1* ops, const Group1* groups, int g0
         margin = fmin(margin, fabs(uu - cum));
         if (kk == 3 && uu < cum) kk = i;
       }
-      if (margin < d.tie_eps) atomicAdd(&d.ties[b], 1);
+      uint8_t* ch = d.choice + (int64_t)b * d.n_events + o.event;
+      if (d.forced) {
+        kk = *ch;
+      } else {
+        *ch = (uint8_t)kk;
+        if (margin < d.tie_eps) atomicAdd(&d.ties[b], 1);
+      }
       atomicAdd(&d.logp[b], log(p[kk]));
       if (kk == 1) { U[0] = {0, 0}; U[1] = {1, 0}; U[2] = {1, 0}; U[3] = {0, 0}; }
       if (kk == 2) { U[0] = {0, 0}; U[1] = {0, -1}; U[2] = {0, 1}; U[3] = {0, 0}; }
@@ -1098,9 +1111,11 @@ __global__ void k_measure(Dev<R> d, int q, int event, int recbit, int xbasis, in
   double tot = n0 + n1;
   double p1 = n1 / tot, p0 = 1.0 - p1;
   double uu = draw_uniform(d.seed, d.traj[b], (uint32_t)event);
-  int mres = uu >= p0 ? 1 : 0;
+  uint8_t* ch = d.choice + (int64_t)b * d.n_events + event;
+  int mres = d.forced ? (int)*ch : (uu >= p0 ? 1 : 0);
   double pm = mres ? p1 : p0;
-  R sc = (R)(1.0 / sqrt(mres ? n1 : n0));
+  const double nm = mres ? n1 : n0;
+  R sc = nm > 0.0 ? (R)(1.0 / sqrt(nm)) : R(0);
   for (int e = lane; e < cnt; e += 32) {
     int x = e / (dr * du), y = (e / du) % dr;
     int bit = leg == 0 ? x : y;
@@ -1108,7 +1123,10 @@ __global__ void k_measure(Dev<R> d, int q, int event, int recbit, int xbasis, in
   }
   if (lane == 0) {
     d.logp[b] += log(pm);
-    if (fabs(uu - p0) < d.tie_eps) d.ties[b] += 1;
+    if (!d.forced) {
+      *ch = (uint8_t)mres;
+      if (fabs(uu - p0) < d.tie_eps) d.ties[b] += 1;
+    }
     d.rec[(int64_t)b * d.n_rec + recbit] = (uint8_t)mres;
     d.last[(int64_t)b * d.N + q] = (uint8_t)mres;
     if (!(tot > 0.0)) atomicOr(&d.err[b], ERR_ZERO_NORM);
@@ -1141,11 +1159,12 @@ __global__ void k_ad(Dev<R> d, int q, int event, int pos, int B) {
   const double P1 = n1 / tot;
   const double p1 = g * P1;
   const double uu = draw_uniform(d.seed, d.traj[b], (uint32_t)event);
-  const bool jump = uu < p1;
+  uint8_t* ch = d.choice + (int64_t)b * d.n_events + event;
+  const bool jump = d.forced ? (*ch != 0) : (uu < p1);
   __syncwarp();
   if (jump) {
     // K1 = sqrt(g)|0><1|: the |1> slice moves to |0>, normalised by sqrt(n1)
-    R sc = (R)(1.0 / sqrt(n1));
+    R sc = n1 > 0.0 ? (R)(1.0 / sqrt(n1)) : R(0);
     const int half = cnt / 2;
     for (int e = lane; e < half; e += 32) {
       int i0, i1;
@@ -1165,7 +1184,10 @@ __global__ void k_ad(Dev<R> d, int q, int event, int pos, int B) {
   }
   if (lane == 0) {
     d.logp[b] += jump ? log(p1) : log1p(-p1);
-    if (fabs(uu - p1) < d.tie_eps) d.ties[b] += 1;
+    if (!d.forced) {
+      *ch = (uint8_t)jump;
+      if (fabs(uu - p1) < d.tie_eps) d.ties[b] += 1;
+    }
   }
 }
 
@@ -1302,6 +1324,7 @@ struct Engine {
   int32_t* dErr = nullptr;
   double* dFrob = nullptr;
   int32_t* dTrunc = nullptr;
+  uint8_t* dChoice = nullptr;
   int32_t* dLeafdim = nullptr;
   Op1* dOp1 = nullptr;
   Group1* dGroups = nullptr;
@@ -1379,7 +1402,7 @@ struct Engine {
   size_t bytes_per_traj() const {
     return sizeof(cx<R>) * (size_t)(tstride + wstride + 3 * vstride) +
            sizeof(int32_t) * (2 * c.L + 2 * nmax + 4) + sizeof(double) * (nmax + 5) + c.n_rec + c.N +
-           64;
+           c.n_events + 64;
   }
 
   ttn_status alloc(int Bmax) {
@@ -1406,6 +1429,7 @@ struct Engine {
     CK(cudaMalloc(&dErr, sizeof(int32_t) * B));
     CK(cudaMalloc(&dFrob, sizeof(double) * B));
     CK(cudaMalloc(&dTrunc, sizeof(int32_t) * B));
+    CK(cudaMalloc(&dChoice, (size_t)std::max(1, c.n_events) * B));
     if (profile().active) {
       CK(cudaMalloc(&dLedger, sizeof(unsigned long long) * 2 * NCLASS));
       CK(cudaMemset(dLedger, 0, sizeof(unsigned long long) * 2 * NCLASS));
@@ -1455,13 +1479,16 @@ struct Engine {
     dev.frob = dFrob;
     dev.trunc = dTrunc;
     dev.ledger = dLedger;
+    dev.choice = dChoice;
+    dev.n_events = std::max(1, c.n_events);
+    dev.forced = 0;
     return TTN_OK;
   }
 
   void release() {
     void* ptrs[] = {dT, dW, dV, dR, dG, dOff, dDims, dSv, dPerm, dK, dN, dLogp, dDisc, dTies, dRec,
                     dLast, dTheta, dGamma, dTraj, dErr, dFrob, dTrunc, dLeafdim, dOp1, dGroups,
-                    dLedger};
+                    dLedger, dChoice};
     for (void* p : ptrs)
       if (p) cudaFree(p);
   }
@@ -1629,6 +1656,35 @@ static ttn_status run_impl(const ttn_circuit& c, const RunRequest& rq, RunOutput
     if (out.discarded) CK(cp(out.discarded + t0, eng.dDisc, sizeof(double) * nb));
     if (out.near_ties) CK(cp(out.near_ties + t0, eng.dTies, sizeof(int32_t) * nb));
     CK(cudaMemcpyAsync(err.data(), eng.dErr, sizeof(int32_t) * nb, cudaMemcpyDeviceToHost, st));
+    // score of each trajectory: replay its choices at strength +- h
+    if (rq.grad_wrt >= 0 && !rq.debug_amps) {
+      std::vector<double> lp(nb), lm(nb);
+      for (int sgn = 0; sgn < 2; ++sgn) {
+        const double dh = sgn == 0 ? rq.grad_h : -rq.grad_h;
+        for (int i = 0; i < nb; ++i) {
+          if (rq.grad_wrt == 0) th[i] += dh;
+          else ga[i] += dh;
+        }
+        CK(cudaMemcpyAsync(eng.dTheta, th.data(), sizeof(double) * nb, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(eng.dGamma, ga.data(), sizeof(double) * nb, cudaMemcpyHostToDevice, st));
+        // keep the forward records: the replay writes the same bits
+        eng.dev.forced = 1;
+        ttn_status s3 = eng.launch(nb, stop);
+        eng.dev.forced = 0;
+        if (s3 != TTN_OK) {
+          eng.release();
+          return s3;
+        }
+        CK(cudaMemcpyAsync(sgn == 0 ? lp.data() : lm.data(), eng.dLogp, sizeof(double) * nb,
+                           cudaMemcpyDeviceToHost, st));
+        for (int i = 0; i < nb; ++i) {
+          if (rq.grad_wrt == 0) th[i] -= dh;
+          else ga[i] -= dh;
+        }
+      }
+      CK(cudaStreamSynchronize(st));
+      for (int i = 0; i < nb; ++i) out.score[t0 + i] = (lp[i] - lm[i]) / (2.0 * rq.grad_h);
+    }
     if (rq.debug_amps) {
       std::vector<int32_t> qol(c.L, -1);
       for (int q = 0; q < c.N; ++q) qol[c.leaf_of_qubit[q]] = q;

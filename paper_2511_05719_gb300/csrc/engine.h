@@ -20,6 +20,8 @@ struct RunRequest {
   size_t max_device_bytes = 0;   // 0: 80% of free device memory
   int max_batch = 0;             // 0: as many as fit
   int svd_mode = 0;              // 0 auto, 1 one-sided Jacobi on M, 2 Gram matrix
+  int grad_wrt = -1;             // -1 none, 0 theta, 1 gamma: replay for the score
+  double grad_h = 1e-4;          // replay step
 };
 
 struct RunOutputs {
@@ -30,6 +32,7 @@ struct RunOutputs {
   double* log_prob = nullptr;
   double* discarded = nullptr;
   int32_t* near_ties = nullptr;
+  double* score = nullptr;       // host [n_traj], with grad_wrt >= 0
   int err_flags = 0;
   int batch = 0;
   size_t bytes_per_traj = 0;

@@ -194,3 +194,44 @@ def test_profile_ledger_counts_work():
     assert prof["timed_launches"] > 0 and prof["timed_ms"] > 0
     assert prof["flops"]["svd_jacobi"] > 0 and prof["flops"]["absorb"] > 0
     assert prof["flops"]["gram"] == 0
+
+
+def _exact_pl_d3_c1(theta):
+    circ = build_circuit(3, 1)
+    code = circ.code
+    Pq = code.n_plaq
+    keep = [2 * p for p in range(Pq)] + [2 * Pq + q for q in range(code.n)]
+    dist = DM.record_distribution(circ, theta, keep)
+    G = DEC.DecoderGraphs(3, 1)
+    pl = 0.0
+    for bits, pr in dist.items():
+        rec = np.zeros(circ.n_record_bits, dtype=np.uint8)
+        rec[keep] = bits
+        pl += pr * DEC.decode(G, rec)[0]
+    return pl
+
+
+def test_grad_matches_exact_derivative_d3_c1():
+    # exact dp_L/dtheta: central difference of the exact p_L (deferred
+    # measurement), O(dtheta^2) ~ 1e-6 relative
+    theta, dth = 0.12, 1e-3
+    exact = (_exact_pl_d3_c1(theta + dth) - _exact_pl_d3_c1(theta - dth)) / (2 * dth)
+    c = P.Circuit(3, 1)
+    shots = 12000
+    pl, g, sg, score = P.grad(c, shots, wrt="theta", noise="srx", theta=theta, chi=64,
+                              precision="fp32", seed=W.BASE_SEED + 31, return_score=True)
+    assert sg > 0
+    assert abs(g - exact) < 3 * sg + 1e-3 * abs(exact), (g, sg, exact)
+    # the score has zero mean: E[d log p / d theta] = d/dtheta sum p = 0
+    assert abs(score.mean()) < 3 * score.std() / np.sqrt(shots)
+
+
+def test_grad_ad_and_argument_checks():
+    c = P.Circuit(3, 1)
+    pl, g, sg = P.grad(c, 2000, wrt="gamma", noise="ad", gamma=0.05, chi=64, precision="fp32",
+                       seed=3)
+    assert sg > 0 and np.isfinite(g)
+    with pytest.raises(P.TTNError):
+        P.grad(c, 100, wrt="gamma", noise="srx", theta=0.1, chi=16)
+    with pytest.raises(P.TTNError):
+        P.grad(c, 100, wrt="gamma", noise="ad", gamma=0.0, chi=16)

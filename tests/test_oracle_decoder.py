@@ -53,6 +53,26 @@ def test_dp_matching_equals_brute_force():
         assert covered == list(range(k))
 
 
+def test_component_split_and_blossom_equal_dp():
+    rng = np.random.default_rng(8)
+    for trial in range(40):
+        k = int(rng.integers(1, 12))
+        pts = rng.uniform(0, 20, size=(k, 2))
+        W = np.round(np.abs(pts[:, None, :] - pts[None, :, :]).sum(-1)).astype(int) + 1
+        Wb = np.round(np.minimum(pts[:, 0], 20 - pts[:, 0])).astype(int) + 1
+
+        def wp(i, j):
+            return int(W[i, j]) * dec.WUNIT + dec.pair_hash(i, j, 0, 1)
+
+        def wb(i):
+            return int(Wb[i]) * dec.WUNIT + dec.pair_hash(i, 500, 0, 1)
+        p0, t0 = dec.mwpm_dp(list(range(k)), wp, wb)
+        p1, t1 = dec.mwpm(list(range(k)), wp, wb)
+        p2, t2 = dec.mwpm_blossom(k, wp, wb)
+        assert t0 == t1 == t2
+        assert sorted(p0) == sorted(p1) == sorted(p2)
+
+
 def test_noise_free_records_do_not_fail():
     circ = build_circuit(3, 3)
     G = dec.DecoderGraphs(3, 3)
