@@ -119,6 +119,7 @@ struct Dev {
   double eps, tie_eps, tol;
   double eps_gram, tol_gram, tol_abs_gram;
   int svd_mode;
+  int eig_smem_bytes;    // dynamic shared memory of k_eig launches
   unsigned long long* ledger;  // [2 * NCLASS] algorithmic flops, bytes (or null)
   uint8_t* choice;       // [B][n_events] sampled outcome of every stochastic event
   int n_events;
@@ -619,10 +620,14 @@ __global__ void __launch_bounds__(512) k_eig(Dev<R> d, int v, int w, int capped)
   const int dl = D[2 * v], dr = D[2 * v + 1], du = D[v];
   const int leg = (w == 2 * v) ? 0 : ((w == 2 * v + 1) ? 1 : 2);
   const int n = leg == 0 ? dl : (leg == 1 ? dr : du);
-  cx<R>* G = d.G + (int64_t)b * d.vstride;
+  cx<R>* Gglob = d.G + (int64_t)b * d.vstride;
   cx<R>* V = d.V + (int64_t)b * d.vstride;
   double* sv = d.sv + (int64_t)b * d.nmax;
   int32_t* perm = d.perm + (int64_t)b * d.nmax;
+  // G lives in shared memory when the launch provides room for n x n
+  extern __shared__ __align__(16) unsigned char eig_smem[];
+  const bool in_smem = (int64_t)n * n * sizeof(cx<R>) <= (int64_t)d.eig_smem_bytes;
+  cx<R>* G = in_smem ? reinterpret_cast<cx<R>*>(eig_smem) : Gglob;
   __shared__ R pc[256], ps[256];
   __shared__ cx<R> pe[256];
   __shared__ int pp[256], pq[256];
@@ -638,6 +643,7 @@ __global__ void __launch_bounds__(512) k_eig(Dev<R> d, int v, int w, int capped)
   for (int idx = tid; idx < n * n; idx += nth) {
     int x = idx / n, j = idx - x * n;
     V[idx] = {R(x == j), R(0)};
+    if (in_smem) G[idx] = Gglob[idx];
   }
   if (tid == 0) ledger_add(d.ledger, KC_EIG, 36.0 * (double)n * n * n, 3.0 * sizeof(cx<R>) * n * (double)n);
   if (tid == 0) {
@@ -769,7 +775,7 @@ __global__ void __launch_bounds__(512) k_eig(Dev<R> d, int v, int w, int capped)
   // V_k (n x k, row-major, columns in descending eigenvalue order) into G
   for (int idx = tid; idx < n * k; idx += nth) {
     const int x = idx / k, c = idx - x * k;
-    G[idx] = V[(int64_t)x * n + perm[c]];
+    Gglob[idx] = V[(int64_t)x * n + perm[c]];
   }
 }
 
@@ -1519,7 +1525,9 @@ struct Engine {
             timed(KC_COPY, [&] { k_gather_rows<R><<<dim3(std::max(1, ceil_div(ncap[v], 1024)), nb), 256, 0, st>>>(dev, v, w); });
             const int tn = std::max(1, ceil_div(nmv, 64));
             timed(KC_GRAM, [&] { k_gram<R><<<dim3(tn, tn, nb), 256, 0, st>>>(dev, v, w); });
-            timed(KC_EIG, [&] { k_eig<R><<<nb, 512, 0, st>>>(dev, v, w, s.c); });
+            const int smem = (int)std::min<int64_t>(nmv * nmv * (int64_t)sizeof(cx<R>), 131072);
+            dev.eig_smem_bytes = nmv * nmv * (int64_t)sizeof(cx<R>) <= 131072 ? smem : 0;
+            timed(KC_EIG, [&] { k_eig<R><<<nb, 512, dev.eig_smem_bytes, st>>>(dev, v, w, s.c); });
             timed(KC_FORMU, [&] { k_form_u<R><<<dim3(std::max(1, ceil_div(mmax, 64)), tn, nb), 256, 0, st>>>(dev, v, w); });
             timed(KC_OTHER, [&] { k_unorm<R><<<nb, 256, 0, st>>>(dev, v, w); });
           } else {
@@ -1593,6 +1601,8 @@ static ttn_status run_impl(const ttn_circuit& c, const RunRequest& rq, RunOutput
   eng.dev.tol = sizeof(R) == 8 ? 1e-15 : 1e-7;
   eng.dev.max_sweeps = sizeof(R) == 8 ? 40 : 30;
   eng.dev.svd_mode = rq.svd_mode;
+  eng.dev.eig_smem_bytes = 0;
+  CK(cudaFuncSetAttribute(k_eig<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 131072));
   eng.dev.eps_gram = sizeof(R) == 8 ? 1e-7 : 1e-4;
   eng.dev.tol_gram = sizeof(R) == 8 ? 1e-13 : 3e-6;
   eng.dev.tol_abs_gram = sizeof(R) == 8 ? 1e-15 : 2e-7;
