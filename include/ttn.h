@@ -84,7 +84,11 @@ typedef struct {
   int32_t svd_mode;              /* factorisation of a centre move:
                                     0 auto (FP32 bonds above 64: Gram),
                                     1 one-sided Jacobi on the tensor,
-                                    2 Gram matrix + two-sided Jacobi       */
+                                    2 Gram matrix; eigensolver two-sided
+                                      Jacobi in shared memory up to 128 KB
+                                      of Gram matrix, tridiagonal above,
+                                    3 Gram matrix, tridiagonal eigensolver
+                                      at every size                       */
 } ttn_run_params;
 
 typedef struct ttn_circuit ttn_circuit;  /* opaque, library-owned */

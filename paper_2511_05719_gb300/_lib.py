@@ -146,7 +146,7 @@ class Circuit:
         return out
 
 
-SVD_MODE = {"auto": 0, "jacobi": 1, "gram": 2}
+SVD_MODE = {"auto": 0, "jacobi": 1, "gram": 2, "gram_tri": 3}
 
 
 def _run_params(noise, theta, gamma, chi, precision, seed, first_traj, svd_eps,

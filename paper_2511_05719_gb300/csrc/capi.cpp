@@ -133,7 +133,7 @@ static ttn_status check_params(const ttn_circuit* c, const ttn_run_params* p) {
   if (p->chi < 1 || p->chi > 4096) return fail_with(TTN_EINVAL, "chi must be in [1, 4096]");
   if (!std::isfinite(p->theta)) return fail_with(TTN_EINVAL, "theta must be finite");
   if (!(p->gamma >= 0.0 && p->gamma <= 1.0)) return fail_with(TTN_EINVAL, "gamma must be in [0, 1]");
-  if (p->svd_mode < 0 || p->svd_mode > 2) return fail_with(TTN_EINVAL, "svd_mode must be 0, 1 or 2");
+  if (p->svd_mode < 0 || p->svd_mode > 3) return fail_with(TTN_EINVAL, "svd_mode must be 0, 1, 2 or 3");
   return TTN_OK;
 }
 

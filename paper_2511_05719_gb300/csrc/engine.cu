@@ -98,6 +98,7 @@ struct Dev {
   cx<R>* V;              // [B][vstride] right singular vectors (column-major n x n)
   cx<R>* Rm;             // [B][vstride] factor absorbed by the neighbour (k x n)
   cx<R>* G;              // [B][vstride] Gram matrix / V_k S_k^-1 (Gram path)
+  cx<R>* Ts;             // [B][2 vstride] tridiagonal eigensolver scratch
   int64_t vstride;
   double* sv;            // [B][nmax]
   int32_t* perm;         // [B][nmax]
@@ -131,6 +132,14 @@ struct Dev {
 };
 
 enum : int32_t { ERR_ZERO_NORM = 1, ERR_NO_CONVERGE = 2, ERR_CAPACITY = 4, ERR_NAN = 8 };
+
+// Gram matrices up to this size are diagonalised in shared memory (k_eig);
+// larger ones by the tridiagonal solver (k_eig_tri).
+static constexpr int EIG_SMEM_MAX = 131072;
+template <typename R>
+constexpr int tri_smem_bytes() {
+  return 512 * (5 * 2 * (int)sizeof(R) + 3 * (int)sizeof(R));
+}
 
 template <typename R>
 __device__ __forceinline__ cx<R>* node_ptr(const Dev<R>& d, int b, int v) {
@@ -610,6 +619,75 @@ __global__ void __launch_bounds__(256) k_gram(Dev<R> d, int v, int w) {
       [&](int i, int j, cx<R> val) { G[(int64_t)i * n + j] = val; });
 }
 
+// Selection shared by the Gram eigensolvers: eigenvalues (sv[j], any order)
+// -> singular values, perm = descending order, kept rank k (s > eps_keep
+// s_max, at most chi when capped), bond dimension update.  Returns k to every
+// thread.
+template <typename R>
+__device__ int eig_select(Dev<R>& d, int b, int v, int w, int capped, int n, double trace,
+                          double eps_keep) {
+  const int tid = threadIdx.x, nth = blockDim.x;
+  int* D = d.dims + b * d.ds;
+  double* sv = d.sv + (int64_t)b * d.nmax;
+  int32_t* perm = d.perm + (int64_t)b * d.nmax;
+  __shared__ int s_kk;
+  for (int j = tid; j < n; j += nth) {
+    double lam = sv[j];
+    double sj = lam > 0.0 ? sqrt(lam) : 0.0;
+    if (!(sj < 1e300)) {
+      atomicOr(&d.err[b], ERR_NAN);
+      sj = 0.0;
+    }
+    sv[j] = sj;
+  }
+  __syncthreads();
+  for (int j = tid; j < n; j += nth) {
+    double sj = sv[j];
+    int r = 0;
+    for (int i = 0; i < n; ++i) {
+      double si = sv[i];
+      r += (si > sj) || (si == sj && i < j);
+    }
+    perm[r] = j;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double smax = sv[perm[0]];
+    int k = 0;
+    for (int i = 0; i < n; ++i)
+      if (sv[perm[i]] > eps_keep * smax) ++k;
+    if (k < 1) k = 1;
+    if (smax == 0.0) atomicOr(&d.err[b], ERR_ZERO_NORM);
+    int trunc = 0;
+    if (capped && k > d.chi) {
+      k = d.chi;
+      trunc = 1;
+    }
+    s_kk = k;
+    const int bond = (w == v / 2) ? v : w;
+    D[bond] = k;
+    d.knew[b] = k;
+    d.nold[b] = n;
+    d.frob[b] = trace;
+    d.trunc[b] = trunc;
+  }
+  __syncthreads();
+  return s_kk;
+}
+
+// Jacobi tail: V (row-major n x n eigenvectors) -> V_k into G.
+template <typename R>
+__device__ void eig_select_tail(Dev<R>& d, int b, int v, int w, int capped, int n, const cx<R>* V,
+                                cx<R>* Gglob, double trace) {
+  const int k = eig_select(d, b, v, w, capped, n, trace, d.eps_gram);
+  const int32_t* perm = d.perm + (int64_t)b * d.nmax;
+  // V_k (n x k, row-major, columns in descending eigenvalue order) into G
+  for (int idx = threadIdx.x; idx < n * k; idx += blockDim.x) {
+    const int x = idx / k, c = idx - x * k;
+    Gglob[idx] = V[(int64_t)x * n + perm[c]];
+  }
+}
+
 // Eigen-decomposition of G by cyclic two-sided Jacobi; then the kept rank,
 // V_k S_k^-1 (into G) and R = S_k V_k^H (into Rm).
 template <typename R>
@@ -623,7 +701,6 @@ __global__ void __launch_bounds__(512) k_eig(Dev<R> d, int v, int w, int capped)
   cx<R>* Gglob = d.G + (int64_t)b * d.vstride;
   cx<R>* V = d.V + (int64_t)b * d.vstride;
   double* sv = d.sv + (int64_t)b * d.nmax;
-  int32_t* perm = d.perm + (int64_t)b * d.nmax;
   // G lives in shared memory when the launch provides room for n x n
   extern __shared__ __align__(16) unsigned char eig_smem[];
   const bool in_smem = (int64_t)n * n * sizeof(cx<R>) <= (int64_t)d.eig_smem_bytes;
@@ -631,8 +708,7 @@ __global__ void __launch_bounds__(512) k_eig(Dev<R> d, int v, int w, int capped)
   __shared__ R pc[256], ps[256];
   __shared__ cx<R> pe[256];
   __shared__ int pp[256], pq[256];
-  __shared__ int s_k;
-  __shared__ double s_scale, s_tr;
+  __shared__ double s_tr;
   if ((int64_t)n * n > d.vstride || n > d.nmax || n > 512) {
     if (tid == 0) {
       atomicOr(&d.err[b], ERR_CAPACITY);
@@ -730,53 +806,451 @@ __global__ void __launch_bounds__(512) k_eig(Dev<R> d, int v, int w, int capped)
     }
     if (sweep == d.max_sweeps && tid == 0) atomicOr(&d.err[b], ERR_NO_CONVERGE);
   }
-  for (int j = tid; j < n; j += nth) {
-    double lam = (double)G[(int64_t)j * n + j].x;
-    double sj = lam > 0.0 ? sqrt(lam) : 0.0;
-    if (!(sj < 1e300)) {
-      atomicOr(&d.err[b], ERR_NAN);
-      sj = 0.0;
-    }
-    sv[j] = sj;
+  for (int j = tid; j < n; j += nth) sv[j] = (double)G[(int64_t)j * n + j].x;  // eigenvalues
+  __syncthreads();
+  eig_select_tail(d, b, v, w, capped, n, V, Gglob, s_tr);
+}
+
+// Block-wide sums (blockDim.x a multiple of 32); red holds 64 doubles.
+__device__ __forceinline__ double2 block_sum2(double a, double c, double* red) {
+  a = warp_sum(a);
+  c = warp_sum(c);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __syncthreads();
+  if (lane == 0) {
+    red[warp] = a;
+    red[32 + warp] = c;
   }
   __syncthreads();
-  for (int j = tid; j < n; j += nth) {
-    double sj = sv[j];
-    int r = 0;
-    for (int i = 0; i < n; ++i) {
-      double si = sv[i];
-      r += (si > sj) || (si == sj && i < j);
+  double2 t = make_double2(0.0, 0.0);
+  for (int i = 0; i < nw; ++i) {
+    t.x += red[i];
+    t.y += red[32 + i];
+  }
+  return t;
+}
+
+template <typename R>
+__device__ __forceinline__ R fast_div(R a, R b) {
+  return a / b;
+}
+template <>
+__device__ __forceinline__ float fast_div<float>(float a, float b) {
+  return __fdividef(a, b);
+}
+
+// Householder vector of column c of A (rows c+1..n-1, already updated):
+// H = I - tau v v^H with H x = alpha e_1; v scaled so that |v_0| = 1.
+// Writes v into vout[0..m) and into A's column c below the diagonal.
+template <typename R>
+__device__ void tri_reflector(cx<R>* A, int n, int c, cx<R>* vout, R* tau, cx<R>* ek, double* red) {
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int m = n - c - 1;
+  double x2 = 0.0, t2 = 0.0;
+  for (int r = tid; r < m; r += nth) {
+    const cx<R> x = A[(int64_t)(c + 1 + r) * n + c];
+    const double a2 = (double)x.x * x.x + (double)x.y * x.y;
+    x2 += a2;
+    if (r > 0) t2 += a2;
+  }
+  const double2 sums = block_sum2(x2, t2, red);
+  const cx<R> x0 = A[(int64_t)(c + 1) * n + c];
+  if (sums.y == 0.0) {  // already reduced: H = I
+    for (int r = tid; r < m; r += nth) vout[r] = {R(0), R(0)};
+    if (tid == 0) {
+      tau[c] = R(0);
+      ek[c] = x0;
     }
-    perm[r] = j;
+    __syncthreads();
+    return;
+  }
+  const double xn = sqrt(sums.x);
+  const double ax0 = sqrt((double)x0.x * x0.x + (double)x0.y * x0.y);
+  const double phr = ax0 > 0.0 ? x0.x / ax0 : 1.0, phi = ax0 > 0.0 ? x0.y / ax0 : 0.0;
+  const double den = ax0 + xn;  // |x_0 - alpha|
+  __syncthreads();               // every thread has read x0
+  for (int r = tid; r < m; r += nth) {
+    cx<R> vr;
+    if (r == 0) {
+      vr = {(R)phr, (R)phi};
+    } else {
+      const cx<R> x = A[(int64_t)(c + 1 + r) * n + c];
+      vr = {(R)(x.x / den), (R)(x.y / den)};
+    }
+    vout[r] = vr;
+    A[(int64_t)(c + 1 + r) * n + c] = vr;
+  }
+  if (tid == 0) {
+    tau[c] = (R)(2.0 / (1.0 + sums.y / (den * den)));
+    ek[c] = {(R)(-phr * xn), (R)(-phi * xn)};  // alpha = -phase(x_0) |x|
+  }
+  __syncthreads();
+}
+
+// Hermitian eigensolver for Gram matrices too large for shared memory
+// (n <= 512), one CTA per trajectory, G resident in L2:
+//  1. Householder reduction G = Q T Q^H to Hermitian tridiagonal form, the
+//     rank-2 update of step j fused with the matrix-vector product of step
+//     j+1 (one read-modify-write pass over the trailing block per step);
+//  2. a diagonal phase matrix makes T real symmetric; couplings below
+//     2 eps |T| are dropped, splitting T into unreduced blocks;
+//  3. eigenvalues by bisection on Sturm counts (thread per eigenvalue);
+//  4. eigenvectors of the kept eigenvalues by inverse iteration on the
+//     pivoted LU factors of T - lambda I restricted to the eigenvalue's block
+//     (thread per vector; unresolved eigenvalues of one block get shifts
+//     spaced by a few ulps so their vectors stay independent, as in LAPACK's
+//     stein), made orthonormal by Cholesky QR applied twice;
+//  5. back-transformation by the stored reflectors.
+// (Golub & Van Loan, Matrix Computations, Ch. 8.)  Selection and output as in
+// k_eig: V_k (n x k, row-major) into G.
+template <typename R>
+__global__ void __launch_bounds__(512) k_eig_tri(Dev<R> d, int v, int w, int capped) {
+  const int b = blockIdx.x;
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int* D = d.dims + b * d.ds;
+  const int leg = (w == 2 * v) ? 0 : ((w == 2 * v + 1) ? 1 : 2);
+  const int n = leg == 0 ? D[2 * v] : (leg == 1 ? D[2 * v + 1] : D[v]);
+  if ((int64_t)n * n > d.vstride || n > d.nmax || n > nth || nth > 512) {
+    if (tid == 0) {
+      atomicOr(&d.err[b], ERR_CAPACITY);
+      d.knew[b] = 0;
+    }
+    return;
+  }
+  cx<R>* A = d.G + (int64_t)b * d.vstride;
+  cx<R>* Vk = d.V + (int64_t)b * d.vstride;
+  // real scratch (4 n^2): eigenvectors Z of T and the LU factors U0, U1, U2
+  R* Z = reinterpret_cast<R*>(d.Ts + (int64_t)b * 2 * d.vstride);
+  R* U0 = Z + (int64_t)n * n;
+  R* U1 = U0 + (int64_t)n * n;
+  R* U2 = U1 + (int64_t)n * n;
+  double* sv = d.sv + (int64_t)b * d.nmax;
+  const int32_t* perm = d.perm + (int64_t)b * d.nmax;
+  extern __shared__ __align__(16) unsigned char tri_smem[];
+  cx<R>* vk = reinterpret_cast<cx<R>*>(tri_smem);  // reflector of the current step
+  cx<R>* wk = vk + 512;                             // w = p - K v; later the phases D
+  cx<R>* vn = wk + 512;                             // next reflector; later b^2, lambda
+  cx<R>* pp = vn + 512;                             // matvec partials / p
+  cx<R>* ek = pp + 512;                             // sub-diagonal of T
+  R* dg = reinterpret_cast<R*>(ek + 512);          // diagonal of T
+  R* bt = dg + 512;                                 // |sub-diagonal|
+  R* tau = bt + 512;                                // reflector scalars
+  __shared__ double red[64];
+  __shared__ double s_sc;
+  __shared__ int bstart[512], bend[512];  // unreduced block [bstart, bend) of each row
+
+  double trp = 0.0;
+  for (int j = tid; j < n; j += nth) trp += (double)A[(int64_t)j * n + j].x;
+  const double trace = block_sum2(trp, 0.0, red).x;
+
+  // ---- 1. tridiagonalisation
+  if (tid == 0) dg[0] = A[0].x;
+  if (n == 2 && tid == 0) {
+    ek[0] = A[2];
+    dg[1] = A[3].x;
+  }
+  if (n >= 3) {
+    tri_reflector(A, n, 0, vk, tau, ek, red);
+    {  // p_0 = tau_0 A[1:, 1:] v_0
+      const int m = n - 1, G = nth / m, col = tid % m, g = tid / m;
+      if (g < G) {
+        cx<R> acc = {R(0), R(0)};
+        for (int j = g; j < m; j += G)
+          acc = cadd(acc, cmulc(A[(int64_t)(1 + j) * n + 1 + col], vk[j]));
+        pp[g * m + col] = acc;
+      }
+      __syncthreads();
+      if (tid < m) {
+        cx<R> acc = pp[tid];
+        for (int gg = 1; gg < G; ++gg) acc = cadd(acc, pp[gg * m + tid]);
+        pp[tid] = cscale(acc, tau[0]);
+      }
+      __syncthreads();
+    }
+    for (int k = 0; k + 3 <= n; ++k) {
+      const int o = k + 1, m = n - o;  // trailing block rows/cols o..n-1
+      // (a) K = tau/2 v^H p (real), w = p - K v
+      double kp = 0.0;
+      for (int r = tid; r < m; r += nth) kp += (double)vk[r].x * pp[r].x + (double)vk[r].y * pp[r].y;
+      const R K = (R)(0.5 * (double)tau[k] * block_sum2(kp, 0.0, red).x);
+      for (int r = tid; r < m; r += nth) wk[r] = {pp[r].x - K * vk[r].x, pp[r].y - K * vk[r].y};
+      __syncthreads();
+      // (b) column o of the trailing block
+      const cx<R> cw0 = {wk[0].x, -wk[0].y}, cv0 = {vk[0].x, -vk[0].y};
+      for (int r = tid; r < m; r += nth) {
+        cx<R> a = A[(int64_t)(o + r) * n + o];
+        const cx<R> t1 = cmul(vk[r], cw0), t2 = cmul(wk[r], cv0);
+        a = {a.x - t1.x - t2.x, a.y - t1.y - t2.y};
+        A[(int64_t)(o + r) * n + o] = a;
+        if (r == 0) dg[o] = a.x;
+      }
+      __syncthreads();
+      // (c) next reflector from the updated column o
+      const bool has_next = (o + 3 <= n);
+      if (has_next) {
+        tri_reflector(A, n, o, vn, tau, ek, red);
+      } else if (tid == 0) {
+        ek[o] = A[(int64_t)(n - 1) * n + o];
+      }
+      // (d) rank-2 update of rows/cols o+1.. fused with p_next = A' v_next
+      const int mp = m - 1;
+      if (mp > 0) {
+        const int G = nth / mp, col = tid % mp, g = tid / mp;
+        if (g < G) {
+          const cx<R> cvi = {vk[1 + col].x, -vk[1 + col].y}, cwi = {wk[1 + col].x, -wk[1 + col].y};
+          cx<R> acc = {R(0), R(0)};
+          for (int j = g; j < mp; j += G) {
+            cx<R>* ap = A + (int64_t)(o + 1 + j) * n + o + 1 + col;
+            cx<R> a = *ap;
+            const cx<R> t1 = cmul(vk[1 + j], cwi), t2 = cmul(wk[1 + j], cvi);
+            a = {a.x - t1.x - t2.x, a.y - t1.y - t2.y};
+            *ap = a;
+            if (has_next) acc = cadd(acc, cmulc(a, vn[j]));
+          }
+          if (has_next) pp[g * mp + col] = acc;
+        }
+        __syncthreads();
+        if (has_next) {
+          if (tid < mp) {
+            cx<R> acc = pp[tid];
+            for (int gg = 1; gg < G; ++gg) acc = cadd(acc, pp[gg * mp + tid]);
+            pp[tid] = cscale(acc, tau[o]);
+          }
+          for (int r = tid; r < mp; r += nth) vk[r] = vn[r];
+          __syncthreads();
+        }
+      }
+    }
+    if (tid == 0) dg[n - 1] = A[(int64_t)(n - 1) * n + n - 1].x;
+  }
+  __syncthreads();
+
+  // ---- 2. phases D (T = D T_real D^H), scale to |T| <= 1, split
+  R* b2 = reinterpret_cast<R*>(vn);
+  R* lam = b2 + 512;
+  if (tid == 0) {
+    cx<R> ph = {R(1), R(0)};
+    double dmax = 0.0, bmax = 0.0;
+    for (int j = 0; j < n; ++j) {
+      wk[j] = ph;
+      dmax = fmax(dmax, fabs((double)dg[j]));
+      if (j + 1 < n) {
+        const cx<R> e = ek[j];
+        const double ae = sqrt((double)e.x * e.x + (double)e.y * e.y);
+        bt[j] = (R)ae;
+        bmax = fmax(bmax, ae);
+        if (ae > 0.0) ph = cmul(ph, cx<R>{(R)(e.x / ae), (R)(e.y / ae)});
+      }
+    }
+    double sc = dmax + 2.0 * bmax;
+    if (!(sc > 0.0) || !(sc < 1e300)) sc = 1.0;
+    s_sc = sc;
+  }
+  __syncthreads();
+  const double sc = s_sc;
+  const R epsR = sizeof(R) == 8 ? R(2.220446049250313e-16) : R(1.1920929e-07);
+  const R pivmin = sizeof(R) == 8 ? R(1e-280) : R(1e-30);
+  for (int j = tid; j < n; j += nth) {
+    dg[j] = (R)(dg[j] / sc);
+    if (j + 1 < n) {
+      R bj = (R)(bt[j] / sc);
+      if (bj <= 2 * epsR) bj = R(0);
+      bt[j] = bj;
+      b2[j] = bj * bj;
+    }
   }
   __syncthreads();
   if (tid == 0) {
-    double smax = sv[perm[0]];
-    int k = 0;
-    for (int i = 0; i < n; ++i)
-      if (sv[perm[i]] > d.eps_gram * smax) ++k;
-    if (k < 1) k = 1;
-    if (smax == 0.0) atomicOr(&d.err[b], ERR_ZERO_NORM);
-    int trunc = 0;
-    if (capped && k > d.chi) {
-      k = d.chi;
-      trunc = 1;
+    int st = 0;
+    for (int i = 0; i < n; ++i) {
+      bstart[i] = st;
+      if (i == n - 1 || bt[i] == R(0)) {
+        for (int r = st; r <= i; ++r) bend[r] = i + 1;
+        st = i + 1;
+      }
     }
-    s_k = k;
-    const int bond = (w == v / 2) ? v : w;
-    D[bond] = k;
-    d.knew[b] = k;
-    d.nold[b] = n;
-    d.frob[b] = s_tr;
-    d.trunc[b] = trunc;
   }
   __syncthreads();
-  const int k = s_k;
-  // V_k (n x k, row-major, columns in descending eigenvalue order) into G
+
+  // ---- 3. bisection: thread j finds eigenvalue number j - s (ascending) of
+  // the block [s, e) that holds row j
+  if (tid < n) {
+    const int j = tid, s0 = bstart[j], e0 = bend[j];
+    R lo = R(-1) - 4 * epsR, hi = R(1) + 4 * epsR;
+    for (int it = 0; it < 128; ++it) {
+      const R mid = R(0.5) * (lo + hi);
+      if (!(hi - lo > fmax(2 * epsR * fmax(fabs(lo), fabs(hi)), R(0.125) * epsR)) || mid == lo || mid == hi)
+        break;
+      R q = dg[s0] - mid;
+      if (fabs(q) < pivmin) q = -pivmin;
+      int cnt = q < R(0);
+      for (int i = s0 + 1; i < e0; ++i) {
+        q = (dg[i] - mid) - fast_div(b2[i - 1], q);
+        if (fabs(q) < pivmin) q = -pivmin;
+        cnt += q < R(0);
+      }
+      if (cnt <= j - s0) lo = mid;
+      else hi = mid;
+    }
+    const R l = R(0.5) * (lo + hi);
+    lam[j] = l;
+    sv[j] = (double)l * sc;
+  }
+  __syncthreads();
+  // eigenvalues below a few ulps of |T| are not resolved in this precision
+  const double eps_keep = fmax(d.eps_gram, sqrt(4.0 * (double)epsR));
+  const int k = eig_select(d, b, v, w, capped, n, trace, eps_keep);
+  if (tid == 0)
+    ledger_add(d.ledger, KC_EIG, 16.0 / 3.0 * (double)n * n * n + 8.0 * (double)n * n * k,
+               (double)sizeof(cx<R>) * ((double)n * n + (double)n * k));
+
+  // ---- 4. inverse iteration, thread c for kept column c (eigenvalue perm[c])
+  if (tid < k) {
+    const int c = tid, jj = perm[c], s0 = bstart[jj], e0 = bend[jj];
+    const R tolc = 16 * epsR;
+    int rk = 0;
+    while (jj - rk - 1 >= s0 && lam[jj - rk] - lam[jj - rk - 1] < tolc) ++rk;
+    const R l = lam[jj] + (R)rk * tolc;
+    for (int i = 0; i < n; ++i) {  // start vector: hashed, in (-1, 1), zero off the block
+      uint32_t h = (uint32_t)i * 0x9E3779B1u ^ ((uint32_t)c + 0x7F4A7C15u) * 0x85EBCA77u;
+      h ^= h >> 15;
+      h *= 0x2C1B3C6Du;
+      h ^= h >> 12;
+      const R x = (R)((double)(h >> 8) * (2.0 / 16777216.0) - 1.0 + 1.0 / 16777216.0);
+      Z[(int64_t)i * n + c] = (i >= s0 && i < e0) ? x : R(0);
+    }
+    for (int iter = 0; iter < 3; ++iter) {
+      // forward elimination with partial pivoting, right-hand side carried along
+      R cd = dg[s0] - l, cu = s0 + 1 < e0 ? bt[s0] : R(0), cr = Z[(int64_t)s0 * n + c];
+      for (int i = s0; i + 1 < e0; ++i) {
+        const R lo_ = bt[i], dn = dg[i + 1] - l, un = (i + 2 < e0) ? bt[i + 1] : R(0);
+        const R rn = Z[(int64_t)(i + 1) * n + c];
+        const int64_t at = (int64_t)i * n + c;
+        if (fabs(cd) >= fabs(lo_)) {
+          const R piv = cd == R(0) ? epsR : cd;
+          const R mlt = lo_ / piv;
+          U0[at] = piv;
+          U1[at] = cu;
+          U2[at] = R(0);
+          Z[at] = cr;
+          cd = dn - mlt * cu;
+          cu = un;
+          cr = rn - mlt * cr;
+        } else {
+          const R mlt = cd / lo_;
+          U0[at] = lo_;
+          U1[at] = dn;
+          U2[at] = un;
+          Z[at] = rn;
+          cd = cu - mlt * dn;
+          cu = -mlt * un;
+          cr = cr - mlt * rn;
+        }
+      }
+      U0[(int64_t)(e0 - 1) * n + c] = cd;
+      Z[(int64_t)(e0 - 1) * n + c] = cr;
+      // back substitution; pivots below eps |T| are replaced by eps |T|
+      R y1 = R(0), y2 = R(0), ymax = R(0);
+      for (int i = e0 - 1; i >= s0; --i) {
+        const int64_t at = (int64_t)i * n + c;
+        R u = U0[at];
+        if (fabs(u) < epsR) u = u < R(0) ? -epsR : epsR;
+        R y = Z[at];
+        if (i + 1 < e0) y -= U1[at] * y1;
+        if (i + 2 < e0) y -= U2[at] * y2;
+        y = y / u;
+        Z[at] = y;
+        y2 = y1;
+        y1 = y;
+        ymax = fmax(ymax, fabs(y));
+      }
+      const R inv = ymax > R(0) && ymax < R(1e30) ? R(1) / ymax : R(1);
+      double nrm = 0.0;
+      for (int i = s0; i < e0; ++i) {
+        const R y = Z[(int64_t)i * n + c] * inv;
+        nrm += (double)y * y;
+      }
+      const R s2 = (R)(1.0 / sqrt(fmax(nrm, 1e-300)));
+      for (int i = s0; i < e0; ++i) Z[(int64_t)i * n + c] = Z[(int64_t)i * n + c] * inv * s2;
+    }
+  }
+  __syncthreads();
+
+  // ---- 4b. Cholesky QR, applied twice, of Z[:, :k]: S = Z^T Z = L L^T, Z <- Z L^-T
+  for (int rep = 0; rep < 2 && k > 1; ++rep) {
+    R* S = U0;  // k x k
+    for (int idx = tid; idx < k * k; idx += nth) {
+      const int p = idx / k, q = idx - p * k;
+      if (q > p) continue;
+      R acc = R(0);
+      for (int i = 0; i < n; ++i) acc += Z[(int64_t)i * n + p] * Z[(int64_t)i * n + q];
+      S[idx] = acc;
+    }
+    __syncthreads();
+    for (int j = 0; j < k; ++j) {
+      R piv = S[j * k + j];
+      if (rep == 1 && !(piv > R(0.25)) && tid == 0) atomicOr(&d.err[b], ERR_NO_CONVERGE);
+      if (!(piv > R(1e-12))) piv = R(1e-12);
+      const R rj = sqrt(piv), irj = R(1) / rj;
+      __syncthreads();
+      if (tid == 0) S[j * k + j] = rj;
+      for (int p = j + 1 + tid; p < k; p += nth) S[p * k + j] *= irj;
+      __syncthreads();
+      const int t = k - j - 1;
+      for (int idx = tid; idx < t * t; idx += nth) {
+        const int p = j + 1 + idx / t, q = j + 1 + idx % t;
+        if (q > p) continue;
+        S[p * k + q] -= S[p * k + j] * S[q * k + j];
+      }
+      __syncthreads();
+    }
+    // rows of Z: y L^T = z, forward substitution per row
+    for (int i = tid; i < n; i += nth) {
+      R* zi = Z + (int64_t)i * n;
+      for (int q = 0; q < k; ++q) {
+        R y = zi[q];
+        for (int p = 0; p < q; ++p) y -= zi[p] * S[q * k + p];
+        zi[q] = y / S[q * k + q];
+      }
+    }
+    __syncthreads();
+  }
+
+  // ---- 5. back-transformation: V_k = H_0 ... H_{n-3} D Z_k (n x k in Vk)
   for (int idx = tid; idx < n * k; idx += nth) {
     const int x = idx / k, c = idx - x * k;
-    Gglob[idx] = V[(int64_t)x * n + perm[c]];
+    const R z = Z[(int64_t)x * n + c];
+    Vk[idx] = {wk[x].x * z, wk[x].y * z};
   }
+  __syncthreads();
+  for (int kk = n - 3; kk >= 0; --kk) {
+    const R tk = tau[kk];
+    if (tk == R(0)) continue;  // uniform across the block
+    const int m = n - kk - 1;
+    for (int r = tid; r < m; r += nth) vk[r] = A[(int64_t)(kk + 1 + r) * n + kk];
+    __syncthreads();
+    const int G = nth / k, c = tid % k, g = tid / k;
+    if (g < G) {
+      cx<R> acc = {R(0), R(0)};
+      for (int r = g; r < m; r += G) acc = cadd(acc, cmulc(vk[r], Vk[(int64_t)(kk + 1 + r) * k + c]));
+      pp[g * k + c] = acc;
+    }
+    __syncthreads();
+    if (tid < k) {
+      cx<R> acc = pp[tid];
+      for (int gg = 1; gg < G; ++gg) acc = cadd(acc, pp[gg * k + tid]);
+      pp[tid] = cscale(acc, tk);
+    }
+    __syncthreads();
+    for (int idx = tid; idx < m * k; idx += nth) {
+      const int r = idx / k, cc = idx - r * k;
+      cx<R>* vp = Vk + (int64_t)(kk + 1 + r) * k + cc;
+      const cx<R> t = cmul(vk[r], pp[cc]);
+      *vp = {vp->x - t.x, vp->y - t.y};
+    }
+    __syncthreads();
+  }
+  for (int idx = tid; idx < n * k; idx += nth) A[idx] = Vk[idx];
 }
 
 // Exact singular values of the kept columns: Y = M V_k was written into T_v;
@@ -1313,6 +1787,7 @@ struct Engine {
   cx<R>* dV = nullptr;
   cx<R>* dR = nullptr;
   cx<R>* dG = nullptr;
+  cx<R>* dTs = nullptr;
   int64_t* dOff = nullptr;
   int32_t* dDims = nullptr;
   double* dSv = nullptr;
@@ -1418,6 +1893,7 @@ struct Engine {
     CK(cudaMalloc(&dV, sizeof(cx<R>) * (size_t)vstride * B));
     CK(cudaMalloc(&dR, sizeof(cx<R>) * (size_t)vstride * B));
     CK(cudaMalloc(&dG, sizeof(cx<R>) * (size_t)vstride * B));
+    CK(cudaMalloc(&dTs, sizeof(cx<R>) * (size_t)vstride * 2 * B));
     CK(cudaMalloc(&dOff, sizeof(int64_t) * c.L));
     CK(cudaMalloc(&dDims, sizeof(int32_t) * 2 * c.L * B));
     CK(cudaMalloc(&dSv, sizeof(double) * nmax * B));
@@ -1462,6 +1938,7 @@ struct Engine {
     dev.V = dV;
     dev.Rm = dR;
     dev.G = dG;
+    dev.Ts = dTs;
     dev.vstride = vstride;
     dev.sv = dSv;
     dev.perm = dPerm;
@@ -1492,7 +1969,7 @@ struct Engine {
   }
 
   void release() {
-    void* ptrs[] = {dT, dW, dV, dR, dG, dOff, dDims, dSv, dPerm, dK, dN, dLogp, dDisc, dTies, dRec,
+    void* ptrs[] = {dT, dW, dV, dR, dG, dTs, dOff, dDims, dSv, dPerm, dK, dN, dLogp, dDisc, dTies, dRec,
                     dLast, dTheta, dGamma, dTraj, dErr, dFrob, dTrunc, dLeafdim, dOp1, dGroups,
                     dLedger, dChoice};
     for (void* p : ptrs)
@@ -1514,7 +1991,7 @@ struct Engine {
           const int v = s.a, w = s.b;
           const int bond = (w == v / 2) ? v : w;
           const int64_t nmv = 2 * (int64_t)bcap[bond];
-          const bool gram = dev.svd_mode == 2 || (dev.svd_mode == 0 && sizeof(R) == 4 && nmv > 64);
+          const bool gram = dev.svd_mode >= 2 || (dev.svd_mode == 0 && sizeof(R) == 4 && nmv > 64);
           if (gram) {
             const int lv = (w == 2 * v) ? 0 : ((w == 2 * v + 1) ? 1 : 2);
             int64_t c3[3] = {2 * (int64_t)bcap[2 * v], 2 * (int64_t)bcap[2 * v + 1],
@@ -1525,9 +2002,12 @@ struct Engine {
             timed(KC_COPY, [&] { k_gather_rows<R><<<dim3(std::max(1, ceil_div(ncap[v], 1024)), nb), 256, 0, st>>>(dev, v, w); });
             const int tn = std::max(1, ceil_div(nmv, 64));
             timed(KC_GRAM, [&] { k_gram<R><<<dim3(tn, tn, nb), 256, 0, st>>>(dev, v, w); });
-            const int smem = (int)std::min<int64_t>(nmv * nmv * (int64_t)sizeof(cx<R>), 131072);
-            dev.eig_smem_bytes = nmv * nmv * (int64_t)sizeof(cx<R>) <= 131072 ? smem : 0;
-            timed(KC_EIG, [&] { k_eig<R><<<nb, 512, dev.eig_smem_bytes, st>>>(dev, v, w, s.c); });
+            if (dev.svd_mode != 3 && nmv * nmv * (int64_t)sizeof(cx<R>) <= EIG_SMEM_MAX) {
+              dev.eig_smem_bytes = (int)(nmv * nmv * (int64_t)sizeof(cx<R>));
+              timed(KC_EIG, [&] { k_eig<R><<<nb, 512, dev.eig_smem_bytes, st>>>(dev, v, w, s.c); });
+            } else {
+              timed(KC_EIG, [&] { k_eig_tri<R><<<nb, 512, tri_smem_bytes<R>(), st>>>(dev, v, w, s.c); });
+            }
             timed(KC_FORMU, [&] { k_form_u<R><<<dim3(std::max(1, ceil_div(mmax, 64)), tn, nb), 256, 0, st>>>(dev, v, w); });
             timed(KC_OTHER, [&] { k_unorm<R><<<nb, 256, 0, st>>>(dev, v, w); });
           } else {
@@ -1602,7 +2082,8 @@ static ttn_status run_impl(const ttn_circuit& c, const RunRequest& rq, RunOutput
   eng.dev.max_sweeps = sizeof(R) == 8 ? 40 : 30;
   eng.dev.svd_mode = rq.svd_mode;
   eng.dev.eig_smem_bytes = 0;
-  CK(cudaFuncSetAttribute(k_eig<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 131072));
+  CK(cudaFuncSetAttribute(k_eig<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, EIG_SMEM_MAX));
+  CK(cudaFuncSetAttribute(k_eig_tri<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, tri_smem_bytes<R>()));
   eng.dev.eps_gram = sizeof(R) == 8 ? 1e-7 : 1e-4;
   eng.dev.tol_gram = sizeof(R) == 8 ? 1e-13 : 3e-6;
   eng.dev.tol_abs_gram = sizeof(R) == 8 ? 1e-15 : 2e-7;

@@ -167,9 +167,10 @@ def test_batching_does_not_change_results():
 GRAM_TOL = {"fp64": 1e-5, "fp32": 3e-3}
 
 
+@pytest.mark.parametrize("svd_mode", ["gram", "gram_tri"])
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 @pytest.mark.parametrize("noise", ["srx", "ad", "srx_ad"])
-def test_gram_path_amplitudes(noise, precision):
+def test_gram_path_amplitudes(noise, precision, svd_mode):
     circ = build_circuit(3, 2)
     th, ga = STRENGTH[noise]
     c = P.Circuit(3, 2, layout="optimized")
@@ -180,7 +181,7 @@ def test_gram_path_amplitudes(noise, precision):
             continue
         for L in layers:
             amp = P.debug_state(c, traj, L, noise=noise, theta=th, gamma=ga, chi=64,
-                                precision=precision, seed=W.BASE_SEED, svd_mode="gram")
+                                precision=precision, seed=W.BASE_SEED, svd_mode=svd_mode)
             want = ref["states"][L]
             err = np.linalg.norm(amp - want) / np.linalg.norm(want)
             assert err < GRAM_TOL[precision], (noise, traj, L, err)
