@@ -25,10 +25,11 @@
 //   Matching weights are w * 2^40 + h(a, b), h a 28-bit splitmix64 hash of
 //   the node pair, stage and colour, so the optimum is unique.
 // Exact matching: the optimum splits over connected components of the pairs
-// cheaper than sending both defects to the boundary; each component is
-// solved by a subset DP.  At most KMAX defects per instance and KCOMP per
-// component (beyond that the overflow counter is raised and the shot's fail
-// byte is 2).
+// cheaper than sending both defects to the boundary; a component of at most
+// KCOMP defects is solved by a subset DP, a larger one by the weighted
+// blossom algorithm (blossom.cuh) on the defects and their boundary copies.
+// At most KMAX defects per instance (beyond that the overflow counter is
+// raised and the shot's fail byte is 2).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -37,12 +38,14 @@
 #include <string>
 #include <vector>
 
+#include "blossom.cuh"
 #include "engine.h"
 
 namespace ttn {
 
 static constexpr int KMAX = 128;   // defects per matching instance
-static constexpr int KCOMP = 16;   // defects per independent component (subset DP)
+static constexpr int KCOMP = 12;   // largest component solved by the subset DP
+static_assert(2 * KMAX <= BL_NMAX, "blossom size");
 static constexpr int64_t WUNIT = (int64_t)1 << 40;
 static constexpr int64_t INF64 = (int64_t)1 << 62;
 
@@ -168,6 +171,8 @@ struct DecDev {
   int* defs;               // [4 * KMAX] defects, partners, components, local ids
   int64_t* wb;             // [KMAX] boundary weights
   size_t dp_stride, d2_stride, e1_stride;
+  unsigned char* bls;      // blossom scratch, bl_stride bytes per shot
+  size_t bl_stride;
   int32_t* overflow;
 };
 
@@ -193,10 +198,11 @@ __device__ __forceinline__ uint64_t pair_hash(int a, int b, int stage, int color
 // components of the graph of the other pairs; each component is solved
 // exactly by a subset DP.  wfun(i, j) / wb[i] return the perturbed weight or
 // a negative value when absent.  Returns the total, or -1 when a component
-// exceeds KCOMP defects (overflow), -2 when no perfect matching exists.
+// -2 when no perfect matching exists.  Components above KCOMP defects go to
+// the blossom matcher (scratch bl).
 template <typename WF>
 __device__ int64_t mwpm_exact(int k, WF wfun, const int64_t* wb, int64_t* f, int8_t* ch, int* partner,
-                              int* comp, int* loc) {
+                              int* comp, int* loc, void* bl) {
   // union-find by label propagation (k <= KMAX_TOTAL)
   for (int i = 0; i < k; ++i) comp[i] = i;
   bool changed = true;
@@ -219,7 +225,16 @@ __device__ int64_t mwpm_exact(int k, WF wfun, const int64_t* wb, int64_t* f, int
     for (int i = 0; i < k; ++i)
       if (comp[i] == root) loc[s++] = i;
     if (s == 0) continue;
-    if (s > KCOMP) return -1;
+    if (s > KCOMP) {
+      int* part = reinterpret_cast<int*>(f);  // the DP table is free here
+      auto wp = [&](int i, int j) -> int64_t { return wfun(loc[i], loc[j]); };
+      auto wbl = [&](int i) -> int64_t { return wb[loc[i]]; };
+      const int64_t t = min_matching_boundary(s, wp, wbl, part, bl);
+      if (t < 0) return t;
+      total += t;
+      for (int i = 0; i < s; ++i) partner[loc[i]] = part[i] >= 0 ? loc[part[i]] : -1;
+      continue;
+    }
     const int full = (1 << s) - 1;
     f[0] = 0;
     for (int mask = 1; mask <= full; ++mask) {
@@ -402,6 +417,7 @@ __global__ void k_decode(DecDev d, int nb, const uint8_t* records, uint8_t* fail
   int* comp = defs + 2 * KMAX;
   int* loc = defs + 3 * KMAX;
   int64_t* Wb = d.wb + (int64_t)s * KMAX;
+  void* bl = d.bls + (int64_t)s * d.bl_stride;
   // detectors into resid scratch temporarily: Dbit(t, p)
   auto Dbit = [&](int t, int p) -> int {
     int cur = t < C ? rec[t * 2 * P + 2 * p] : 0;
@@ -439,7 +455,7 @@ __global__ void k_decode(DecDev d, int nb, const uint8_t* records, uint8_t* fail
       const int dd = D1[(size_t)defs[i] * NN + defs[j]];
       return dd < 0 ? -1 : (int64_t)dd * WUNIT + (int64_t)pair_hash(defs[i], defs[j], 0, c);
     };
-    int64_t tot1 = mwpm_exact(k, w1, Wb, f, ch, partner, comp, loc);
+    int64_t tot1 = mwpm_exact(k, w1, Wb, f, ch, partner, comp, loc, bl);
     if (tot1 < 0) {
       if (tot1 == -2) atomicAdd(d.overflow + 1, 1);
       over = true;
@@ -509,7 +525,7 @@ __global__ void k_decode(DecDev d, int nb, const uint8_t* records, uint8_t* fail
       const int64_t kk = dist2[(size_t)i * NN + defs[j]];
       return kk >= INF64 ? -1 : (kk >> 20) * WUNIT + (int64_t)pair_hash(defs[i], defs[j], 1, c);
     };
-    int64_t tot2 = mwpm_exact(k2, w2, Wb, f, ch, partner, comp, loc);
+    int64_t tot2 = mwpm_exact(k2, w2, Wb, f, ch, partner, comp, loc, bl);
     if (tot2 < 0) {
       if (tot2 == -2) atomicAdd(d.overflow + 1, 1);
       over = true;
@@ -649,6 +665,7 @@ ttn_status decode_device(const ttn_circuit& c, int nb, const uint8_t* d_records,
   UP(inc, inc);
 #undef UP
   d.dp_stride = (size_t)1 << KCOMP;
+  d.bl_stride = (boundary_matching_scratch_bytes(KMAX) + 255) / 256 * 256;
   d.d2_stride = (size_t)(KMAX + 1) * t.n_nodes;
   d.e1_stride = (size_t)t.T * t.n_cls_max + (size_t)t.T * t.P;
   auto alloc = [&](void** p, size_t bytes) -> bool {
@@ -664,6 +681,7 @@ ttn_status decode_device(const ttn_circuit& c, int nb, const uint8_t* d_records,
             alloc((void**)&d.resid, (size_t)2 * t.n_nodes * chunk) &&
             alloc((void**)&d.defs, sizeof(int) * 4 * KMAX * chunk) &&
             alloc((void**)&d.wb, sizeof(int64_t) * KMAX * chunk) &&
+            alloc((void**)&d.bls, d.bl_stride * chunk) &&
             alloc((void**)&d.overflow, 2 * sizeof(int32_t));
   if (!ok) {
     cleanup();
@@ -712,12 +730,11 @@ ttn_status decode_device(const ttn_circuit& c, int nb, const uint8_t* d_records,
   }
   if (ovf[0] > 0) {
     set_error("decoder: " + std::to_string(ovf[0]) + " shot(s) exceed " + std::to_string(KMAX) +
-              " defects per instance or " + std::to_string(KCOMP) +
-              " per matching component (fail byte set to 2)");
+              " defects per matching instance (fail byte set to 2)");
     return TTN_EOVERFLOW;
   }
   if (ovf[1] > 0) {
-    set_error("decoder: canonical stage-2 path not found");
+    set_error("decoder: canonical path or perfect matching not found");
     return TTN_ECUDA;
   }
   return TTN_OK;

@@ -237,3 +237,18 @@ def test_grad_ad_and_argument_checks():
         P.grad(c, 100, wrt="gamma", noise="srx", theta=0.1, chi=16)
     with pytest.raises(P.TTNError):
         P.grad(c, 100, wrt="gamma", noise="ad", gamma=0.0, chi=16)
+
+
+def test_decoder_dense_syndromes_blossom_path():
+    """Dense syndrome histories: matching components far above the subset-DP
+    size go through the kernel's blossom matcher; bit-exact with the oracle."""
+    rng = np.random.default_rng(23)
+    for d, C, dens in ((5, 5, 0.3), (7, 3, 0.12), (7, 7, 0.1)):
+        c = P.Circuit(d, C)
+        G = DEC.DecoderGraphs(d, C)
+        n = 12
+        recs = (rng.random((n, c.n_record_bits)) < dens).astype(np.uint8)
+        fail, color, score = P.decode(c, recs)
+        for i in range(n):
+            f, col, s = DEC.decode(G, recs[i])
+            assert (fail[i], color[i], score[i]) == (f, col, s), (d, C, i)
