@@ -136,9 +136,11 @@ enum : int32_t { ERR_ZERO_NORM = 1, ERR_NO_CONVERGE = 2, ERR_CAPACITY = 4, ERR_N
 // Gram matrices up to this size are diagonalised in shared memory (k_eig);
 // larger ones by the tridiagonal solver (k_eig_tri).
 static constexpr int EIG_SMEM_MAX = 131072;
+static constexpr int TRI_UNROLL = 16;  // loads in flight per thread in L2-resident sweeps
+static constexpr int TRI_NB = 8;       // reflectors per compact-WY block of the back-transformation
 template <typename R>
 constexpr int tri_smem_bytes() {
-  return 512 * (5 * 2 * (int)sizeof(R) + 3 * (int)sizeof(R));
+  return 512 * (5 * 2 * (int)sizeof(R) + 3 * (int)sizeof(R)) + 2 * TRI_NB * 512 * 2 * (int)sizeof(R);
 }
 
 template <typename R>
@@ -999,13 +1001,25 @@ __global__ void __launch_bounds__(512) k_eig_tri(Dev<R> d, int v, int w, int cap
         if (g < G) {
           const cx<R> cvi = {vk[1 + col].x, -vk[1 + col].y}, cwi = {wk[1 + col].x, -wk[1 + col].y};
           cx<R> acc = {R(0), R(0)};
-          for (int j = g; j < mp; j += G) {
-            cx<R>* ap = A + (int64_t)(o + 1 + j) * n + o + 1 + col;
-            cx<R> a = *ap;
-            const cx<R> t1 = cmul(vk[1 + j], cwi), t2 = cmul(wk[1 + j], cvi);
-            a = {a.x - t1.x - t2.x, a.y - t1.y - t2.y};
-            *ap = a;
-            if (has_next) acc = cadd(acc, cmulc(a, vn[j]));
+          cx<R>* colp = A + (int64_t)(o + 1) * n + o + 1 + col;
+          // TRI_UNROLL rows per batch: all loads issued before any store
+          for (int j0 = g; j0 < mp; j0 += G * TRI_UNROLL) {
+            cx<R> a[TRI_UNROLL];
+#pragma unroll
+            for (int u = 0; u < TRI_UNROLL; ++u) {
+              const int j = j0 + u * G;
+              if (j < mp) a[u] = colp[(int64_t)j * n];
+            }
+#pragma unroll
+            for (int u = 0; u < TRI_UNROLL; ++u) {
+              const int j = j0 + u * G;
+              if (j < mp) {
+                const cx<R> t1 = cmul(vk[1 + j], cwi), t2 = cmul(wk[1 + j], cvi);
+                a[u] = {a[u].x - t1.x - t2.x, a[u].y - t1.y - t2.y};
+                colp[(int64_t)j * n] = a[u];
+                if (has_next) acc = cadd(acc, cmulc(a[u], vn[j]));
+              }
+            }
           }
           if (has_next) pp[g * mp + col] = acc;
         }
@@ -1149,7 +1163,12 @@ __global__ void __launch_bounds__(512) k_eig_tri(Dev<R> d, int v, int w, int cap
       }
       U0[(int64_t)(e0 - 1) * n + c] = cd;
       Z[(int64_t)(e0 - 1) * n + c] = cr;
-      // back substitution; pivots below eps |T| are replaced by eps |T|
+      // back substitution; pivots below eps |T| are replaced by eps |T|.
+      // The solution grows by up to 1/eps per small pivot: whenever it
+      // passes BIG, the solved part and the remaining right-hand side are
+      // scaled down together (the system is linear; the vector is
+      // normalised afterwards).
+      const R BIG = sizeof(R) == 8 ? R(1e150) : R(1e15);
       R y1 = R(0), y2 = R(0), ymax = R(0);
       for (int i = e0 - 1; i >= s0; --i) {
         const int64_t at = (int64_t)i * n + c;
@@ -1159,6 +1178,15 @@ __global__ void __launch_bounds__(512) k_eig_tri(Dev<R> d, int v, int w, int cap
         if (i + 1 < e0) y -= U1[at] * y1;
         if (i + 2 < e0) y -= U2[at] * y2;
         y = y / u;
+        if (!(fabs(y) <= BIG)) {
+          const R f = fabs(y) > R(0) && fabs(y) <= BIG * BIG ? R(1) / fabs(y) : R(0);
+          for (int t = s0; t < e0; ++t)
+            if (t != i) Z[(int64_t)t * n + c] *= f;
+          y = f > R(0) ? y * f : (y > R(0) ? R(1) : R(-1));
+          y1 *= f;
+          y2 *= f;
+          ymax *= f;
+        }
         Z[at] = y;
         y2 = y1;
         y1 = y;
@@ -1216,37 +1244,106 @@ __global__ void __launch_bounds__(512) k_eig_tri(Dev<R> d, int v, int w, int cap
     __syncthreads();
   }
 
-  // ---- 5. back-transformation: V_k = H_0 ... H_{n-3} D Z_k (n x k in Vk)
+  // ---- 5. back-transformation V_k = H_0 ... H_{n-3} D Z_k (n x k in Vk),
+  // TRI_NB reflectors at a time in compact WY form (Schreiber & Van Loan):
+  // H_j0 ... H_j1 = I - Vb Tb Vb^H, so Vk <- Vk - Vb (Tb (Vb^H Vk)).
   for (int idx = tid; idx < n * k; idx += nth) {
     const int x = idx / k, c = idx - x * k;
     const R z = Z[(int64_t)x * n + c];
     Vk[idx] = {wk[x].x * z, wk[x].y * z};
   }
+  cx<R>* Vb = reinterpret_cast<cx<R>*>(tau + 512);  // [TRI_NB][512] reflectors, by row
+  cx<R>* Wp = Vb + TRI_NB * 512;                      // [512 * TRI_NB] partial products
+  __shared__ cx<R> Tb[TRI_NB][TRI_NB], Sb[TRI_NB][TRI_NB];
   __syncthreads();
-  for (int kk = n - 3; kk >= 0; --kk) {
-    const R tk = tau[kk];
-    if (tk == R(0)) continue;  // uniform across the block
-    const int m = n - kk - 1;
-    for (int r = tid; r < m; r += nth) vk[r] = A[(int64_t)(kk + 1 + r) * n + kk];
-    __syncthreads();
-    const int G = nth / k, c = tid % k, g = tid / k;
-    if (g < G) {
-      cx<R> acc = {R(0), R(0)};
-      for (int r = g; r < m; r += G) acc = cadd(acc, cmulc(vk[r], Vk[(int64_t)(kk + 1 + r) * k + c]));
-      pp[g * k + c] = acc;
+  for (int jhi = n - 3; jhi >= 0; jhi -= TRI_NB) {
+    const int j0 = jhi - TRI_NB + 1 > 0 ? jhi - TRI_NB + 1 : 0, nbk = jhi - j0 + 1;
+    for (int idx = tid; idx < nbk * n; idx += nth) {
+      const int i = idx / n, r = idx - i * n, j = j0 + i;
+      Vb[i * 512 + r] = (r > j && tau[j] != R(0)) ? A[(int64_t)r * n + j] : cx<R>{R(0), R(0)};
     }
     __syncthreads();
-    if (tid < k) {
-      cx<R> acc = pp[tid];
-      for (int gg = 1; gg < G; ++gg) acc = cadd(acc, pp[gg * k + tid]);
-      pp[tid] = cscale(acc, tk);
+    if (tid < nbk * nbk) {  // Sb = Vb^H Vb (upper part)
+      const int l = tid / nbk, i = tid - l * nbk;
+      if (l < i) {
+        cx<R> acc = {R(0), R(0)};
+        for (int r = j0 + i + 1; r < n; ++r) acc = cadd(acc, cmulc(Vb[l * 512 + r], Vb[i * 512 + r]));
+        Sb[l][i] = acc;
+      }
     }
     __syncthreads();
-    for (int idx = tid; idx < m * k; idx += nth) {
-      const int r = idx / k, cc = idx - r * k;
-      cx<R>* vp = Vk + (int64_t)(kk + 1 + r) * k + cc;
-      const cx<R> t = cmul(vk[r], pp[cc]);
-      *vp = {vp->x - t.x, vp->y - t.y};
+    if (tid == 0) {  // forward recurrence for the triangular factor
+      for (int i = 0; i < nbk; ++i) {
+        const R ti = tau[j0 + i];
+        for (int l = 0; l < i; ++l) {
+          cx<R> acc = {R(0), R(0)};
+          for (int m2 = l; m2 < i; ++m2) acc = cadd(acc, cmul(Tb[l][m2], Sb[m2][i]));
+          Tb[l][i] = cscale(acc, -ti);
+        }
+        Tb[i][i] = {ti, R(0)};
+        for (int l = i + 1; l < nbk; ++l) Tb[l][i] = {R(0), R(0)};
+      }
+    }
+    __syncthreads();
+    {  // Wp = Vb^H Vk, partial sums over row groups
+      const int G = nth / k, c = tid % k, g = tid / k;
+      if (g < G) {
+        cx<R> acc[TRI_NB];
+#pragma unroll
+        for (int i = 0; i < TRI_NB; ++i) acc[i] = {R(0), R(0)};
+        for (int r = j0 + 1 + g; r < n; r += G) {
+          const cx<R> x = Vk[(int64_t)r * k + c];
+#pragma unroll
+          for (int i = 0; i < TRI_NB; ++i)
+            if (i < nbk) acc[i] = cadd(acc[i], cmulc(Vb[i * 512 + r], x));
+        }
+#pragma unroll
+        for (int i = 0; i < TRI_NB; ++i) Wp[(g * TRI_NB + i) * k + c] = acc[i];
+      }
+      __syncthreads();
+      if (tid < k) {  // reduce, then apply Tb
+        cx<R> wv[TRI_NB];
+#pragma unroll
+        for (int i = 0; i < TRI_NB; ++i) {
+          cx<R> acc = Wp[i * k + tid];
+          for (int gg = 1; gg < G; ++gg) acc = cadd(acc, Wp[(gg * TRI_NB + i) * k + tid]);
+          wv[i] = acc;
+        }
+#pragma unroll
+        for (int l = 0; l < TRI_NB; ++l) {
+          cx<R> acc = {R(0), R(0)};
+#pragma unroll
+          for (int i = 0; i < TRI_NB; ++i)
+            if (i >= l && i < nbk) acc = cadd(acc, cmul(Tb[l][i], wv[i]));
+          Wp[l * k + tid] = acc;
+        }
+      }
+      __syncthreads();
+    }
+    // Vk -= Vb Wp on rows j0+1..n-1 (loads of a batch issued before its stores)
+    const int rows = n - j0 - 1, tot = rows * k;
+    for (int base = tid; base < tot; base += nth * TRI_UNROLL) {
+      cx<R> x[TRI_UNROLL];
+#pragma unroll
+      for (int u = 0; u < TRI_UNROLL; ++u) {
+        const int idx = base + u * nth;
+        if (idx < tot) x[u] = Vk[(int64_t)(j0 + 1) * k + idx];
+      }
+#pragma unroll
+      for (int u = 0; u < TRI_UNROLL; ++u) {
+        const int idx = base + u * nth;
+        if (idx < tot) {
+          const int r = j0 + 1 + idx / k, c = idx % k;
+          cx<R> acc = x[u];
+#pragma unroll
+          for (int i = 0; i < TRI_NB; ++i)
+            if (i < nbk) {
+              const cx<R> t = cmul(Vb[i * 512 + r], Wp[i * k + c]);
+              acc = {acc.x - t.x, acc.y - t.y};
+            }
+          Vk[(int64_t)(j0 + 1) * k + idx] = acc;
+        }
+      }
     }
     __syncthreads();
   }
