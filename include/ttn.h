@@ -89,6 +89,13 @@ typedef struct {
                                       of Gram matrix, tridiagonal above,
                                     3 Gram matrix, tridiagonal eigensolver
                                       at every size                       */
+  int32_t gemm_mode;             /* FP32 contractions (Gram matrix, Y = M V,
+                                    neighbour absorb): 0 auto (tensor cores
+                                    on Gram-path moves), 1 FP32 FMA units,
+                                    2 tensor cores for every move.  Tensor
+                                    cores use TF32 with a 3-term split
+                                    (FP32-level accuracy).  FP64 runs ignore
+                                    it.                                   */
 } ttn_run_params;
 
 typedef struct ttn_circuit ttn_circuit;  /* opaque, library-owned */

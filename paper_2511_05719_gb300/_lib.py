@@ -28,7 +28,7 @@ class RunParams(ctypes.Structure):
                 ("chi", ctypes.c_int32), ("precision", ctypes.c_int32), ("seed", ctypes.c_uint64),
                 ("first_traj", ctypes.c_uint64), ("svd_eps", ctypes.c_double),
                 ("theta_per_traj", c_dblp), ("gamma_per_traj", c_dblp),
-                ("svd_mode", ctypes.c_int32)]
+                ("svd_mode", ctypes.c_int32), ("gemm_mode", ctypes.c_int32)]
 
 
 class TTNError(RuntimeError):
@@ -147,10 +147,11 @@ class Circuit:
 
 
 SVD_MODE = {"auto": 0, "jacobi": 1, "gram": 2, "gram_tri": 3}
+GEMM_MODE = {"auto": 0, "fma": 1, "tensor": 2}
 
 
 def _run_params(noise, theta, gamma, chi, precision, seed, first_traj, svd_eps,
-                theta_per_traj=None, gamma_per_traj=None, svd_mode="auto"):
+                theta_per_traj=None, gamma_per_traj=None, svd_mode="auto", gemm_mode="auto"):
     p = RunParams()
     p.noise = NOISE[noise] if isinstance(noise, str) else int(noise)
     p.theta = float(theta)
@@ -161,6 +162,7 @@ def _run_params(noise, theta, gamma, chi, precision, seed, first_traj, svd_eps,
     p.first_traj = int(first_traj)
     p.svd_eps = float(svd_eps)
     p.svd_mode = SVD_MODE[svd_mode] if isinstance(svd_mode, str) else int(svd_mode)
+    p.gemm_mode = GEMM_MODE[gemm_mode] if isinstance(gemm_mode, str) else int(gemm_mode)
     keep = []
     if theta_per_traj is not None:
         a = np.ascontiguousarray(theta_per_traj, dtype=np.float64)
@@ -176,14 +178,14 @@ def _run_params(noise, theta, gamma, chi, precision, seed, first_traj, svd_eps,
 def run_trajectories(circuit, n_traj, noise="srx", theta=0.0, gamma=0.0, chi=16,
                      precision="fp64", seed=0, first_traj=0, svd_eps=0.0,
                      theta_per_traj=None, gamma_per_traj=None, out=None, stream=None,
-                     svd_mode="auto"):
+                     svd_mode="auto", gemm_mode="auto"):
     """Runs n_traj trajectories.  With `out=None` returns host numpy arrays
     {records, fail, log_prob, discarded, near_ties}.  With `out` a dict of
     torch CUDA tensors (any subset of those keys) and `stream` a CUDA stream
     handle (int), writes them on the device."""
     lib = load_library()
     p, keep = _run_params(noise, theta, gamma, chi, precision, seed, first_traj, svd_eps,
-                          theta_per_traj, gamma_per_traj, svd_mode)
+                          theta_per_traj, gamma_per_traj, svd_mode, gemm_mode)
     if out is None:
         out = dict(records=np.zeros((n_traj, circuit.n_record_bits), dtype=np.uint8),
                    fail=np.zeros(n_traj, dtype=np.uint8),
@@ -203,10 +205,11 @@ def run_trajectories(circuit, n_traj, noise="srx", theta=0.0, gamma=0.0, chi=16,
 
 
 def logical_error_rate(circuit, shots, noise="srx", theta=0.0, gamma=0.0, chi=16,
-                       precision="fp64", seed=0, first_traj=0, svd_eps=0.0, svd_mode="auto"):
+                       precision="fp64", seed=0, first_traj=0, svd_eps=0.0, svd_mode="auto",
+                       gemm_mode="auto"):
     lib = load_library()
     p, keep = _run_params(noise, theta, gamma, chi, precision, seed, first_traj, svd_eps,
-                          svd_mode=svd_mode)
+                          svd_mode=svd_mode, gemm_mode=gemm_mode)
     pl, sg, nf = ctypes.c_double(), ctypes.c_double(), ctypes.c_uint64()
     _check(lib.ttn_logical_error_rate(circuit.handle, ctypes.byref(p), shots, ctypes.byref(pl),
                                       ctypes.byref(sg), ctypes.byref(nf)))
@@ -226,10 +229,10 @@ def decode(circuit, records):
 
 
 def debug_state(circuit, traj, layer, noise="srx", theta=0.0, gamma=0.0, chi=16,
-                precision="fp64", seed=0, svd_eps=0.0, svd_mode="auto"):
+                precision="fp64", seed=0, svd_eps=0.0, svd_mode="auto", gemm_mode="auto"):
     lib = load_library()
     p, keep = _run_params(noise, theta, gamma, chi, precision, seed, 0, svd_eps,
-                          svd_mode=svd_mode)
+                          svd_mode=svd_mode, gemm_mode=gemm_mode)
     amps = np.zeros(2 * (1 << circuit.n_qubits))
     _check(lib.ttn_debug_state(circuit.handle, ctypes.byref(p), traj, layer,
                                amps.ctypes.data_as(c_dblp)))
@@ -268,11 +271,12 @@ def profile_end():
 
 
 def grad(circuit, shots, wrt="theta", noise="srx", theta=0.0, gamma=0.0, chi=16, precision="fp64",
-         seed=0, first_traj=0, h=1e-4, svd_eps=0.0, svd_mode="auto", return_score=False):
+         seed=0, first_traj=0, h=1e-4, svd_eps=0.0, svd_mode="auto", gemm_mode="auto",
+         return_score=False):
     """Score-function estimate of dp_L/d(theta or gamma): (p_L, dpL, sigma[, score])."""
     lib = load_library()
     p, keep = _run_params(noise, theta, gamma, chi, precision, seed, first_traj, svd_eps,
-                          svd_mode=svd_mode)
+                          svd_mode=svd_mode, gemm_mode=gemm_mode)
     pl, g, sg = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
     score = np.zeros(shots) if return_score else None
     _check(lib.ttn_grad(circuit.handle, ctypes.byref(p), shots, 0 if wrt == "theta" else 1, h,

@@ -134,6 +134,7 @@ static ttn_status check_params(const ttn_circuit* c, const ttn_run_params* p) {
   if (!std::isfinite(p->theta)) return fail_with(TTN_EINVAL, "theta must be finite");
   if (!(p->gamma >= 0.0 && p->gamma <= 1.0)) return fail_with(TTN_EINVAL, "gamma must be in [0, 1]");
   if (p->svd_mode < 0 || p->svd_mode > 3) return fail_with(TTN_EINVAL, "svd_mode must be 0, 1, 2 or 3");
+  if (p->gemm_mode < 0 || p->gemm_mode > 2) return fail_with(TTN_EINVAL, "gemm_mode must be 0, 1 or 2");
   return TTN_OK;
 }
 
@@ -152,6 +153,7 @@ static RunRequest make_request(const ttn_run_params* p, uint64_t n_traj, void* s
   rq.gamma_per_traj = p->gamma_per_traj;
   rq.stream = stream;
   rq.svd_mode = p->svd_mode;
+  rq.gemm_mode = p->gemm_mode;
   return rq;
 }
 

@@ -407,87 +407,6 @@ __global__ void __launch_bounds__(256) k_svd_move(Dev<R> d, int v, int w, int ca
   }
 }
 
-// Neighbour w absorbs R (k x n) on its leg towards v:
-//   out[o][i][u] = sum_x R[i][x] in[o][x][u]   (o, u: the other legs)
-// written to the workspace W (then copied back).
-template <typename R>
-__global__ void __launch_bounds__(256) k_absorb(Dev<R> d, int w, int v) {
-  const int b = blockIdx.z;
-  const int* D = d.dims + b * d.ds;
-  const int lw = (v == 2 * w) ? 0 : ((v == 2 * w + 1) ? 1 : 2);
-  const int dl = D[2 * w], dr = D[2 * w + 1], du = D[w];
-  const int n = d.nold[b], k = d.knew[b];
-  int outer, inner;
-  if (lw == 0) {
-    outer = 1;
-    inner = dr * du;
-  } else if (lw == 1) {
-    outer = dl;
-    inner = du;
-  } else {
-    outer = dl * dr;
-    inner = 1;
-  }
-  const int J = outer * inner;
-  const int i0 = blockIdx.y * 64, j0 = blockIdx.x * 64;
-  if (k <= 0 || (int64_t)k * J > d.wstride || (int64_t)n * J > d.wstride) return;
-  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0)
-    ledger_add(d.ledger, KC_ABSORB, 8.0 * k * (double)n * J,
-               sizeof(cx<R>) * ((double)n * J + (double)k * n + (double)k * J));
-  if (i0 >= k || j0 >= J) return;
-  const cx<R>* Rm = d.Rm + (int64_t)b * d.vstride;
-  const cx<R>* in = node_ptr(d, b, w);
-  cx<R>* out = d.W + (int64_t)b * d.wstride;
-  __shared__ cx<R> As[16][64];
-  __shared__ cx<R> Bs[16][64];
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  cx<R> acc[4][4];
-#pragma unroll
-  for (int a = 0; a < 4; ++a)
-#pragma unroll
-    for (int c = 0; c < 4; ++c) acc[a][c] = {R(0), R(0)};
-  for (int x0 = 0; x0 < n; x0 += 16) {
-    for (int e = threadIdx.x; e < 16 * 64; e += 256) {
-      int xx = e / 64, ii = e % 64;
-      int i = i0 + ii, x = x0 + xx;
-      As[xx][ii] = (i < k && x < n) ? Rm[(int64_t)i * n + x] : cx<R>{R(0), R(0)};
-      int j = j0 + ii;
-      cx<R> bv = {R(0), R(0)};
-      if (j < J && x < n) {
-        int o = j / inner, u = j - o * inner;
-        bv = in[((int64_t)o * n + x) * inner + u];
-      }
-      Bs[xx][ii] = bv;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int xx = 0; xx < 16; ++xx) {
-      cx<R> av[4], bv[4];
-#pragma unroll
-      for (int a = 0; a < 4; ++a) av[a] = As[xx][ty * 4 + a];
-#pragma unroll
-      for (int c = 0; c < 4; ++c) bv[c] = Bs[xx][tx * 4 + c];
-#pragma unroll
-      for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int c = 0; c < 4; ++c) acc[a][c] = cadd(acc[a][c], cmul(av[a], bv[c]));
-    }
-    __syncthreads();
-  }
-#pragma unroll
-  for (int a = 0; a < 4; ++a) {
-    int i = i0 + ty * 4 + a;
-    if (i >= k) continue;
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      int j = j0 + tx * 4 + c;
-      if (j >= J) continue;
-      int o = j / inner, u = j - o * inner;
-      out[((int64_t)o * k + i) * inner + u] = acc[a][c];
-    }
-  }
-}
-
 // Copy the workspace back into node v (count from its current dims).
 template <typename R>
 __global__ void k_copy_back(Dev<R> d, int v) {
@@ -576,6 +495,220 @@ __device__ __forceinline__ void tile_gemm64(int Mr, int Nc, int K, int i0, int j
   }
 }
 
+// ------------------------------------------------------------------ tensor-core tile
+// 64 x 64 output tile of C = A B (complex FP32) on the tensor cores:
+// mma.sync m16n8k8 with TF32 operands and FP32 accumulation, each FP32
+// operand split as x = hi + lo (hi = tf32(x), lo = tf32(x - hi)) and the
+// product formed as hi*hi + hi*lo + lo*hi ("3xTF32"), which keeps FP32-level
+// accuracy.  The complex product takes four real products (Ar Br - Ai Bi,
+// Ar Bi + Ai Br).  Same operand / output functors as tile_gemm64; the next
+// K-chunk's global loads are issued before the current chunk's MMAs.
+__device__ __forceinline__ uint32_t tf32_bits(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+__device__ __forceinline__ void mma_tf32_16x8x8(float (&c)[4], const uint32_t (&a)[4], uint32_t b0,
+                                                uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+static constexpr int TC_KT = 16;          // K per shared-memory chunk
+static constexpr int TC_AST = TC_KT + 4;  // A row stride (words): conflict-free fragment loads
+static constexpr int TC_BST = 64 + 8;     // B row stride (words)
+
+template <bool A_KFAST, typename FA, typename FB, typename FC>
+__device__ __forceinline__ void tc_tile_gemm64(int Mr, int Nc, int K, int i0, int j0, FA fa, FB fb,
+                                               FC fc) {
+  // planes: 0 re-hi, 1 re-lo, 2 im-hi, 3 im-lo
+  __shared__ uint32_t As[4][64 * TC_AST];
+  __shared__ uint32_t Bs[4][TC_KT * TC_BST];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int g = lane >> 2, t = lane & 3;
+  const int wm = warp & 1, wn = warp >> 1;  // warp tile: rows wm*32.., cols wn*16..
+  float accr[2][2][4], acci[2][2][4];
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 2; ++b)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) accr[a][b][e] = acci[a][b][e] = 0.f;
+  cx<float> ra[4], rb[4];  // this thread's elements of the next chunk
+  auto fetch = [&](int k0) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int e = tid + q * 256;
+      int kk, ii;
+      if (A_KFAST) {
+        kk = e & 15;
+        ii = e >> 4;
+      } else {
+        kk = e >> 6;
+        ii = e & 63;
+      }
+      const int i = i0 + ii, k = k0 + kk;
+      ra[q] = (i < Mr && k < K) ? fa(i, k) : cx<float>{0.f, 0.f};
+      const int kb = e >> 6, jb = e & 63;
+      const int j = j0 + jb, k2 = k0 + kb;
+      rb[q] = (j < Nc && k2 < K) ? fb(k2, j) : cx<float>{0.f, 0.f};
+    }
+  };
+  auto stash = [&]() {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int e = tid + q * 256;
+      int kk, ii;
+      if (A_KFAST) {
+        kk = e & 15;
+        ii = e >> 4;
+      } else {
+        kk = e >> 6;
+        ii = e & 63;
+      }
+      const uint32_t rh = tf32_bits(ra[q].x), ih = tf32_bits(ra[q].y);
+      const int ao = ii * TC_AST + kk;
+      As[0][ao] = rh;
+      As[1][ao] = tf32_bits(ra[q].x - __uint_as_float(rh));
+      As[2][ao] = ih;
+      As[3][ao] = tf32_bits(ra[q].y - __uint_as_float(ih));
+      const int kb = e >> 6, jb = e & 63;
+      const uint32_t brh = tf32_bits(rb[q].x), bih = tf32_bits(rb[q].y);
+      const int bo = kb * TC_BST + jb;
+      Bs[0][bo] = brh;
+      Bs[1][bo] = tf32_bits(rb[q].x - __uint_as_float(brh));
+      Bs[2][bo] = bih;
+      Bs[3][bo] = tf32_bits(rb[q].y - __uint_as_float(bih));
+    }
+  };
+  if (K > 0) fetch(0);
+  for (int k0 = 0; k0 < K; k0 += TC_KT) {
+    stash();
+    __syncthreads();
+    if (k0 + TC_KT < K) fetch(k0 + TC_KT);
+#pragma unroll
+    for (int ks = 0; ks < TC_KT; ks += 8) {
+      uint32_t af[2][4][4];  // [m-tile][plane][reg]
+#pragma unroll
+      for (int mt = 0; mt < 2; ++mt) {
+        const int r = wm * 32 + mt * 16 + g;
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+          af[mt][p][0] = As[p][r * TC_AST + ks + t];
+          af[mt][p][1] = As[p][(r + 8) * TC_AST + ks + t];
+          af[mt][p][2] = As[p][r * TC_AST + ks + t + 4];
+          af[mt][p][3] = As[p][(r + 8) * TC_AST + ks + t + 4];
+        }
+      }
+      uint32_t bf[2][4][2];  // [n-tile][plane][reg]
+#pragma unroll
+      for (int nt = 0; nt < 2; ++nt) {
+        const int cc = wn * 16 + nt * 8 + g;
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+          bf[nt][p][0] = Bs[p][(ks + t) * TC_BST + cc];
+          bf[nt][p][1] = Bs[p][(ks + t + 4) * TC_BST + cc];
+        }
+      }
+#pragma unroll
+      for (int mt = 0; mt < 2; ++mt) {
+        uint32_t nah[4], nal[4];  // -Ai (hi, lo): sign bit flipped
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          nah[e] = af[mt][2][e] ^ 0x80000000u;
+          nal[e] = af[mt][3][e] ^ 0x80000000u;
+        }
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt) {
+          float(&cr)[4] = accr[mt][nt];
+          float(&ci)[4] = acci[mt][nt];
+          // small cross terms first
+          mma_tf32_16x8x8(cr, af[mt][1], bf[nt][0][0], bf[nt][0][1]);
+          mma_tf32_16x8x8(cr, af[mt][0], bf[nt][1][0], bf[nt][1][1]);
+          mma_tf32_16x8x8(cr, nal, bf[nt][2][0], bf[nt][2][1]);
+          mma_tf32_16x8x8(cr, nah, bf[nt][3][0], bf[nt][3][1]);
+          mma_tf32_16x8x8(cr, af[mt][0], bf[nt][0][0], bf[nt][0][1]);
+          mma_tf32_16x8x8(cr, nah, bf[nt][2][0], bf[nt][2][1]);
+          mma_tf32_16x8x8(ci, af[mt][1], bf[nt][2][0], bf[nt][2][1]);
+          mma_tf32_16x8x8(ci, af[mt][0], bf[nt][3][0], bf[nt][3][1]);
+          mma_tf32_16x8x8(ci, af[mt][3], bf[nt][0][0], bf[nt][0][1]);
+          mma_tf32_16x8x8(ci, af[mt][2], bf[nt][1][0], bf[nt][1][1]);
+          mma_tf32_16x8x8(ci, af[mt][0], bf[nt][2][0], bf[nt][2][1]);
+          mma_tf32_16x8x8(ci, af[mt][2], bf[nt][0][0], bf[nt][0][1]);
+        }
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int i = i0 + wm * 32 + mt * 16 + g + (e >> 1) * 8;
+        const int j = j0 + wn * 16 + nt * 8 + 2 * t + (e & 1);
+        if (i < Mr && j < Nc) fc(i, j, cx<float>{accr[mt][nt][e], acci[mt][nt][e]});
+      }
+}
+
+// C = A B tile on the tensor cores (TC, FP32 only) or on the FP32/FP64 FMA units.
+template <typename R, bool TC, bool A_KFAST, typename FA, typename FB, typename FC>
+__device__ __forceinline__ void gemm_tile64(int Mr, int Nc, int K, int i0, int j0, FA fa, FB fb, FC fc) {
+  if constexpr (TC && sizeof(R) == 4) {
+    tc_tile_gemm64<A_KFAST>(Mr, Nc, K, i0, j0, fa, fb, fc);
+  } else {
+    tile_gemm64<R, A_KFAST>(Mr, Nc, K, i0, j0, fa, fb, fc);
+  }
+}
+
+// Neighbour w absorbs R (k x n) on its leg towards v:
+//   out[o][i][u] = sum_x R[i][x] in[o][x][u]   (o, u: the other legs)
+// written to the workspace W (then copied back).
+template <typename R, bool TC>
+__global__ void __launch_bounds__(256) k_absorb(Dev<R> d, int w, int v) {
+  const int b = blockIdx.z;
+  const int* D = d.dims + b * d.ds;
+  const int lw = (v == 2 * w) ? 0 : ((v == 2 * w + 1) ? 1 : 2);
+  const int dl = D[2 * w], dr = D[2 * w + 1], du = D[w];
+  const int n = d.nold[b], k = d.knew[b];
+  int outer, inner;
+  if (lw == 0) {
+    outer = 1;
+    inner = dr * du;
+  } else if (lw == 1) {
+    outer = dl;
+    inner = du;
+  } else {
+    outer = dl * dr;
+    inner = 1;
+  }
+  const int J = outer * inner;
+  const int i0 = blockIdx.y * 64, j0 = blockIdx.x * 64;
+  if (k <= 0 || (int64_t)k * J > d.wstride || (int64_t)n * J > d.wstride) return;
+  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0)
+    ledger_add(d.ledger, KC_ABSORB, 8.0 * k * (double)n * J,
+               sizeof(cx<R>) * ((double)n * J + (double)k * n + (double)k * J));
+  if (i0 >= k || j0 >= J) return;
+  const cx<R>* Rm = d.Rm + (int64_t)b * d.vstride;
+  const cx<R>* in = node_ptr(d, b, w);
+  cx<R>* out = d.W + (int64_t)b * d.wstride;
+  gemm_tile64<R, TC, true>(
+      k, J, n, i0, j0, [&](int i, int x) { return Rm[(int64_t)i * n + x]; },
+      [&](int x, int j) {
+        const int o = j / inner, u = j - o * inner;
+        return in[((int64_t)o * n + x) * inner + u];
+      },
+      [&](int i, int j, cx<R> val) {
+        const int o = j / inner, u = j - o * inner;
+        out[((int64_t)o * k + i) * inner + u] = val;
+      });
+}
+
 // M (m x n, row-major) into the workspace.
 template <typename R>
 __global__ void k_gather_rows(Dev<R> d, int v, int w) {
@@ -595,7 +728,7 @@ __global__ void k_gather_rows(Dev<R> d, int v, int w) {
 }
 
 // G = M^H M (n x n)
-template <typename R>
+template <typename R, bool TC>
 __global__ void __launch_bounds__(256) k_gram(Dev<R> d, int v, int w) {
   const int b = blockIdx.z;
   const int* D = d.dims + b * d.ds;
@@ -611,7 +744,7 @@ __global__ void __launch_bounds__(256) k_gram(Dev<R> d, int v, int w) {
   if (i0 >= n || j0 >= n) return;
   const cx<R>* Mw = d.W + (int64_t)b * d.wstride;
   cx<R>* G = d.G + (int64_t)b * d.vstride;
-  tile_gemm64<R, false>(
+  gemm_tile64<R, TC, false>(
       n, n, m, i0, j0,
       [&](int i, int k) {
         cx<R> x = Mw[(int64_t)k * n + i];
@@ -1412,7 +1545,7 @@ __global__ void __launch_bounds__(256) k_unorm(Dev<R> d, int v, int w) {
 }
 
 // Y = M V_k: m x k, written into T_v with bond dimension k.
-template <typename R>
+template <typename R, bool TC>
 __global__ void __launch_bounds__(256) k_form_u(Dev<R> d, int v, int w) {
   const int b = blockIdx.z;
   const int* D = d.dims + b * d.ds;
@@ -1432,7 +1565,7 @@ __global__ void __launch_bounds__(256) k_form_u(Dev<R> d, int v, int w) {
   const cx<R>* Mw = d.W + (int64_t)b * d.wstride;
   const cx<R>* Vs = d.G + (int64_t)b * d.vstride;  // V_k
   cx<R>* T = node_ptr(d, b, v);
-  tile_gemm64<R, true>(
+  gemm_tile64<R, TC, true>(
       m, k, n, i0, j0, [&](int i, int kk) { return Mw[(int64_t)i * n + kk]; },
       [&](int kk, int j) { return Vs[(int64_t)kk * k + j]; },
       [&](int i, int c, cx<R> val) {
@@ -1872,6 +2005,7 @@ struct Engine {
   const ttn_circuit& c;
   const Program& prog;
   int chi, noise, B;
+  int gemm_mode = 0;               // 0 auto, 1 FMA units, 2 tensor cores (FP32)
   cudaStream_t st;
   std::vector<int> bcap;           // bond caps (outside gates)
   std::vector<int64_t> ncap;       // node slot capacity (elements)
@@ -2089,6 +2223,8 @@ struct Engine {
           const int bond = (w == v / 2) ? v : w;
           const int64_t nmv = 2 * (int64_t)bcap[bond];
           const bool gram = dev.svd_mode >= 2 || (dev.svd_mode == 0 && sizeof(R) == 4 && nmv > 64);
+          // contractions of this move on the tensor cores (FP32 only)
+          const bool tc = sizeof(R) == 4 && (gemm_mode == 2 || (gemm_mode == 0 && gram));
           if (gram) {
             const int lv = (w == 2 * v) ? 0 : ((w == 2 * v + 1) ? 1 : 2);
             int64_t c3[3] = {2 * (int64_t)bcap[2 * v], 2 * (int64_t)bcap[2 * v + 1],
@@ -2098,14 +2234,21 @@ struct Engine {
               if (t != lv) mmax *= c3[t];
             timed(KC_COPY, [&] { k_gather_rows<R><<<dim3(std::max(1, ceil_div(ncap[v], 1024)), nb), 256, 0, st>>>(dev, v, w); });
             const int tn = std::max(1, ceil_div(nmv, 64));
-            timed(KC_GRAM, [&] { k_gram<R><<<dim3(tn, tn, nb), 256, 0, st>>>(dev, v, w); });
+            timed(KC_GRAM, [&] {
+              if (tc) k_gram<R, true><<<dim3(tn, tn, nb), 256, 0, st>>>(dev, v, w);
+              else k_gram<R, false><<<dim3(tn, tn, nb), 256, 0, st>>>(dev, v, w);
+            });
             if (dev.svd_mode != 3 && nmv * nmv * (int64_t)sizeof(cx<R>) <= EIG_SMEM_MAX) {
               dev.eig_smem_bytes = (int)(nmv * nmv * (int64_t)sizeof(cx<R>));
               timed(KC_EIG, [&] { k_eig<R><<<nb, 512, dev.eig_smem_bytes, st>>>(dev, v, w, s.c); });
             } else {
               timed(KC_EIG, [&] { k_eig_tri<R><<<nb, 512, tri_smem_bytes<R>(), st>>>(dev, v, w, s.c); });
             }
-            timed(KC_FORMU, [&] { k_form_u<R><<<dim3(std::max(1, ceil_div(mmax, 64)), tn, nb), 256, 0, st>>>(dev, v, w); });
+            timed(KC_FORMU, [&] {
+              const dim3 gf(std::max(1, ceil_div(mmax, 64)), tn, nb);
+              if (tc) k_form_u<R, true><<<gf, 256, 0, st>>>(dev, v, w);
+              else k_form_u<R, false><<<gf, 256, 0, st>>>(dev, v, w);
+            });
             timed(KC_OTHER, [&] { k_unorm<R><<<nb, 256, 0, st>>>(dev, v, w); });
           } else {
             timed(KC_SVD, [&] { k_svd_move<R><<<nb, 256, 0, st>>>(dev, v, w, s.c); });
@@ -2118,7 +2261,10 @@ struct Engine {
           int64_t Jmax = ncap[w] * 2 / std::max<int64_t>(1, kmax);
           Jmax = std::min<int64_t>(Jmax, (lw == 0 ? cr * cu : (lw == 1 ? cl * cu : cl * cr)));
           dim3 ga(std::max(1, ceil_div(Jmax, 64)), std::max(1, ceil_div(kmax, 64)), nb);
-          timed(KC_ABSORB, [&] { k_absorb<R><<<ga, 256, 0, st>>>(dev, w, v); });
+          timed(KC_ABSORB, [&] {
+            if (tc) k_absorb<R, true><<<ga, 256, 0, st>>>(dev, w, v);
+            else k_absorb<R, false><<<ga, 256, 0, st>>>(dev, w, v);
+          });
           timed(KC_COPY, [&] { k_copy_back<R><<<dim3(std::max(1, ceil_div(ncap[w], 256 * 4)), nb), 256, 0, st>>>(dev, w); });
           break;
         }
@@ -2178,6 +2324,7 @@ static ttn_status run_impl(const ttn_circuit& c, const RunRequest& rq, RunOutput
   eng.dev.tol = sizeof(R) == 8 ? 1e-15 : 1e-7;
   eng.dev.max_sweeps = sizeof(R) == 8 ? 40 : 30;
   eng.dev.svd_mode = rq.svd_mode;
+  eng.gemm_mode = rq.gemm_mode;
   eng.dev.eig_smem_bytes = 0;
   CK(cudaFuncSetAttribute(k_eig<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, EIG_SMEM_MAX));
   CK(cudaFuncSetAttribute(k_eig_tri<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, tri_smem_bytes<R>()));

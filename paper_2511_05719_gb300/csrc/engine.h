@@ -19,7 +19,8 @@ struct RunRequest {
   void* stream = nullptr;
   size_t max_device_bytes = 0;   // 0: 80% of free device memory
   int max_batch = 0;             // 0: as many as fit
-  int svd_mode = 0;              // 0 auto, 1 one-sided Jacobi on M, 2 Gram matrix
+  int svd_mode = 0;              // 0 auto, 1 one-sided Jacobi on M, 2/3 Gram matrix
+  int gemm_mode = 0;             // 0 auto, 1 FMA units, 2 tensor cores for FP32 contractions
   int grad_wrt = -1;             // -1 none, 0 theta, 1 gamma: replay for the score
   double grad_h = 1e-4;          // replay step
 };

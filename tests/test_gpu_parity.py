@@ -256,3 +256,28 @@ def test_decoder_dense_syndromes_blossom_path():
         for i in range(n):
             f, col, s = DEC.decode(G, recs[i])
             assert (fail[i], color[i], score[i]) == (f, col, s), (d, C, i)
+
+
+TC_TOL = {"fp32": 2e-5}
+
+
+@pytest.mark.parametrize("svd_mode", ["jacobi", "gram"])
+@pytest.mark.parametrize("noise", ["srx", "ad", "srx_ad"])
+def test_tensor_core_contractions_amplitudes(noise, svd_mode):
+    """Every FP32 contraction on the tensor cores (3xTF32): amplitudes against
+    the statevector oracle through both rounds."""
+    circ = build_circuit(3, 2)
+    th, ga = STRENGTH[noise]
+    c = P.Circuit(3, 2, layout="optimized")
+    tol = TC_TOL["fp32"] if svd_mode == "jacobi" else GRAM_TOL["fp32"]
+    for traj in (0, 5):
+        layers = [4, 13, 20, circ.n_layers - 1]
+        ref = SV.run_trajectory(circ, MODELS[noise], th, ga, W.BASE_SEED, traj, snapshot_layers=layers)
+        if ref["margin"] < 1e-3:
+            continue
+        for L in layers:
+            amp = P.debug_state(c, traj, L, noise=noise, theta=th, gamma=ga, chi=64, precision="fp32",
+                                seed=W.BASE_SEED, svd_mode=svd_mode, gemm_mode="tensor")
+            want = ref["states"][L]
+            err = np.linalg.norm(amp - want) / np.linalg.norm(want)
+            assert err < tol, (noise, svd_mode, traj, L, err)
