@@ -161,6 +161,26 @@ ttn_status ttn_grad(const ttn_circuit* circuit, const ttn_run_params* params, ui
 ttn_status ttn_decode(const ttn_circuit* circuit, uint64_t n, const uint8_t* records,
                       uint8_t* fail, int32_t* color, int64_t* score, void* cuda_stream);
 
+/* Allocation-free variant of ttn_decode.  The paper has no counterpart: it
+ * serves callers that cannot allocate device memory -- an application whose
+ * memory pool or caching allocator already owns the GPU, a framework whose
+ * allocator hooks forbid direct driver allocations, or code that must avoid
+ * the device-wide synchronisation cudaMalloc / cudaFree may imply.  It calls
+ * no cudaMalloc, cudaFree or other allocating routine: the decoder tables and
+ * per-shot scratch live in static device arrays of about 2 MB that every GPU
+ * loading the library holds until exit.  records [n][n_record_bits], fail
+ * [n], color [n], score [n] are always DEVICE pointers, ordered on
+ * cuda_stream (NULL = the default stream; color/score may be NULL); the call
+ * synchronises that stream before returning.  Results equal ttn_decode's.
+ * Limits: (rounds + 1) * #faces + 1 <= 145 detector nodes (EINVAL beyond
+ * that, e.g. d = 7 with more than 7 rounds); any number of shots.  The first
+ * call on a device resolves the static arrays' device addresses: make it
+ * before any stream capture.  The first call with a circuit packs its decoder
+ * tables into host memory kept with the circuit.  All calls share the static
+ * arrays, so calls that overlap on the GPU race; order them on one stream. */
+ttn_status ttn_decode_noalloc(const ttn_circuit* circuit, uint64_t n, const uint8_t* records,
+                              uint8_t* fail, int32_t* color, int64_t* score, void* cuda_stream);
+
 /* Runs one trajectory through the end of `layer` (0-based; -1 = before the
  * first op) and writes its 2^N amplitudes, little-endian in the qubit index
  * (qubit q = bit q), as interleaved (re, im) doubles.  N <= 24, at most 16

@@ -9,5 +9,5 @@ raises if it is missing.
 from ._lib import (  # noqa: F401
     NOISE, PRECISION, LAYOUT, TTNError, Circuit, run_trajectories, logical_error_rate,
     decode, debug_state, philox_uniforms, load_library, library_path,
-    profile_begin, profile_end, KERNEL_CLASSES, grad, logical_error_rate_fn,
+    profile_begin, profile_end, KERNEL_CLASSES, grad, logical_error_rate_fn, decode_noalloc,
 )

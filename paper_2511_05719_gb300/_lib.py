@@ -40,7 +40,7 @@ class TTNError(RuntimeError):
 EXPORTS = ["ttn_build_circuit", "ttn_free_circuit", "ttn_circuit_info", "ttn_circuit_ops",
            "ttn_circuit_layout", "ttn_run_trajectories", "ttn_logical_error_rate", "ttn_decode",
            "ttn_debug_state", "ttn_philox_uniforms", "ttn_profile_begin", "ttn_profile_end",
-           "ttn_grad",
+           "ttn_grad", "ttn_decode_noalloc",
            "ttn_status_string", "ttn_last_error"]
 
 
@@ -68,6 +68,7 @@ def load_library():
     lib.ttn_logical_error_rate.argtypes = [vp, ctypes.POINTER(RunParams), ctypes.c_uint64, c_dblp,
                                            c_dblp, c_u64p]
     lib.ttn_decode.argtypes = [vp, ctypes.c_uint64, vp, vp, vp, vp, vp]
+    lib.ttn_decode_noalloc.argtypes = [vp, ctypes.c_uint64, vp, vp, vp, vp, vp]
     lib.ttn_debug_state.argtypes = [vp, ctypes.POINTER(RunParams), ctypes.c_uint64, ctypes.c_int32,
                                     c_dblp]
     lib.ttn_philox_uniforms.argtypes = [ctypes.c_uint64, c_u64p, ctypes.c_uint64, c_i32p,
@@ -304,3 +305,15 @@ def logical_error_rate_fn(circuit, shots, **kw):
             return gout * ctx.g
 
     return _PL.apply
+
+
+def decode_noalloc(circuit, records, fail, color=None, score=None, stream=None):
+    """Allocation-free decoding of records already on the device (torch CUDA
+    tensors: records uint8 [n][n_record_bits], fail uint8 [n], color int32 [n],
+    score int64 [n]).  The library decodes with static device scratch and
+    calls no cudaMalloc, for callers whose memory pool owns the device.
+    `stream` is a CUDA stream handle (int); 0 or None = the default stream."""
+    n = int(records.shape[0])
+    st = ctypes.c_void_p(int(stream)) if stream else None
+    _check(load_library().ttn_decode_noalloc(circuit.handle, n, _ptr(records), _ptr(fail),
+                                             _ptr(color), _ptr(score), st))

@@ -50,7 +50,7 @@ struct BlossomState {
   int nfree, qh, qt;
 };
 
-BL_HD inline size_t bl_scratch_bytes(int n) {
+BL_HD constexpr size_t bl_scratch_bytes(int n) {
   return (size_t)2 * n * sizeof(int64_t) + (size_t)3 * n * sizeof(int16_t) +
          (size_t)15 * 2 * n * sizeof(int16_t);
 }
@@ -614,7 +614,7 @@ struct BoundaryWeights {
   }
 };
 
-BL_HD inline size_t boundary_matching_scratch_bytes(int k) { return bl_scratch_bytes(2 * k); }
+BL_HD constexpr size_t boundary_matching_scratch_bytes(int k) { return bl_scratch_bytes(2 * k); }
 
 // Minimum-weight matching of k defects, each paired with another defect
 // (wp(i, j) >= 0; negative = no such pair) or sent to the boundary

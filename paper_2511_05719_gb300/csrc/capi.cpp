@@ -271,6 +271,13 @@ ttn_status ttn_decode(const ttn_circuit* c, uint64_t n, const uint8_t* records, 
   return s;
 }
 
+ttn_status ttn_decode_noalloc(const ttn_circuit* c, uint64_t n, const uint8_t* records, uint8_t* fail,
+                              int32_t* color, int64_t* score, void* cuda_stream) {
+  if (!c || !records || !fail) return fail_with(TTN_EINVAL, "null argument");
+  if (n == 0) return TTN_OK;
+  return decode_noalloc(*c, n, records, fail, color, score, cuda_stream);
+}
+
 ttn_status ttn_debug_state(const ttn_circuit* c, const ttn_run_params* p, uint64_t traj,
                            int32_t layer, double* amps) {
   ttn_status s = check_params(c, p);

@@ -35,6 +35,7 @@
 #include <algorithm>
 #include <deque>
 #include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -726,6 +727,220 @@ ttn_status decode_device(const ttn_circuit& c, int nb, const uint8_t* d_records,
   cleanup();
   if (e != cudaSuccess) {
     set_error(std::string("CUDA: decode: ") + cudaGetErrorString(e));
+    return TTN_ECUDA;
+  }
+  if (ovf[0] > 0) {
+    set_error("decoder: " + std::to_string(ovf[0]) + " shot(s) exceed " + std::to_string(KMAX) +
+              " defects per matching instance (fail byte set to 2)");
+    return TTN_EOVERFLOW;
+  }
+  if (ovf[1] > 0) {
+    set_error("decoder: canonical path or perfect matching not found");
+    return TTN_ECUDA;
+  }
+  return TTN_OK;
+}
+
+// ------------------------------------------------------------------ allocation-free decoding
+// ttn_decode_noalloc serves callers that must not allocate device memory: an
+// application whose memory pool or caching allocator already owns the GPU
+// memory, a host framework whose allocator hooks forbid direct driver
+// allocations, or code that cannot afford the device-wide synchronisation
+// that cudaMalloc / cudaFree may imply.  It runs the same decoder kernel, but
+// its tables and per-shot scratch live in file-scope static device arrays
+// instead of cudaMalloc'ed buffers.  Every GPU that loads the library holds
+// these arrays (about 2 MB) until the process exits.  The first call on a
+// device resolves the arrays' device addresses (cudaGetSymbolAddress); make
+// that first call before any stream capture.  The first call with a given
+// circuit also packs its decoder tables into one host array kept with the
+// circuit.
+//
+// Limits: at most NA_NODES detector nodes ((rounds + 1) * #faces + 1 <= 145,
+// e.g. d = 7 with up to 7 rounds) and NA_TABLE_INTS packed table entries; any
+// number of shots, decoded NA_SHOTS at a time.  All calls share the arrays:
+// calls that overlap on the GPU (different streams or host threads without
+// ordering) race and corrupt each other's results.
+static constexpr int NA_SHOTS = 8;
+static constexpr int NA_NODES = 145;
+static constexpr int NA_TABLE_INTS = 80000;
+static constexpr size_t NA_E1_BYTES = 2048;
+static constexpr size_t na_align(size_t x) { return (x + 255) / 256 * 256; }
+static constexpr size_t NA_DPF = na_align(sizeof(int64_t) << KCOMP);
+static constexpr size_t NA_DPC = na_align((size_t)1 << KCOMP);
+static constexpr size_t NA_D2 = na_align(sizeof(int64_t) * (KMAX + 1) * NA_NODES);
+static constexpr size_t NA_E1 = na_align(NA_E1_BYTES);
+static constexpr size_t NA_RES = na_align(2 * NA_NODES);
+static constexpr size_t NA_DEFS = na_align(sizeof(int) * 4 * KMAX);
+static constexpr size_t NA_WB = na_align(sizeof(int64_t) * KMAX);
+static constexpr size_t NA_BL = na_align(boundary_matching_scratch_bytes(KMAX));
+static constexpr size_t NA_PER_SHOT = NA_DPF + NA_DPC + NA_D2 + NA_E1 + NA_RES + NA_DEFS + NA_WB + NA_BL;
+static constexpr size_t NA_SCRATCH_BYTES = NA_PER_SHOT * NA_SHOTS + 256;
+
+static __device__ __align__(256) unsigned char g_na_scratch[NA_SCRATCH_BYTES];
+static __device__ __align__(256) int32_t g_na_tables[NA_TABLE_INTS];
+
+DecoderBlob build_decoder_blob(const DecoderTables& t) {
+  DecoderBlob b;
+  std::vector<int32_t> clsof((size_t)3 * t.P * (t.P + 1), -1);
+  std::vector<int32_t> inc_off(3 * (t.P + 1), 0), inc;
+  for (int cc = 0; cc < 3; ++cc) {
+    for (int i = 0; i < t.n_cls[cc]; ++i) {
+      int f1 = t.cls_f[(cc * t.n_cls_max + i) * 2], f2 = t.cls_f[(cc * t.n_cls_max + i) * 2 + 1];
+      if (f1 >= 0) clsof[((size_t)cc * t.P + f1) * (t.P + 1) + (f2 < 0 ? t.P : f2)] = i;
+    }
+    std::vector<std::vector<int>> per(t.P);
+    for (int i = 0; i < t.n_cls[cc]; ++i)
+      for (int j = t.cls_off[cc * (t.n_cls_max + 1) + i]; j < t.cls_off[cc * (t.n_cls_max + 1) + i + 1]; ++j) {
+        int q = t.cls_q[j];
+        int g = t.cface[cc * t.n + q];
+        if (g >= 0) {
+          per[g].push_back(i);
+          per[g].push_back(q);
+        }
+      }
+    for (int g = 0; g < t.P; ++g) {
+      inc_off[cc * (t.P + 1) + g] = (int)inc.size() / 2;
+      for (int x : per[g]) inc.push_back(x);
+    }
+    inc_off[cc * (t.P + 1) + t.P] = (int)inc.size() / 2;
+  }
+  const std::vector<int32_t>* parts[14] = {&t.color, &t.support_off, &t.support, &t.dist1, &t.adj1_off,
+                                           &t.adj1, &t.cls_off, &t.cls_q, &t.cls_f, &t.n_cls,
+                                           &clsof, &t.cface, &inc_off, &inc};
+  for (int i = 0; i < 14; ++i) {
+    b.off[i] = (int32_t)b.data.size();
+    b.data.insert(b.data.end(), parts[i]->begin(), parts[i]->end());
+    while (b.data.size() % 4) b.data.push_back(0);  // 16-byte aligned parts
+  }
+  b.off[14] = (int32_t)b.data.size();
+  return b;
+}
+
+// Device addresses of the static arrays, resolved once per device.
+static std::mutex g_na_mutex;
+static unsigned char* g_na_scratch_ptr[64] = {nullptr};
+static int32_t* g_na_tables_ptr[64] = {nullptr};
+
+static ttn_status na_setup(int* dev_out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) {
+    set_error(std::string("CUDA: cudaGetDevice: ") + cudaGetErrorString(e));
+    return TTN_ECUDA;
+  }
+  if (dev < 0 || dev >= 64) {
+    set_error("ttn_decode_noalloc: device index above 63");
+    return TTN_EUNSUPPORTED;
+  }
+  std::lock_guard<std::mutex> lock(g_na_mutex);
+  if (!g_na_scratch_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_na_scratch);
+    if (e != cudaSuccess) {
+      set_error(std::string("CUDA: cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e));
+      return TTN_ECUDA;
+    }
+    void* q = nullptr;
+    e = cudaGetSymbolAddress(&q, g_na_tables);
+    if (e != cudaSuccess) {
+      set_error(std::string("CUDA: cudaGetSymbolAddress(tables): ") + cudaGetErrorString(e));
+      return TTN_ECUDA;
+    }
+    g_na_scratch_ptr[dev] = (unsigned char*)p;
+    g_na_tables_ptr[dev] = (int32_t*)q;
+  }
+  *dev_out = dev;
+  return TTN_OK;
+}
+
+ttn_status decode_noalloc(const ttn_circuit& c, uint64_t n, const uint8_t* d_records, uint8_t* d_fail,
+                          int32_t* d_color, int64_t* d_score, void* stream) {
+  const DecoderTables& t = c.dec;
+  if (t.n_nodes > NA_NODES) {
+    set_error("ttn_decode_noalloc: " + std::to_string(t.n_nodes) + " detector nodes; the static scratch holds " +
+              std::to_string(NA_NODES) + " ((rounds + 1) * faces + 1)");
+    return TTN_EINVAL;
+  }
+  {
+    std::lock_guard<std::mutex> lock(g_na_mutex);
+    if (!c.dec_blob_ready) {
+      c.dec_blob = build_decoder_blob(t);
+      c.dec_blob_ready = true;
+    }
+  }
+  const DecoderBlob& blob = c.dec_blob;
+  if ((int64_t)blob.data.size() > NA_TABLE_INTS ||
+      (size_t)t.T * t.n_cls_max + (size_t)t.T * t.P > NA_E1_BYTES) {
+    set_error("ttn_decode_noalloc: decoder tables exceed the static table size");
+    return TTN_EINVAL;
+  }
+  int dev = 0;
+  ttn_status s = na_setup(&dev);
+  if (s != TTN_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  unsigned char* scratch = g_na_scratch_ptr[dev];
+  int32_t* tables = g_na_tables_ptr[dev];
+  cudaError_t e = cudaMemcpyAsync(tables, blob.data.data(), sizeof(int32_t) * blob.data.size(),
+                                  cudaMemcpyHostToDevice, st);
+  DecDev d{};
+  d.T = t.T;
+  d.P = t.P;
+  d.B = t.B;
+  d.NN = t.n_nodes;
+  d.n = t.n;
+  d.n_rec = c.n_rec;
+  d.C = c.C;
+  d.ncm = t.n_cls_max;
+  d.color = tables + blob.off[0];
+  d.support_off = tables + blob.off[1];
+  d.support = tables + blob.off[2];
+  d.dist1 = tables + blob.off[3];
+  d.adj1_off = tables + blob.off[4];
+  d.adj1 = tables + blob.off[5];
+  d.cls_off = tables + blob.off[6];
+  d.cls_q = tables + blob.off[7];
+  d.cls_f = tables + blob.off[8];
+  d.n_cls = tables + blob.off[9];
+  d.clsof = tables + blob.off[10];
+  d.cface = tables + blob.off[11];
+  d.inc_off = tables + blob.off[12];
+  d.inc = tables + blob.off[13];
+  // per-shot scratch regions, NA_SHOTS shots side by side
+  unsigned char* base = scratch;
+  d.dp_f = (int64_t*)base;
+  base += NA_DPF * NA_SHOTS;
+  d.dp_c = (int8_t*)base;
+  base += NA_DPC * NA_SHOTS;
+  d.dist2 = (int64_t*)base;
+  base += NA_D2 * NA_SHOTS;
+  d.e1 = base;
+  base += NA_E1 * NA_SHOTS;
+  d.resid = base;
+  base += NA_RES * NA_SHOTS;
+  d.defs = (int*)base;
+  base += NA_DEFS * NA_SHOTS;
+  d.wb = (int64_t*)base;
+  base += NA_WB * NA_SHOTS;
+  d.bls = base;
+  base += NA_BL * NA_SHOTS;
+  d.overflow = (int32_t*)base;  // the last 256 bytes
+  d.dp_stride = NA_DPF / sizeof(int64_t);
+  d.d2_stride = NA_D2 / sizeof(int64_t);
+  d.e1_stride = NA_E1;
+  d.bl_stride = NA_BL;
+  // the overflow counters must start at zero; the rest is overwritten per shot
+  if (e == cudaSuccess) e = cudaMemsetAsync(d.overflow, 0, 2 * sizeof(int32_t), st);
+  for (uint64_t s0 = 0; s0 < n && e == cudaSuccess; s0 += NA_SHOTS) {
+    const int m = (int)std::min<uint64_t>(NA_SHOTS, n - s0);
+    k_decode<<<1, 64, 0, st>>>(d, m, d_records + s0 * c.n_rec, d_fail + s0,
+                               d_color ? d_color + s0 : nullptr, d_score ? d_score + s0 : nullptr);
+    e = cudaGetLastError();
+  }
+  int32_t ovf[2] = {0, 0};
+  if (e == cudaSuccess) e = cudaMemcpyAsync(ovf, d.overflow, sizeof(ovf), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    set_error(std::string("CUDA: ttn_decode_noalloc: ") + cudaGetErrorString(e));
     return TTN_ECUDA;
   }
   if (ovf[0] > 0) {

@@ -65,6 +65,10 @@ ttn_status run_trajectories_device(const ttn_circuit& c, const RunRequest& rq, R
 ttn_status decode_device(const ttn_circuit& c, int nb, const uint8_t* d_records, uint8_t* fail,
                          int32_t* color, int64_t* score, void* stream, bool on_device);
 
+// Allocation-free decoding with static device scratch (device pointers).
+ttn_status decode_noalloc(const ttn_circuit& c, uint64_t n, const uint8_t* d_records, uint8_t* d_fail,
+                          int32_t* d_color, int64_t* d_score, void* stream);
+
 ttn_status philox_uniforms_device(uint64_t seed, const uint64_t* trajs, uint64_t n_traj,
                                   const int32_t* events, int32_t n_events, double* out);
 

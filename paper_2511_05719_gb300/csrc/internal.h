@@ -95,6 +95,15 @@ struct DecoderTables {
 
 DecoderTables build_decoder_tables(const Code& code, int rounds);
 
+// All decoder tables packed into one int32 array (offsets in `off`), built
+// once per circuit (host memory) so that the allocation-free decoder entry
+// point only copies it into its static device table.
+struct DecoderBlob {
+  std::vector<int32_t> data;
+  int32_t off[16] = {0};
+};
+DecoderBlob build_decoder_blob(const DecoderTables& t);
+
 // ---------------------------------------------------------------- circuit handle
 }  // namespace ttn
 
@@ -105,6 +114,9 @@ struct ttn_circuit {
   std::vector<ttn::Op> ops;
   std::vector<int> leaf_of_qubit;
   ttn::DecoderTables dec;
+  // packed decoder tables, built by the first ttn_decode_noalloc call
+  mutable ttn::DecoderBlob dec_blob;
+  mutable bool dec_blob_ready = false;
 };
 
 namespace ttn {
