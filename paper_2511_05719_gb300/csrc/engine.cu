@@ -138,6 +138,7 @@ enum : int32_t { ERR_ZERO_NORM = 1, ERR_NO_CONVERGE = 2, ERR_CAPACITY = 4, ERR_N
 static constexpr int EIG_SMEM_MAX = 131072;
 static constexpr int TRI_UNROLL = 16;  // loads in flight per thread in L2-resident sweeps
 static constexpr int TRI_NB = 8;       // reflectors per compact-WY block of the back-transformation
+static constexpr int TRI_INV_ITERS = 4;  // inverse-iteration / Gram-Schmidt rounds
 template <typename R>
 constexpr int tri_smem_bytes() {
   return 512 * (5 * 2 * (int)sizeof(R) + 3 * (int)sizeof(R)) + 2 * TRI_NB * 512 * 2 * (int)sizeof(R);
@@ -1032,9 +1033,9 @@ __device__ void tri_reflector(cx<R>* A, int n, int c, cx<R>* vout, R* tau, cx<R>
 //  3. eigenvalues by bisection on Sturm counts (thread per eigenvalue);
 //  4. eigenvectors of the kept eigenvalues by inverse iteration on the
 //     pivoted LU factors of T - lambda I restricted to the eigenvalue's block
-//     (thread per vector; unresolved eigenvalues of one block get shifts
-//     spaced by a few ulps so their vectors stay independent, as in LAPACK's
-//     stein), made orthonormal by Cholesky QR applied twice;
+//     (thread per vector), alternating with classical Gram-Schmidt applied
+//     twice (as LAPACK's stein re-orthogonalises clusters), then a
+//     Rayleigh-Ritz step on the kept subspace;
 //  5. back-transformation by the stored reflectors.
 // (Golub & Van Loan, Matrix Computations, Ch. 8.)  Selection and output as in
 // k_eig: V_k (n x k, row-major) into G.
@@ -1244,29 +1245,42 @@ __global__ void __launch_bounds__(512) k_eig_tri(Dev<R> d, int v, int w, int cap
     sv[j] = (double)l * sc;
   }
   __syncthreads();
-  // eigenvalues below a few ulps of |T| are not resolved in this precision
-  const double eps_keep = fmax(d.eps_gram, sqrt(4.0 * (double)epsR));
+  // singular values below sqrt(eps) s_max are not resolved by a Gram matrix
+  // in this precision
+  const double eps_keep = fmax(d.eps_gram, sqrt((double)epsR));
   const int k = eig_select(d, b, v, w, capped, n, trace, eps_keep);
   if (tid == 0)
     ledger_add(d.ledger, KC_EIG, 16.0 / 3.0 * (double)n * n * n + 8.0 * (double)n * n * k,
                (double)sizeof(cx<R>) * ((double)n * n + (double)n * k));
 
-  // ---- 4. inverse iteration, thread c for kept column c (eigenvalue perm[c])
-  if (tid < k) {
-    const int c = tid, jj = perm[c], s0 = bstart[jj], e0 = bend[jj];
-    const R tolc = 16 * epsR;
-    int rk = 0;
-    while (jj - rk - 1 >= s0 && lam[jj - rk] - lam[jj - rk - 1] < tolc) ++rk;
-    const R l = lam[jj] + (R)rk * tolc;
-    for (int i = 0; i < n; ++i) {  // start vector: hashed, in (-1, 1), zero off the block
-      uint32_t h = (uint32_t)i * 0x9E3779B1u ^ ((uint32_t)c + 0x7F4A7C15u) * 0x85EBCA77u;
+  // ---- 4. eigenvectors of the kept eigenvalues.  Inverse iteration (thread c
+  // for kept column c, eigenvalue perm[c], on that eigenvalue's block)
+  // alternates with classical Gram-Schmidt applied twice in column order; a
+  // column that loses almost all of its norm there restarts from a fresh
+  // vector.  Eigenvalues closer than the arithmetic resolves (flat spectra of
+  // stabiliser-like states) thus still get independent vectors spanning their
+  // invariant subspace, and a Rayleigh-Ritz step on the kept subspace
+  // (H = Z^T T Z = Q L Q^T by cyclic Jacobi, Z <- Z Q) diagonalises it.
+  auto start_vec = [&](int c, int salt, int s0, int e0) {
+    for (int i = tid; i < n; i += nth) {
+      uint32_t h = (uint32_t)(i + 7919 * salt) * 0x9E3779B1u ^ ((uint32_t)c + 0x7F4A7C15u) * 0x85EBCA77u;
       h ^= h >> 15;
       h *= 0x2C1B3C6Du;
       h ^= h >> 12;
       const R x = (R)((double)(h >> 8) * (2.0 / 16777216.0) - 1.0 + 1.0 / 16777216.0);
       Z[(int64_t)i * n + c] = (i >= s0 && i < e0) ? x : R(0);
     }
-    for (int iter = 0; iter < 3; ++iter) {
+  };
+  for (int c = 0; c < k; ++c) {
+    const int jj = perm[c];
+    start_vec(c, 0, bstart[jj], bend[jj]);
+  }
+  __syncthreads();
+  R* cf = reinterpret_cast<R*>(pp);  // Gram-Schmidt coefficients (k <= 512)
+  for (int iter = 0; iter < TRI_INV_ITERS; ++iter) {
+    if (tid < k) {
+      const int c = tid, jj = perm[c], s0 = bstart[jj], e0 = bend[jj];
+      const R l = lam[jj];
       // forward elimination with partial pivoting, right-hand side carried along
       R cd = dg[s0] - l, cu = s0 + 1 < e0 ? bt[s0] : R(0), cr = Z[(int64_t)s0 * n + c];
       for (int i = s0; i + 1 < e0; ++i) {
@@ -1299,8 +1313,7 @@ __global__ void __launch_bounds__(512) k_eig_tri(Dev<R> d, int v, int w, int cap
       // back substitution; pivots below eps |T| are replaced by eps |T|.
       // The solution grows by up to 1/eps per small pivot: whenever it
       // passes BIG, the solved part and the remaining right-hand side are
-      // scaled down together (the system is linear; the vector is
-      // normalised afterwards).
+      // scaled down together (the system is linear).
       const R BIG = sizeof(R) == 8 ? R(1e150) : R(1e15);
       R y1 = R(0), y2 = R(0), ymax = R(0);
       for (int i = e0 - 1; i >= s0; --i) {
@@ -1326,56 +1339,138 @@ __global__ void __launch_bounds__(512) k_eig_tri(Dev<R> d, int v, int w, int cap
         ymax = fmax(ymax, fabs(y));
       }
       const R inv = ymax > R(0) && ymax < R(1e30) ? R(1) / ymax : R(1);
-      double nrm = 0.0;
-      for (int i = s0; i < e0; ++i) {
-        const R y = Z[(int64_t)i * n + c] * inv;
-        nrm += (double)y * y;
-      }
-      const R s2 = (R)(1.0 / sqrt(fmax(nrm, 1e-300)));
-      for (int i = s0; i < e0; ++i) Z[(int64_t)i * n + c] = Z[(int64_t)i * n + c] * inv * s2;
+      for (int i = s0; i < e0; ++i) Z[(int64_t)i * n + c] *= inv;
     }
+    __syncthreads();
+    // classical Gram-Schmidt, twice, columns in order
+    for (int a = 0; a < k; ++a) {
+      const int jj = perm[a];
+      for (int rep = 0; rep < 2; ++rep) {
+        for (int attempt = 0; attempt < 2; ++attempt) {
+          for (int bb = tid; bb < a; bb += nth) {
+            R acc = R(0);
+            for (int i = 0; i < n; ++i) acc += Z[(int64_t)i * n + bb] * Z[(int64_t)i * n + a];
+            cf[bb] = acc;
+          }
+          __syncthreads();
+          double n0 = 0.0, n1 = 0.0;
+          for (int i = tid; i < n; i += nth) {
+            R* zi = Z + (int64_t)i * n;
+            R z = zi[a];
+            n0 += (double)z * z;
+            for (int bb = 0; bb < a; ++bb) z -= cf[bb] * zi[bb];
+            zi[a] = z;
+            n1 += (double)z * z;
+          }
+          const double2 nn = block_sum2(n0, n1, red);
+          if (nn.y > 1e-6 * nn.x && nn.y > 0.0) {
+            const R sc1 = (R)(1.0 / sqrt(nn.y));
+            for (int i = tid; i < n; i += nth) Z[(int64_t)i * n + a] *= sc1;
+            __syncthreads();
+            break;
+          }
+          // dependent on the previous columns: restart from a fresh vector
+          start_vec(a, 1 + iter * 4 + rep * 2 + attempt, bstart[jj], bend[jj]);
+          __syncthreads();
+        }
+      }
+    }
+  }
+  // Rayleigh-Ritz: TZ into U0, H = Z^T (TZ) into U1 (k x k), Q into U2
+  R* TZ = U0;
+  R* H = U1;
+  R* Q = U2;
+  for (int idx = tid; idx < n * k; idx += nth) {
+    const int i = idx / k, c = idx - i * k;
+    R t = dg[i] * Z[(int64_t)i * n + c];
+    if (i > 0) t += bt[i - 1] * Z[(int64_t)(i - 1) * n + c];
+    if (i + 1 < n) t += bt[i] * Z[(int64_t)(i + 1) * n + c];
+    TZ[idx] = t;
   }
   __syncthreads();
-
-  // ---- 4b. Cholesky QR, applied twice, of Z[:, :k]: S = Z^T Z = L L^T, Z <- Z L^-T
-  for (int rep = 0; rep < 2 && k > 1; ++rep) {
-    R* S = U0;  // k x k
-    for (int idx = tid; idx < k * k; idx += nth) {
-      const int p = idx / k, q = idx - p * k;
-      if (q > p) continue;
-      R acc = R(0);
-      for (int i = 0; i < n; ++i) acc += Z[(int64_t)i * n + p] * Z[(int64_t)i * n + q];
-      S[idx] = acc;
-    }
-    __syncthreads();
-    for (int j = 0; j < k; ++j) {
-      R piv = S[j * k + j];
-      if (rep == 1 && !(piv > R(0.25)) && tid == 0) atomicOr(&d.err[b], ERR_NO_CONVERGE);
-      if (!(piv > R(1e-12))) piv = R(1e-12);
-      const R rj = sqrt(piv), irj = R(1) / rj;
-      __syncthreads();
-      if (tid == 0) S[j * k + j] = rj;
-      for (int p = j + 1 + tid; p < k; p += nth) S[p * k + j] *= irj;
-      __syncthreads();
-      const int t = k - j - 1;
-      for (int idx = tid; idx < t * t; idx += nth) {
-        const int p = j + 1 + idx / t, q = j + 1 + idx % t;
-        if (q > p) continue;
-        S[p * k + q] -= S[p * k + j] * S[q * k + j];
-      }
-      __syncthreads();
-    }
-    // rows of Z: y L^T = z, forward substitution per row
-    for (int i = tid; i < n; i += nth) {
-      R* zi = Z + (int64_t)i * n;
-      for (int q = 0; q < k; ++q) {
-        R y = zi[q];
-        for (int p = 0; p < q; ++p) y -= zi[p] * S[q * k + p];
-        zi[q] = y / S[q * k + q];
-      }
-    }
-    __syncthreads();
+  for (int idx = tid; idx < k * k; idx += nth) {
+    const int a = idx / k, c = idx - a * k;
+    Q[idx] = R(a == c);
+    if (c < a) continue;
+    R acc = R(0);
+    for (int i = 0; i < n; ++i) acc += Z[(int64_t)i * n + a] * TZ[(int64_t)i * k + c];
+    H[a * k + c] = acc;
+    H[c * k + a] = acc;
   }
+  __syncthreads();
+  if (k > 1) {
+    __shared__ R rc[256], rs[256];
+    __shared__ int rp[256], rq[256];
+    const int ke = k + (k & 1), M1 = ke - 1, np2 = ke / 2;
+    const R rtol = sizeof(R) == 8 ? R(1e-14) : R(1e-7);
+    for (int sweep = 0; sweep < 12; ++sweep) {
+      int rotated = 0;
+      for (int st = 0; st < M1; ++st) {
+        for (int pr = tid; pr < np2; pr += nth) {
+          int p, q;
+          if (pr == 0) {
+            p = 0;
+            q = (st % M1) + 1;
+          } else {
+            p = ((pr + st) % M1) + 1;
+            q = ((M1 - pr + st) % M1) + 1;
+          }
+          rp[pr] = -1;
+          if (p >= k || q >= k) continue;
+          const R hpp = H[p * k + p], hqq = H[q * k + q], hpq = H[p * k + q];
+          if (!(fabs(hpq) > rtol * (fabs(hpp) + fabs(hqq))) || hpq == R(0)) continue;
+          rotated = 1;
+          const R zeta = (hqq - hpp) / (R(2) * hpq);
+          const R t = (zeta >= R(0) ? R(1) : R(-1)) / (fabs(zeta) + sqrt(R(1) + zeta * zeta));
+          const R c = R(1) / sqrt(R(1) + t * t);
+          rp[pr] = p;
+          rq[pr] = q;
+          rc[pr] = c;
+          rs[pr] = c * t;
+        }
+        __syncthreads();
+        for (int idx = tid; idx < np2 * k; idx += nth) {  // rows of H
+          const int pr = idx / k, col = idx - pr * k;
+          const int p = rp[pr];
+          if (p < 0) continue;
+          const int q = rq[pr];
+          const R c = rc[pr], sn = rs[pr];
+          const R hp = H[p * k + col], hq = H[q * k + col];
+          H[p * k + col] = c * hp - sn * hq;
+          H[q * k + col] = sn * hp + c * hq;
+        }
+        __syncthreads();
+        for (int idx = tid; idx < np2 * k; idx += nth) {  // columns of H and Q
+          const int pr = idx / k, row = idx - pr * k;
+          const int p = rp[pr];
+          if (p < 0) continue;
+          const int q = rq[pr];
+          const R c = rc[pr], sn = rs[pr];
+          const R hp = H[row * k + p], hq = H[row * k + q];
+          H[row * k + p] = c * hp - sn * hq;
+          H[row * k + q] = sn * hp + c * hq;
+          const R qp = Q[row * k + p], qq = Q[row * k + q];
+          Q[row * k + p] = c * qp - sn * qq;
+          Q[row * k + q] = sn * qp + c * qq;
+        }
+        __syncthreads();
+      }
+      if (!__syncthreads_or(rotated)) break;
+    }
+  }
+  // Z_k Q into TZ (n x k), then back into Z's first k columns
+  for (int idx = tid; idx < n * k; idx += nth) {
+    const int i = idx / k, c = idx - i * k;
+    R acc = R(0);
+    for (int a = 0; a < k; ++a) acc += Z[(int64_t)i * n + a] * Q[a * k + c];
+    TZ[idx] = acc;
+  }
+  __syncthreads();
+  for (int idx = tid; idx < n * k; idx += nth) {
+    const int i = idx / k, c = idx - i * k;
+    Z[(int64_t)i * n + c] = TZ[idx];
+  }
+  __syncthreads();
 
   // ---- 5. back-transformation V_k = H_0 ... H_{n-3} D Z_k (n x k in Vk),
   // TRI_NB reflectors at a time in compact WY form (Schreiber & Van Loan):
