@@ -195,15 +195,20 @@ ttn_status ttn_philox_uniforms(uint64_t seed, const uint64_t* trajs, uint64_t n_
 
 /* Profiling ledger.  Kernel classes: 0 one-sided Jacobi SVD move, 1 Gram
  * GEMM, 2 Gram eigendecomposition, 3 U = M V GEMM, 4 bond absorption GEMM,
- * 5 tensor copies, 6 other.  Between ttn_profile_begin(c) and
+ * 5 tensor copies, 6 other move kernels, 7 gate threading, single-qubit,
+ * measurement and damping kernels.  Between ttn_profile_begin(c) and
  * ttn_profile_end, every run adds each class's algorithmic flops and bytes
- * (counted from the live bond dimensions: complex GEMM 8mnk, eigensolver
- * 36n^3, thin SVD 24mn^2 + 44n^3, bytes = operands read + written) and the
- * device time of every launch of class c (CUDA events on the launch stream;
- * c = -1 times nothing).  flops, bytes, launches: host [7] or NULL. */
+ * (counted from the live bond dimensions: complex GEMM 8mnk, Jacobi
+ * eigensolver 36n^3, tridiagonal eigensolver 16/3 n^3 + 8n^2 k, thin SVD
+ * 24mn^2 + 44n^3, bytes = operands read + written) and the device time of
+ * every launch of class c (CUDA events on the launch stream; c = -1 times
+ * nothing, c = 8 times every class).  flops, bytes, launches: host [8] or
+ * NULL.  ttn_profile_class_ms: the timed device milliseconds per class of the
+ * current (or last) profile, host [8]. */
 ttn_status ttn_profile_begin(int32_t timed_class);
 ttn_status ttn_profile_end(double* timed_ms, uint64_t* timed_launches, double* flops,
                            double* bytes, uint64_t* launches);
+ttn_status ttn_profile_class_ms(double* class_ms);
 
 const char* ttn_status_string(ttn_status status);
 const char* ttn_last_error(void);

@@ -40,7 +40,7 @@ class TTNError(RuntimeError):
 EXPORTS = ["ttn_build_circuit", "ttn_free_circuit", "ttn_circuit_info", "ttn_circuit_ops",
            "ttn_circuit_layout", "ttn_run_trajectories", "ttn_logical_error_rate", "ttn_decode",
            "ttn_debug_state", "ttn_philox_uniforms", "ttn_profile_begin", "ttn_profile_end",
-           "ttn_grad", "ttn_decode_noalloc",
+           "ttn_grad", "ttn_decode_noalloc", "ttn_profile_class_ms",
            "ttn_status_string", "ttn_last_error"]
 
 
@@ -76,6 +76,7 @@ def load_library():
     lib.ttn_grad.argtypes = [vp, ctypes.POINTER(RunParams), ctypes.c_uint64, ctypes.c_int32,
                              ctypes.c_double, c_dblp, c_dblp, c_dblp, c_dblp]
     lib.ttn_profile_begin.argtypes = [ctypes.c_int32]
+    lib.ttn_profile_class_ms.argtypes = [c_dblp]
     lib.ttn_profile_end.argtypes = [c_dblp, c_u64p, c_dblp, c_dblp, c_u64p]
     lib.ttn_status_string.restype = ctypes.c_char_p
     lib.ttn_status_string.argtypes = [ctypes.c_int]
@@ -250,25 +251,30 @@ def philox_uniforms(seed, trajs, events):
     return out
 
 
-KERNEL_CLASSES = ["svd_jacobi", "gram", "eig", "form_u", "absorb", "copy", "other"]
+KERNEL_CLASSES = ["svd_jacobi", "gram", "eig", "form_u", "absorb", "copy", "other", "local"]
 
 
 def profile_begin(timed_class=-1):
-    """Starts the profiling ledger; launches of `timed_class` are timed."""
+    """Starts the profiling ledger; launches of `timed_class` are timed
+    ("all" times every class, at some launch overhead)."""
     if isinstance(timed_class, str):
-        timed_class = KERNEL_CLASSES.index(timed_class)
+        timed_class = len(KERNEL_CLASSES) if timed_class == "all" else KERNEL_CLASSES.index(timed_class)
     _check(load_library().ttn_profile_begin(int(timed_class)))
 
 
 def profile_end():
+    nc = len(KERNEL_CLASSES)
     ms, nl = ctypes.c_double(), ctypes.c_uint64()
-    fl = (ctypes.c_double * 7)()
-    by = (ctypes.c_double * 7)()
-    la = (ctypes.c_uint64 * 7)()
-    _check(load_library().ttn_profile_end(ctypes.byref(ms), ctypes.byref(nl), fl, by, la))
+    fl = (ctypes.c_double * nc)()
+    by = (ctypes.c_double * nc)()
+    la = (ctypes.c_uint64 * nc)()
+    cm = (ctypes.c_double * nc)()
+    lib = load_library()
+    _check(lib.ttn_profile_end(ctypes.byref(ms), ctypes.byref(nl), fl, by, la))
+    _check(lib.ttn_profile_class_ms(cm))
     return dict(timed_ms=ms.value, timed_launches=nl.value,
                 flops=dict(zip(KERNEL_CLASSES, list(fl))), bytes=dict(zip(KERNEL_CLASSES, list(by))),
-                launches=dict(zip(KERNEL_CLASSES, list(la))))
+                launches=dict(zip(KERNEL_CLASSES, list(la))), class_ms=dict(zip(KERNEL_CLASSES, list(cm))))
 
 
 def grad(circuit, shots, wrt="theta", noise="srx", theta=0.0, gamma=0.0, chi=16, precision="fp64",

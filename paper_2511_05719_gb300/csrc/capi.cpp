@@ -300,7 +300,7 @@ ttn_status ttn_debug_state(const ttn_circuit* c, const ttn_run_params* p, uint64
 }
 
 ttn_status ttn_profile_begin(int32_t timed_class) {
-  if (timed_class < -1 || timed_class >= NCLASS) return fail_with(TTN_EINVAL, "unknown kernel class");
+  if (timed_class < -1 || timed_class > NCLASS) return fail_with(TTN_EINVAL, "unknown kernel class");
   Profile& p = profile();
   p = Profile();
   p.active = true;
@@ -320,6 +320,13 @@ ttn_status ttn_profile_end(double* timed_ms, uint64_t* timed_launches, double* f
     if (launches) launches[c] = p.class_launches[c];
   }
   p.active = false;
+  return TTN_OK;
+}
+
+ttn_status ttn_profile_class_ms(double* class_ms) {
+  if (!class_ms) return fail_with(TTN_EINVAL, "null argument");
+  const Profile& p = profile();
+  for (int c = 0; c < NCLASS; ++c) class_ms[c] = p.class_ms[c];
   return TTN_OK;
 }
 

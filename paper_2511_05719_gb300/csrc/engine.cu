@@ -2137,6 +2137,7 @@ struct Engine {
   Group1* dGroups = nullptr;
   unsigned long long* dLedger = nullptr;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> events;
+  std::vector<int> event_class;
   uint64_t class_launches[NCLASS] = {0};
   Dev<R> dev{};
 
@@ -2146,7 +2147,7 @@ struct Engine {
   void timed(int cls, F&& fn) {
     Profile& pf = profile();
     class_launches[cls]++;
-    if (pf.active && pf.timed_class == cls) {
+    if (pf.active && (pf.timed_class == cls || pf.timed_class == NCLASS)) {
       cudaEvent_t a, b;
       cudaEventCreate(&a);
       cudaEventCreate(&b);
@@ -2154,6 +2155,7 @@ struct Engine {
       fn();
       cudaEventRecord(b, st);
       events.push_back({a, b});
+      event_class.push_back(cls);
     } else {
       fn();
     }
@@ -2162,14 +2164,19 @@ struct Engine {
   void collect_profile() {
     Profile& pf = profile();
     if (!pf.active) return;
-    for (auto& e : events) {
+    for (size_t i = 0; i < events.size(); ++i) {
+      auto& e = events[i];
       float ms = 0.f;
-      if (cudaEventElapsedTime(&ms, e.first, e.second) == cudaSuccess) pf.ms += ms;
+      if (cudaEventElapsedTime(&ms, e.first, e.second) == cudaSuccess) {
+        pf.ms += ms;
+        pf.class_ms[event_class[i]] += ms;
+      }
       pf.launches++;
       cudaEventDestroy(e.first);
       cudaEventDestroy(e.second);
     }
     events.clear();
+    event_class.clear();
     unsigned long long h[2 * NCLASS] = {0};
     if (dLedger && cudaMemcpy(h, dLedger, sizeof(h), cudaMemcpyDeviceToHost) == cudaSuccess)
       for (int c = 0; c < NCLASS; ++c) {
@@ -2364,38 +2371,58 @@ struct Engine {
           break;
         }
         case S_THREAD_LEAF: {
-          k_thread_leaf<R><<<dim3(std::max(1, ceil_div(ncap[s.a], 256)), nb), 256, 0, st>>>(
-              dev, s.a, s.b, s.c);
-          k_thread_dims_leaf<R><<<ceil_div(nb, 128), 128, 0, st>>>(dev, s.a, nb);
-          k_copy_back<R><<<dim3(std::max(1, ceil_div(ncap[s.a], 256 * 4)), nb), 256, 0, st>>>(dev, s.a);
+          timed(KC_LOCAL, [&] {
+            k_thread_leaf<R><<<dim3(std::max(1, ceil_div(ncap[s.a], 256)), nb), 256, 0, st>>>(
+                dev, s.a, s.b, s.c);
+            k_thread_dims_leaf<R><<<ceil_div(nb, 128), 128, 0, st>>>(dev, s.a, nb);
+          });
+          timed(KC_COPY, [&] {
+            k_copy_back<R><<<dim3(std::max(1, ceil_div(ncap[s.a], 256 * 4)), nb), 256, 0, st>>>(dev, s.a);
+          });
           break;
         }
         case S_THREAD_NODE: {
-          k_thread_node<R><<<dim3(std::max(1, ceil_div(ncap[s.a], 256)), nb), 256, 0, st>>>(
-              dev, s.a, s.b);
-          k_thread_dims_leaf<R><<<ceil_div(nb, 128), 128, 0, st>>>(dev, s.a, nb);
-          k_copy_back<R><<<dim3(std::max(1, ceil_div(ncap[s.a], 256 * 4)), nb), 256, 0, st>>>(dev, s.a);
+          timed(KC_LOCAL, [&] {
+            k_thread_node<R><<<dim3(std::max(1, ceil_div(ncap[s.a], 256)), nb), 256, 0, st>>>(
+                dev, s.a, s.b);
+            k_thread_dims_leaf<R><<<ceil_div(nb, 128), 128, 0, st>>>(dev, s.a, nb);
+          });
+          timed(KC_COPY, [&] {
+            k_copy_back<R><<<dim3(std::max(1, ceil_div(ncap[s.a], 256 * 4)), nb), 256, 0, st>>>(dev, s.a);
+          });
           break;
         }
         case S_THREAD_LCA: {
-          k_thread_lca<R><<<dim3(std::max(1, ceil_div(ncap[s.a], 256)), nb), 256, 0, st>>>(dev, s.a);
-          k_copy_back<R><<<dim3(std::max(1, ceil_div(ncap[s.a], 256 * 4)), nb), 256, 0, st>>>(dev, s.a);
+          timed(KC_LOCAL, [&] {
+            k_thread_lca<R><<<dim3(std::max(1, ceil_div(ncap[s.a], 256)), nb), 256, 0, st>>>(dev, s.a);
+          });
+          timed(KC_COPY, [&] {
+            k_copy_back<R><<<dim3(std::max(1, ceil_div(ncap[s.a], 256 * 4)), nb), 256, 0, st>>>(dev, s.a);
+          });
           break;
         }
         case S_GATE_NODE:
-          k_gate_node<R><<<ceil_div((int64_t)nb * 64, 256), 256, 0, st>>>(dev, s.a, s.b, nb);
+          timed(KC_LOCAL, [&] {
+            k_gate_node<R><<<ceil_div((int64_t)nb * 64, 256), 256, 0, st>>>(dev, s.a, s.b, nb);
+          });
           break;
         case S_LAYER1Q: {
           const int ng = s.d - s.c;
-          k_layer1q<R><<<ceil_div((int64_t)nb * ng, 128), 128, 0, st>>>(dev, dOp1, dGroups, s.c, ng, nb);
+          timed(KC_LOCAL, [&] {
+            k_layer1q<R><<<ceil_div((int64_t)nb * ng, 128), 128, 0, st>>>(dev, dOp1, dGroups, s.c, ng, nb);
+          });
           break;
         }
         case S_MEASURE:
-          k_measure<R><<<ceil_div(nb, 4), 128, 0, st>>>(dev, s.a, s.b, s.c, s.d,
-                                                        L + c.leaf_of_qubit[s.a], nb);
+          timed(KC_LOCAL, [&] {
+            k_measure<R><<<ceil_div(nb, 4), 128, 0, st>>>(dev, s.a, s.b, s.c, s.d,
+                                                          L + c.leaf_of_qubit[s.a], nb);
+          });
           break;
         case S_AD:
-          k_ad<R><<<ceil_div(nb, 4), 128, 0, st>>>(dev, s.a, s.b, L + c.leaf_of_qubit[s.a], nb);
+          timed(KC_LOCAL, [&] {
+            k_ad<R><<<ceil_div(nb, 4), 128, 0, st>>>(dev, s.a, s.b, L + c.leaf_of_qubit[s.a], nb);
+          });
           break;
       }
     }

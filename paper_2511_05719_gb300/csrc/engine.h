@@ -42,11 +42,12 @@ struct RunOutputs {
 
 // Kernel classes of the profiling ledger.
 enum KernelClass { KC_SVD = 0, KC_GRAM = 1, KC_EIG = 2, KC_FORMU = 3, KC_ABSORB = 4, KC_COPY = 5,
-                   KC_OTHER = 6, NCLASS = 7 };
+                   KC_OTHER = 6, KC_LOCAL = 7, NCLASS = 8 };
 
 // Process-wide profiling state: while active, every run adds algorithmic
-// flops/bytes per class to `ledger`, and launches of class `timed_class` are
-// bracketed by CUDA events whose elapsed times accumulate in `ms`.
+// flops/bytes per class to `ledger`, and launches of class `timed_class`
+// (every class when timed_class == NCLASS) are bracketed by CUDA events whose
+// elapsed times accumulate in `ms` and per class in `class_ms`.
 struct Profile {
   bool active = false;
   int timed_class = -1;
@@ -55,6 +56,7 @@ struct Profile {
   double flops[NCLASS] = {0};
   double bytes[NCLASS] = {0};
   uint64_t class_launches[NCLASS] = {0};
+  double class_ms[NCLASS] = {0};
 };
 Profile& profile();
 
