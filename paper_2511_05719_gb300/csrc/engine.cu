@@ -129,9 +129,18 @@ struct Dev {
   int32_t* trunc;        // [B] 1 if that move truncated
   int max_sweeps;
   int32_t* err;          // [B] error flags
+  int32_t* err_step;     // [B] step index of the first error (-1: none)
+  int cur_step;          // step of the program being launched
 };
 
 enum : int32_t { ERR_ZERO_NORM = 1, ERR_NO_CONVERGE = 2, ERR_CAPACITY = 4, ERR_NAN = 8 };
+
+// Raise an error flag of trajectory b and remember the first failing step.
+template <typename R>
+__device__ __forceinline__ void flag_err(const Dev<R>& d, int b, int32_t code) {
+  atomicOr(&d.err[b], code);
+  if (code != ERR_NO_CONVERGE) atomicCAS(&d.err_step[b], -1, d.cur_step);
+}
 
 // Gram matrices up to this size are diagonalised in shared memory (k_eig);
 // larger ones by the tridiagonal solver (k_eig_tri).
@@ -177,6 +186,7 @@ __global__ void k_init(Dev<R> d, const int32_t* leafdim, int B) {
     d.disc[b] = 0.0;
     d.ties[b] = 0;
     d.err[b] = 0;
+    d.err_step[b] = -1;
   }
   for (int i = threadIdx.x + blockIdx.x * blockDim.x; i < d.N; i += blockDim.x * gridDim.x)
     d.last[(int64_t)b * d.N + i] = 0;
@@ -213,7 +223,7 @@ __global__ void __launch_bounds__(256) k_svd_move(Dev<R> d, int v, int w, int ca
   __shared__ double s_scale;
   if ((int64_t)m * n > d.wstride || n > d.nmax || (int64_t)n * n > d.vstride) {
     if (tid == 0) {
-      atomicOr(&d.err[b], ERR_CAPACITY);
+      flag_err(d, b, ERR_CAPACITY);
       d.knew[b] = 0;
     }
     return;
@@ -318,7 +328,7 @@ __global__ void __launch_bounds__(256) k_svd_move(Dev<R> d, int v, int w, int ca
       // every thread takes the same decision (a block-wide OR at one barrier)
       if (!__syncthreads_or(rotated)) break;
     }
-    if (sweep == d.max_sweeps && tid == 0) atomicOr(&d.err[b], ERR_NO_CONVERGE);
+    if (sweep == d.max_sweeps && tid == 0) flag_err(d, b, ERR_NO_CONVERGE);
   }
 
   // singular values (double), sort descending, rank
@@ -330,7 +340,7 @@ __global__ void __launch_bounds__(256) k_svd_move(Dev<R> d, int v, int w, int ca
     if (lane == 0) {
       double sj = sqrt(acc);
       if (!(sj >= 0.0 && sj < 1e300)) {  // NaN / inf: flag, rank it last
-        atomicOr(&d.err[b], ERR_NAN);
+        flag_err(d, b, ERR_NAN);
         sj = 0.0;
       }
       sv[j] = sj;
@@ -349,7 +359,7 @@ __global__ void __launch_bounds__(256) k_svd_move(Dev<R> d, int v, int w, int ca
   __syncthreads();
   if (tid == 0) {
     for (int i = 0; i < n; ++i)
-      if (perm[i] < 0 || perm[i] >= n) atomicOr(&d.err[b], ERR_NAN);
+      if (perm[i] < 0 || perm[i] >= n) flag_err(d, b, ERR_NAN);
     double smax = sv[perm[0]];
     int k = 0;
     double tot = 0.0;
@@ -360,7 +370,7 @@ __global__ void __launch_bounds__(256) k_svd_move(Dev<R> d, int v, int w, int ca
     }
     if (k < 1) k = 1;
     double scale = 1.0;
-    if (smax == 0.0) atomicOr(&d.err[b], ERR_ZERO_NORM);
+    if (smax == 0.0) flag_err(d, b, ERR_ZERO_NORM);
     if (capped && k > d.chi) {
       double dsc = 0.0;
       for (int i = d.chi; i < n; ++i) dsc += sv[perm[i]] * sv[perm[i]];
@@ -771,7 +781,7 @@ __device__ int eig_select(Dev<R>& d, int b, int v, int w, int capped, int n, dou
     double lam = sv[j];
     double sj = lam > 0.0 ? sqrt(lam) : 0.0;
     if (!(sj < 1e300)) {
-      atomicOr(&d.err[b], ERR_NAN);
+      flag_err(d, b, ERR_NAN);
       sj = 0.0;
     }
     sv[j] = sj;
@@ -793,7 +803,7 @@ __device__ int eig_select(Dev<R>& d, int b, int v, int w, int capped, int n, dou
     for (int i = 0; i < n; ++i)
       if (sv[perm[i]] > eps_keep * smax) ++k;
     if (k < 1) k = 1;
-    if (smax == 0.0) atomicOr(&d.err[b], ERR_ZERO_NORM);
+    if (smax == 0.0) flag_err(d, b, ERR_ZERO_NORM);
     int trunc = 0;
     if (capped && k > d.chi) {
       k = d.chi;
@@ -847,7 +857,7 @@ __global__ void __launch_bounds__(512) k_eig(Dev<R> d, int v, int w, int capped)
   __shared__ double s_tr;
   if ((int64_t)n * n > d.vstride || n > d.nmax || n > 512) {
     if (tid == 0) {
-      atomicOr(&d.err[b], ERR_CAPACITY);
+      flag_err(d, b, ERR_CAPACITY);
       d.knew[b] = 0;
     }
     return;
@@ -940,7 +950,7 @@ __global__ void __launch_bounds__(512) k_eig(Dev<R> d, int v, int w, int capped)
       }
       if (!__syncthreads_or(rotated)) break;
     }
-    if (sweep == d.max_sweeps && tid == 0) atomicOr(&d.err[b], ERR_NO_CONVERGE);
+    if (sweep == d.max_sweeps && tid == 0) flag_err(d, b, ERR_NO_CONVERGE);
   }
   for (int j = tid; j < n; j += nth) sv[j] = (double)G[(int64_t)j * n + j].x;  // eigenvalues
   __syncthreads();
@@ -1048,14 +1058,15 @@ __global__ void __launch_bounds__(512) k_eig_tri(Dev<R> d, int v, int w, int cap
   const int n = leg == 0 ? D[2 * v] : (leg == 1 ? D[2 * v + 1] : D[v]);
   if ((int64_t)n * n > d.vstride || n > d.nmax || n > nth || nth > 512) {
     if (tid == 0) {
-      atomicOr(&d.err[b], ERR_CAPACITY);
+      flag_err(d, b, ERR_CAPACITY);
       d.knew[b] = 0;
     }
     return;
   }
   cx<R>* A = d.G + (int64_t)b * d.vstride;
   cx<R>* Vk = d.V + (int64_t)b * d.vstride;
-  // real scratch (4 n^2): eigenvectors Z of T and the LU factors U0, U1, U2
+  // real scratch (4 n^2, column-major): eigenvectors Z of T and the LU
+  // factors U0, U1, U2
   R* Z = reinterpret_cast<R*>(d.Ts + (int64_t)b * 2 * d.vstride);
   R* U0 = Z + (int64_t)n * n;
   R* U1 = U0 + (int64_t)n * n;
@@ -1268,7 +1279,7 @@ __global__ void __launch_bounds__(512) k_eig_tri(Dev<R> d, int v, int w, int cap
       h *= 0x2C1B3C6Du;
       h ^= h >> 12;
       const R x = (R)((double)(h >> 8) * (2.0 / 16777216.0) - 1.0 + 1.0 / 16777216.0);
-      Z[(int64_t)i * n + c] = (i >= s0 && i < e0) ? x : R(0);
+      Z[(int64_t)c * n + i] = (i >= s0 && i < e0) ? x : R(0);
     }
   };
   for (int c = 0; c < k; ++c) {
@@ -1277,39 +1288,44 @@ __global__ void __launch_bounds__(512) k_eig_tri(Dev<R> d, int v, int w, int cap
   }
   __syncthreads();
   R* cf = reinterpret_cast<R*>(pp);  // Gram-Schmidt coefficients (k <= 512)
+  const int warp_id = tid >> 5, lane_id = tid & 31, nwarp = nth >> 5;
   for (int iter = 0; iter < TRI_INV_ITERS; ++iter) {
     if (tid < k) {
       const int c = tid, jj = perm[c], s0 = bstart[jj], e0 = bend[jj];
       const R l = lam[jj];
       // forward elimination with partial pivoting, right-hand side carried along
-      R cd = dg[s0] - l, cu = s0 + 1 < e0 ? bt[s0] : R(0), cr = Z[(int64_t)s0 * n + c];
+      R* zc = Z + (int64_t)c * n;  // this thread's column (column-major)
+      R* u0 = U0 + (int64_t)c * n;
+      R* u1 = U1 + (int64_t)c * n;
+      R* u2 = U2 + (int64_t)c * n;
+      R cd = dg[s0] - l, cu = s0 + 1 < e0 ? bt[s0] : R(0), cr = zc[s0];
       for (int i = s0; i + 1 < e0; ++i) {
         const R lo_ = bt[i], dn = dg[i + 1] - l, un = (i + 2 < e0) ? bt[i + 1] : R(0);
-        const R rn = Z[(int64_t)(i + 1) * n + c];
-        const int64_t at = (int64_t)i * n + c;
+        const R rn = zc[i + 1];
+        const int at = i;
         if (fabs(cd) >= fabs(lo_)) {
           const R piv = cd == R(0) ? epsR : cd;
           const R mlt = lo_ / piv;
-          U0[at] = piv;
-          U1[at] = cu;
-          U2[at] = R(0);
-          Z[at] = cr;
+          u0[at] = piv;
+          u1[at] = cu;
+          u2[at] = R(0);
+          zc[at] = cr;
           cd = dn - mlt * cu;
           cu = un;
           cr = rn - mlt * cr;
         } else {
           const R mlt = cd / lo_;
-          U0[at] = lo_;
-          U1[at] = dn;
-          U2[at] = un;
-          Z[at] = rn;
+          u0[at] = lo_;
+          u1[at] = dn;
+          u2[at] = un;
+          zc[at] = rn;
           cd = cu - mlt * dn;
           cu = -mlt * un;
           cr = cr - mlt * rn;
         }
       }
-      U0[(int64_t)(e0 - 1) * n + c] = cd;
-      Z[(int64_t)(e0 - 1) * n + c] = cr;
+      u0[e0 - 1] = cd;
+      zc[e0 - 1] = cr;
       // back substitution; pivots below eps |T| are replaced by eps |T|.
       // The solution grows by up to 1/eps per small pivot: whenever it
       // passes BIG, the solved part and the remaining right-hand side are
@@ -1317,29 +1333,29 @@ __global__ void __launch_bounds__(512) k_eig_tri(Dev<R> d, int v, int w, int cap
       const R BIG = sizeof(R) == 8 ? R(1e150) : R(1e15);
       R y1 = R(0), y2 = R(0), ymax = R(0);
       for (int i = e0 - 1; i >= s0; --i) {
-        const int64_t at = (int64_t)i * n + c;
-        R u = U0[at];
+        const int at = i;
+        R u = u0[at];
         if (fabs(u) < epsR) u = u < R(0) ? -epsR : epsR;
-        R y = Z[at];
-        if (i + 1 < e0) y -= U1[at] * y1;
-        if (i + 2 < e0) y -= U2[at] * y2;
+        R y = zc[at];
+        if (i + 1 < e0) y -= u1[at] * y1;
+        if (i + 2 < e0) y -= u2[at] * y2;
         y = y / u;
         if (!(fabs(y) <= BIG)) {
           const R f = fabs(y) > R(0) && fabs(y) <= BIG * BIG ? R(1) / fabs(y) : R(0);
           for (int t = s0; t < e0; ++t)
-            if (t != i) Z[(int64_t)t * n + c] *= f;
+            if (t != i) zc[t] *= f;
           y = f > R(0) ? y * f : (y > R(0) ? R(1) : R(-1));
           y1 *= f;
           y2 *= f;
           ymax *= f;
         }
-        Z[at] = y;
+        zc[at] = y;
         y2 = y1;
         y1 = y;
         ymax = fmax(ymax, fabs(y));
       }
       const R inv = ymax > R(0) && ymax < R(1e30) ? R(1) / ymax : R(1);
-      for (int i = s0; i < e0; ++i) Z[(int64_t)i * n + c] *= inv;
+      for (int i = s0; i < e0; ++i) zc[i] *= inv;
     }
     __syncthreads();
     // classical Gram-Schmidt, twice, columns in order
@@ -1347,25 +1363,28 @@ __global__ void __launch_bounds__(512) k_eig_tri(Dev<R> d, int v, int w, int cap
       const int jj = perm[a];
       for (int rep = 0; rep < 2; ++rep) {
         for (int attempt = 0; attempt < 2; ++attempt) {
-          for (int bb = tid; bb < a; bb += nth) {
+          // coefficients <z_b, z_a>: one warp per b, lanes over rows
+          for (int bb = warp_id; bb < a; bb += nwarp) {
             R acc = R(0);
-            for (int i = 0; i < n; ++i) acc += Z[(int64_t)i * n + bb] * Z[(int64_t)i * n + a];
-            cf[bb] = acc;
+            const R* zb = Z + (int64_t)bb * n;
+            const R* za = Z + (int64_t)a * n;
+            for (int i = lane_id; i < n; i += 32) acc += zb[i] * za[i];
+            acc = warp_sum(acc);
+            if (lane_id == 0) cf[bb] = acc;
           }
           __syncthreads();
           double n0 = 0.0, n1 = 0.0;
           for (int i = tid; i < n; i += nth) {
-            R* zi = Z + (int64_t)i * n;
-            R z = zi[a];
+            R z = Z[(int64_t)a * n + i];
             n0 += (double)z * z;
-            for (int bb = 0; bb < a; ++bb) z -= cf[bb] * zi[bb];
-            zi[a] = z;
+            for (int bb = 0; bb < a; ++bb) z -= cf[bb] * Z[(int64_t)bb * n + i];
+            Z[(int64_t)a * n + i] = z;
             n1 += (double)z * z;
           }
           const double2 nn = block_sum2(n0, n1, red);
           if (nn.y > 1e-6 * nn.x && nn.y > 0.0) {
             const R sc1 = (R)(1.0 / sqrt(nn.y));
-            for (int i = tid; i < n; i += nth) Z[(int64_t)i * n + a] *= sc1;
+            for (int i = tid; i < n; i += nth) Z[(int64_t)a * n + i] *= sc1;
             __syncthreads();
             break;
           }
@@ -1376,26 +1395,33 @@ __global__ void __launch_bounds__(512) k_eig_tri(Dev<R> d, int v, int w, int cap
       }
     }
   }
-  // Rayleigh-Ritz: TZ into U0, H = Z^T (TZ) into U1 (k x k), Q into U2
+  // Rayleigh-Ritz: TZ into U0 (column-major), H = Z^T (TZ) into U1 (k x k),
+  // Q into U2
   R* TZ = U0;
   R* H = U1;
   R* Q = U2;
   for (int idx = tid; idx < n * k; idx += nth) {
-    const int i = idx / k, c = idx - i * k;
-    R t = dg[i] * Z[(int64_t)i * n + c];
-    if (i > 0) t += bt[i - 1] * Z[(int64_t)(i - 1) * n + c];
-    if (i + 1 < n) t += bt[i] * Z[(int64_t)(i + 1) * n + c];
+    const int c = idx / n, i = idx - c * n;
+    const R* zc = Z + (int64_t)c * n;
+    R t = dg[i] * zc[i];
+    if (i > 0) t += bt[i - 1] * zc[i - 1];
+    if (i + 1 < n) t += bt[i] * zc[i + 1];
     TZ[idx] = t;
   }
+  for (int idx = tid; idx < k * k; idx += nth) Q[idx] = R((idx / k) == (idx % k));
   __syncthreads();
-  for (int idx = tid; idx < k * k; idx += nth) {
-    const int a = idx / k, c = idx - a * k;
-    Q[idx] = R(a == c);
+  for (int e = warp_id; e < k * k; e += nwarp) {  // one warp per entry, lanes over rows
+    const int a = e / k, c = e - a * k;
     if (c < a) continue;
     R acc = R(0);
-    for (int i = 0; i < n; ++i) acc += Z[(int64_t)i * n + a] * TZ[(int64_t)i * k + c];
-    H[a * k + c] = acc;
-    H[c * k + a] = acc;
+    const R* za = Z + (int64_t)a * n;
+    const R* tc = TZ + (int64_t)c * n;
+    for (int i = lane_id; i < n; i += 32) acc += za[i] * tc[i];
+    acc = warp_sum(acc);
+    if (lane_id == 0) {
+      H[a * k + c] = acc;
+      H[c * k + a] = acc;
+    }
   }
   __syncthreads();
   if (k > 1) {
@@ -1458,18 +1484,15 @@ __global__ void __launch_bounds__(512) k_eig_tri(Dev<R> d, int v, int w, int cap
       if (!__syncthreads_or(rotated)) break;
     }
   }
-  // Z_k Q into TZ (n x k), then back into Z's first k columns
+  // Z_k Q into TZ (column-major n x k), then back into Z's first k columns
   for (int idx = tid; idx < n * k; idx += nth) {
-    const int i = idx / k, c = idx - i * k;
+    const int c = idx / n, i = idx - c * n;
     R acc = R(0);
-    for (int a = 0; a < k; ++a) acc += Z[(int64_t)i * n + a] * Q[a * k + c];
+    for (int a = 0; a < k; ++a) acc += Z[(int64_t)a * n + i] * Q[a * k + c];
     TZ[idx] = acc;
   }
   __syncthreads();
-  for (int idx = tid; idx < n * k; idx += nth) {
-    const int i = idx / k, c = idx - i * k;
-    Z[(int64_t)i * n + c] = TZ[idx];
-  }
+  for (int idx = tid; idx < n * k; idx += nth) Z[idx] = TZ[idx];
   __syncthreads();
 
   // ---- 5. back-transformation V_k = H_0 ... H_{n-3} D Z_k (n x k in Vk),
@@ -1477,7 +1500,7 @@ __global__ void __launch_bounds__(512) k_eig_tri(Dev<R> d, int v, int w, int cap
   // H_j0 ... H_j1 = I - Vb Tb Vb^H, so Vk <- Vk - Vb (Tb (Vb^H Vk)).
   for (int idx = tid; idx < n * k; idx += nth) {
     const int x = idx / k, c = idx - x * k;
-    const R z = Z[(int64_t)x * n + c];
+    const R z = Z[(int64_t)c * n + x];
     Vk[idx] = {wk[x].x * z, wk[x].y * z};
   }
   cx<R>* Vb = reinterpret_cast<cx<R>*>(tau + 512);  // [TRI_NB][512] reflectors, by row
@@ -1618,7 +1641,7 @@ __global__ void __launch_bounds__(256) k_unorm(Dev<R> d, int v, int w) {
       d.disc[b] += dsc;
       scale = sqrt(fro2 / kept);
     }
-    if (!(kept > 0.0)) atomicOr(&d.err[b], ERR_ZERO_NORM);
+    if (!(kept > 0.0)) flag_err(d, b, ERR_ZERO_NORM);
     s_scale = scale;
   }
   __syncthreads();
@@ -1686,7 +1709,7 @@ __global__ void k_thread_leaf(Dev<R> d, int v, int leg, int side) {
   const int dl = D[2 * v], dr = D[2 * v + 1], du = D[v];
   const int cnt = dl * dr * 2 * du;
   if (cnt > d.wstride) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&d.err[b], ERR_CAPACITY);
+    if (blockIdx.x == 0 && threadIdx.x == 0) flag_err(d, b, ERR_CAPACITY);
     return;
   }
   const cx<R>* T = node_ptr(d, b, v);
@@ -1726,7 +1749,7 @@ __global__ void k_thread_node(Dev<R> d, int v, int leg) {
   const int ol = leg == 0 ? 2 * dl : dl, orr = leg == 1 ? 2 * dr : dr, ou = 2 * du;
   const int cnt = ol * orr * ou;
   if (cnt > d.wstride) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&d.err[b], ERR_CAPACITY);
+    if (blockIdx.x == 0 && threadIdx.x == 0) flag_err(d, b, ERR_CAPACITY);
     return;
   }
   const cx<R>* T = node_ptr(d, b, v);
@@ -1756,7 +1779,7 @@ __global__ void k_thread_lca(Dev<R> d, int v) {
   const int dl = ol / 2, dr = orr / 2;
   const int cnt = ol * orr * du;
   if (cnt > d.wstride) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&d.err[b], ERR_CAPACITY);
+    if (blockIdx.x == 0 && threadIdx.x == 0) flag_err(d, b, ERR_CAPACITY);
     return;
   }
   const cx<R>* T = node_ptr(d, b, v);
@@ -1934,7 +1957,7 @@ __global__ void k_measure(Dev<R> d, int q, int event, int recbit, int xbasis, in
     }
     d.rec[(int64_t)b * d.n_rec + recbit] = (uint8_t)mres;
     d.last[(int64_t)b * d.N + q] = (uint8_t)mres;
-    if (!(tot > 0.0)) atomicOr(&d.err[b], ERR_ZERO_NORM);
+    if (!(tot > 0.0)) flag_err(d, b, ERR_ZERO_NORM);
   }
 }
 
@@ -2129,6 +2152,7 @@ struct Engine {
   double* dGamma = nullptr;
   uint64_t* dTraj = nullptr;
   int32_t* dErr = nullptr;
+  int32_t* dErrStep = nullptr;
   double* dFrob = nullptr;
   int32_t* dTrunc = nullptr;
   uint8_t* dChoice = nullptr;
@@ -2242,6 +2266,7 @@ struct Engine {
     CK(cudaMalloc(&dGamma, sizeof(double) * B));
     CK(cudaMalloc(&dTraj, sizeof(uint64_t) * B));
     CK(cudaMalloc(&dErr, sizeof(int32_t) * B));
+    CK(cudaMalloc(&dErrStep, sizeof(int32_t) * B));
     CK(cudaMalloc(&dFrob, sizeof(double) * B));
     CK(cudaMalloc(&dTrunc, sizeof(int32_t) * B));
     CK(cudaMalloc(&dChoice, (size_t)std::max(1, c.n_events) * B));
@@ -2292,6 +2317,7 @@ struct Engine {
     dev.chi = chi;
     dev.noise = noise;
     dev.err = dErr;
+    dev.err_step = dErrStep;
     dev.frob = dFrob;
     dev.trunc = dTrunc;
     dev.ledger = dLedger;
@@ -2303,7 +2329,7 @@ struct Engine {
 
   void release() {
     void* ptrs[] = {dT, dW, dV, dR, dG, dTs, dOff, dDims, dSv, dPerm, dK, dN, dLogp, dDisc, dTies, dRec,
-                    dLast, dTheta, dGamma, dTraj, dErr, dFrob, dTrunc, dLeafdim, dOp1, dGroups,
+                    dLast, dTheta, dGamma, dTraj, dErr, dErrStep, dFrob, dTrunc, dLeafdim, dOp1, dGroups,
                     dLedger, dChoice};
     for (void* p : ptrs)
       if (p) cudaFree(p);
@@ -2313,12 +2339,14 @@ struct Engine {
   ttn_status launch(int nb, int stop_step) {
     const int L = c.L;
     dim3 gi(1, nb);
+    dev.cur_step = -1;
     k_init<R><<<dim3(std::max(1, ceil_div(2 * L, 256)), nb), 256, 0, st>>>(dev, dLeafdim, nb);
     CK(cudaGetLastError());
     (void)gi;
     const int nsteps = stop_step < 0 ? (int)prog.steps.size() : stop_step;
     for (int si = 0; si < nsteps; ++si) {
       const Step& s = prog.steps[si];
+      dev.cur_step = si;
       switch (s.kind) {
         case S_MOVE: {
           const int v = s.a, w = s.b;
@@ -2513,6 +2541,8 @@ static ttn_status run_impl(const ttn_circuit& c, const RunRequest& rq, RunOutput
     if (out.discarded) CK(cp(out.discarded + t0, eng.dDisc, sizeof(double) * nb));
     if (out.near_ties) CK(cp(out.near_ties + t0, eng.dTies, sizeof(int32_t) * nb));
     CK(cudaMemcpyAsync(err.data(), eng.dErr, sizeof(int32_t) * nb, cudaMemcpyDeviceToHost, st));
+    std::vector<int32_t> err_step(nb, -1);
+    CK(cudaMemcpyAsync(err_step.data(), eng.dErrStep, sizeof(int32_t) * nb, cudaMemcpyDeviceToHost, st));
     // score of each trajectory: replay its choices at strength +- h
     if (rq.grad_wrt >= 0 && !rq.debug_amps) {
       std::vector<double> lp(nb), lm(nb);
@@ -2562,10 +2592,26 @@ static ttn_status run_impl(const ttn_circuit& c, const RunRequest& rq, RunOutput
     eng.collect_profile();
     for (int i = 0; i < nb; ++i) out.err_flags |= err[i];
     if (out.err_flags & (ERR_CAPACITY | ERR_ZERO_NORM | ERR_NAN)) {
+      // first failing trajectory: which step of the program raised it
+      std::string where;
+      for (int i = 0; i < nb; ++i)
+        if (err[i] & (ERR_CAPACITY | ERR_ZERO_NORM | ERR_NAN)) {
+          static const char* kinds[] = {"move", "thread-leaf", "thread-node", "thread-lca",
+                                        "gate-node", "single-qubit layer", "measure", "damping"};
+          const int si = err_step[i];
+          where = " (trajectory " + std::to_string(rq.first_traj + t0 + i) + ", flags " + std::to_string(err[i]);
+          if (si >= 0 && si < (int)prog.steps.size()) {
+            const Step& s = prog.steps[si];
+            where += ", step " + std::to_string(si) + " " + kinds[s.kind] + " a=" + std::to_string(s.a) +
+                     " b=" + std::to_string(s.b);
+          }
+          where += ")";
+          break;
+        }
       eng.release();
       set_error(std::string("engine: ") +
                 ((out.err_flags & ERR_CAPACITY) ? "tensor exceeded its slot capacity"
-                 : (out.err_flags & ERR_NAN) ? "non-finite singular value" : "zero-norm state"));
+                 : (out.err_flags & ERR_NAN) ? "non-finite singular value" : "zero-norm state") + where);
       return TTN_ECUDA;
     }
   }
