@@ -129,7 +129,7 @@ struct Dev {
   int32_t* trunc;        // [B] 1 if that move truncated
   int max_sweeps;
   int32_t* err;          // [B] error flags
-  int32_t* err_step;     // [B] step index of the first error (-1: none)
+  int32_t* err_step;     // [B][2] step of the first fatal error, of the first non-convergence
   int cur_step;          // step of the program being launched
 };
 
@@ -139,7 +139,7 @@ enum : int32_t { ERR_ZERO_NORM = 1, ERR_NO_CONVERGE = 2, ERR_CAPACITY = 4, ERR_N
 template <typename R>
 __device__ __forceinline__ void flag_err(const Dev<R>& d, int b, int32_t code) {
   atomicOr(&d.err[b], code);
-  if (code != ERR_NO_CONVERGE) atomicCAS(&d.err_step[b], -1, d.cur_step);
+  atomicCAS(&d.err_step[b * 2 + (code == ERR_NO_CONVERGE ? 1 : 0)], -1, d.cur_step);
 }
 
 // Gram matrices up to this size are diagonalised in shared memory (k_eig);
@@ -186,7 +186,8 @@ __global__ void k_init(Dev<R> d, const int32_t* leafdim, int B) {
     d.disc[b] = 0.0;
     d.ties[b] = 0;
     d.err[b] = 0;
-    d.err_step[b] = -1;
+    d.err_step[2 * b] = -1;
+    d.err_step[2 * b + 1] = -1;
   }
   for (int i = threadIdx.x + blockIdx.x * blockDim.x; i < d.N; i += blockDim.x * gridDim.x)
     d.last[(int64_t)b * d.N + i] = 0;
@@ -2266,7 +2267,7 @@ struct Engine {
     CK(cudaMalloc(&dGamma, sizeof(double) * B));
     CK(cudaMalloc(&dTraj, sizeof(uint64_t) * B));
     CK(cudaMalloc(&dErr, sizeof(int32_t) * B));
-    CK(cudaMalloc(&dErrStep, sizeof(int32_t) * B));
+    CK(cudaMalloc(&dErrStep, sizeof(int32_t) * 2 * B));
     CK(cudaMalloc(&dFrob, sizeof(double) * B));
     CK(cudaMalloc(&dTrunc, sizeof(int32_t) * B));
     CK(cudaMalloc(&dChoice, (size_t)std::max(1, c.n_events) * B));
@@ -2541,8 +2542,8 @@ static ttn_status run_impl(const ttn_circuit& c, const RunRequest& rq, RunOutput
     if (out.discarded) CK(cp(out.discarded + t0, eng.dDisc, sizeof(double) * nb));
     if (out.near_ties) CK(cp(out.near_ties + t0, eng.dTies, sizeof(int32_t) * nb));
     CK(cudaMemcpyAsync(err.data(), eng.dErr, sizeof(int32_t) * nb, cudaMemcpyDeviceToHost, st));
-    std::vector<int32_t> err_step(nb, -1);
-    CK(cudaMemcpyAsync(err_step.data(), eng.dErrStep, sizeof(int32_t) * nb, cudaMemcpyDeviceToHost, st));
+    std::vector<int32_t> err_step(2 * nb, -1);
+    CK(cudaMemcpyAsync(err_step.data(), eng.dErrStep, sizeof(int32_t) * 2 * nb, cudaMemcpyDeviceToHost, st));
     // score of each trajectory: replay its choices at strength +- h
     if (rq.grad_wrt >= 0 && !rq.debug_amps) {
       std::vector<double> lp(nb), lm(nb);
@@ -2598,12 +2599,14 @@ static ttn_status run_impl(const ttn_circuit& c, const RunRequest& rq, RunOutput
         if (err[i] & (ERR_CAPACITY | ERR_ZERO_NORM | ERR_NAN)) {
           static const char* kinds[] = {"move", "thread-leaf", "thread-node", "thread-lca",
                                         "gate-node", "single-qubit layer", "measure", "damping"};
-          const int si = err_step[i];
           where = " (trajectory " + std::to_string(rq.first_traj + t0 + i) + ", flags " + std::to_string(err[i]);
-          if (si >= 0 && si < (int)prog.steps.size()) {
-            const Step& s = prog.steps[si];
-            where += ", step " + std::to_string(si) + " " + kinds[s.kind] + " a=" + std::to_string(s.a) +
-                     " b=" + std::to_string(s.b);
+          for (int which = 0; which < 2; ++which) {
+            const int si = err_step[2 * i + which];
+            if (si >= 0 && si < (int)prog.steps.size()) {
+              const Step& s = prog.steps[si];
+              where += std::string(which ? "; first non-convergence" : "") + ", step " + std::to_string(si) +
+                       " " + kinds[s.kind] + " a=" + std::to_string(s.a) + " b=" + std::to_string(s.b);
+            }
           }
           where += ")";
           break;
