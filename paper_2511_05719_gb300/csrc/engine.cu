@@ -147,7 +147,7 @@ __device__ __forceinline__ void flag_err(const Dev<R>& d, int b, int32_t code) {
 static constexpr int EIG_SMEM_MAX = 131072;
 static constexpr int TRI_UNROLL = 16;  // loads in flight per thread in L2-resident sweeps
 static constexpr int TRI_NB = 8;       // reflectors per compact-WY block of the back-transformation
-static constexpr int TRI_INV_ITERS = 4;  // inverse-iteration / Gram-Schmidt rounds
+static constexpr int TRI_INV_ITERS = 2;  // inverse-iteration / orthonormalisation rounds
 template <typename R>
 constexpr int tri_smem_bytes() {
   return 512 * (5 * 2 * (int)sizeof(R) + 3 * (int)sizeof(R)) + 2 * TRI_NB * 512 * 2 * (int)sizeof(R);
@@ -1044,9 +1044,8 @@ __device__ void tri_reflector(cx<R>* A, int n, int c, cx<R>* vout, R* tau, cx<R>
 //  3. eigenvalues by bisection on Sturm counts (thread per eigenvalue);
 //  4. eigenvectors of the kept eigenvalues by inverse iteration on the
 //     pivoted LU factors of T - lambda I restricted to the eigenvalue's block
-//     (thread per vector), alternating with classical Gram-Schmidt applied
-//     twice (as LAPACK's stein re-orthogonalises clusters), then a
-//     Rayleigh-Ritz step on the kept subspace;
+//     (thread per vector), alternating with Cholesky QR applied twice, then
+//     a Rayleigh-Ritz step on the kept subspace;
 //  5. back-transformation by the stored reflectors.
 // (Golub & Van Loan, Matrix Computations, Ch. 8.)  Selection and output as in
 // k_eig: V_k (n x k, row-major) into G.
@@ -1266,12 +1265,11 @@ __global__ void __launch_bounds__(512) k_eig_tri(Dev<R> d, int v, int w, int cap
                (double)sizeof(cx<R>) * ((double)n * n + (double)n * k));
 
   // ---- 4. eigenvectors of the kept eigenvalues.  Inverse iteration (thread c
-  // for kept column c, eigenvalue perm[c], on that eigenvalue's block)
-  // alternates with classical Gram-Schmidt applied twice in column order; a
-  // column that loses almost all of its norm there restarts from a fresh
-  // vector.  Eigenvalues closer than the arithmetic resolves (flat spectra of
-  // stabiliser-like states) thus still get independent vectors spanning their
-  // invariant subspace, and a Rayleigh-Ritz step on the kept subspace
+  // for kept column c, shift = its own eigenvalue perm[c], on that
+  // eigenvalue's block) alternates with Cholesky QR applied twice.  Vectors
+  // of eigenvalues closer than the arithmetic resolves (flat spectra of
+  // stabiliser-like states) come out as independent combinations spanning
+  // their invariant subspace, and a Rayleigh-Ritz step on the kept subspace
   // (H = Z^T T Z = Q L Q^T by cyclic Jacobi, Z <- Z Q) diagonalises it.
   auto start_vec = [&](int c, int salt, int s0, int e0) {
     for (int i = tid; i < n; i += nth) {
@@ -1288,7 +1286,6 @@ __global__ void __launch_bounds__(512) k_eig_tri(Dev<R> d, int v, int w, int cap
     start_vec(c, 0, bstart[jj], bend[jj]);
   }
   __syncthreads();
-  R* cf = reinterpret_cast<R*>(pp);  // Gram-Schmidt coefficients (k <= 512)
   const int warp_id = tid >> 5, lane_id = tid & 31, nwarp = nth >> 5;
   for (int iter = 0; iter < TRI_INV_ITERS; ++iter) {
     if (tid < k) {
@@ -1359,41 +1356,44 @@ __global__ void __launch_bounds__(512) k_eig_tri(Dev<R> d, int v, int w, int cap
       for (int i = s0; i < e0; ++i) zc[i] *= inv;
     }
     __syncthreads();
-    // classical Gram-Schmidt, twice, columns in order
-    for (int a = 0; a < k; ++a) {
-      const int jj = perm[a];
-      for (int rep = 0; rep < 2; ++rep) {
-        for (int attempt = 0; attempt < 2; ++attempt) {
-          // coefficients <z_b, z_a>: one warp per b, lanes over rows
-          for (int bb = warp_id; bb < a; bb += nwarp) {
-            R acc = R(0);
-            const R* zb = Z + (int64_t)bb * n;
-            const R* za = Z + (int64_t)a * n;
-            for (int i = lane_id; i < n; i += 32) acc += zb[i] * za[i];
-            acc = warp_sum(acc);
-            if (lane_id == 0) cf[bb] = acc;
-          }
-          __syncthreads();
-          double n0 = 0.0, n1 = 0.0;
-          for (int i = tid; i < n; i += nth) {
-            R z = Z[(int64_t)a * n + i];
-            n0 += (double)z * z;
-            for (int bb = 0; bb < a; ++bb) z -= cf[bb] * Z[(int64_t)bb * n + i];
-            Z[(int64_t)a * n + i] = z;
-            n1 += (double)z * z;
-          }
-          const double2 nn = block_sum2(n0, n1, red);
-          if (nn.y > 1e-6 * nn.x && nn.y > 0.0) {
-            const R sc1 = (R)(1.0 / sqrt(nn.y));
-            for (int i = tid; i < n; i += nth) Z[(int64_t)a * n + i] *= sc1;
-            __syncthreads();
-            break;
-          }
-          // dependent on the previous columns: restart from a fresh vector
-          start_vec(a, 1 + iter * 4 + rep * 2 + attempt, bstart[jj], bend[jj]);
-          __syncthreads();
+    // Cholesky QR, twice: S = Z^T Z = L L^T (S, L in U1), Z <- Z L^-T
+    for (int rep = 0; rep < 2 && k > 1; ++rep) {
+      R* S = U1;
+      for (int e = warp_id; e < k * k; e += nwarp) {  // one warp per entry
+        const int p = e / k, q = e - p * k;
+        if (q > p) continue;
+        R acc = R(0);
+        const R* zp = Z + (int64_t)p * n;
+        const R* zq = Z + (int64_t)q * n;
+        for (int i = lane_id; i < n; i += 32) acc += zp[i] * zq[i];
+        acc = warp_sum(acc);
+        if (lane_id == 0) S[p * k + q] = acc;
+      }
+      __syncthreads();
+      for (int j = 0; j < k; ++j) {
+        R piv = S[j * k + j];
+        if (!(piv > R(1e-12))) piv = R(1e-12);
+        const R rj = sqrt(piv), irj = R(1) / rj;
+        __syncthreads();
+        if (tid == 0) S[j * k + j] = rj;
+        for (int p = j + 1 + tid; p < k; p += nth) S[p * k + j] *= irj;
+        __syncthreads();
+        const int t = k - j - 1;
+        for (int idx = tid; idx < t * t; idx += nth) {
+          const int p = j + 1 + idx / t, q = j + 1 + idx % t;
+          if (q > p) continue;
+          S[p * k + q] -= S[p * k + j] * S[q * k + j];
+        }
+        __syncthreads();
+      }
+      for (int i = tid; i < n; i += nth) {  // row i: y L^T = z
+        for (int q = 0; q < k; ++q) {
+          R y = Z[(int64_t)q * n + i];
+          for (int p = 0; p < q; ++p) y -= Z[(int64_t)p * n + i] * S[q * k + p];
+          Z[(int64_t)q * n + i] = y / S[q * k + q];
         }
       }
+      __syncthreads();
     }
   }
   // Rayleigh-Ritz: TZ into U0 (column-major), H = Z^T (TZ) into U1 (k x k),
@@ -1604,62 +1604,99 @@ __global__ void __launch_bounds__(512) k_eig_tri(Dev<R> d, int v, int w, int cap
 
 // Exact singular values of the kept columns: Y = M V_k was written into T_v;
 // s_c = |Y_c|, U_c = Y_c / s_c, R_c = s_c V_c^H (renormalised after a
-// truncation, the discarded weight 1 - sum s_c^2 / |M|_F^2 recorded).
+// truncation, the discarded weight 1 - sum s_c^2 / |M|_F^2 recorded), spread
+// over the whole grid: k_unorm_sums accumulates s_c^2 per column
+// (shared-memory partials, one atomic per column and block), k_unorm_scale
+// decides the renormalisation, k_unorm_apply scales U and forms R.  The column of element a of T_v in its
+// storage order: leg 2 (i, c): a % k; leg 0 (c, i): a / m; leg 1 (l, c, u):
+// (a / du) % k.
 template <typename R>
-__global__ void __launch_bounds__(256) k_unorm(Dev<R> d, int v, int w) {
-  const int b = blockIdx.x;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+__device__ __forceinline__ void unorm_dims(const Dev<R>& d, int b, int v, int w, int& leg, int& n, int& k,
+                                           int& m, int& du) {
   const int* D = d.dims + b * d.ds;
-  const int leg = (w == 2 * v) ? 0 : ((w == 2 * v + 1) ? 1 : 2);
-  const int n = d.nold[b], k = d.knew[b];
-  if (k <= 0) return;
+  leg = (w == 2 * v) ? 0 : ((w == 2 * v + 1) ? 1 : 2);
+  n = d.nold[b];
+  k = d.knew[b];
   const int dl0 = D[2 * v], dr0 = D[2 * v + 1], du0 = D[v];
-  const int dl = leg == 0 ? n : dl0, dr = leg == 1 ? n : dr0, du = leg == 2 ? n : du0;
-  const int m = dl * dr * du / n;
-  cx<R>* T = node_ptr(d, b, v);
+  const int dl = leg == 0 ? n : dl0, dr = leg == 1 ? n : dr0;
+  du = leg == 2 ? n : du0;
+  m = k > 0 ? dl * dr * du / n : 0;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_unorm_sums(Dev<R> d, int v, int w) {
+  const int b = blockIdx.y;
+  int leg, n, k, m, du;
+  unorm_dims(d, b, v, w, leg, n, k, m, du);
+  if (k <= 0 || k > 512) return;
+  __shared__ double part[512];
+  for (int c = threadIdx.x; c < k; c += blockDim.x) part[c] = 0.0;
+  __syncthreads();
+  const cx<R>* T = node_ptr(d, b, v);
+  const int64_t tot = (int64_t)m * k;
+  for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < tot; a += (int64_t)gridDim.x * blockDim.x) {
+    const int c = leg == 2 ? (int)(a % k) : (leg == 0 ? (int)(a / m) : (int)((a / du) % k));
+    atomicAdd(&part[c], (double)cabs2(T[a]));
+  }
+  __syncthreads();
+  double* acc = d.sv + (int64_t)b * d.nmax;
+  for (int c = threadIdx.x; c < k; c += blockDim.x)
+    if (part[c] != 0.0) atomicAdd(&acc[c], part[c]);
+}
+
+template <typename R>
+__global__ void k_unorm_zero(Dev<R> d, int B) {
+  const int b = blockIdx.x;
+  if (b >= B) return;
+  for (int c = threadIdx.x; c < d.nmax; c += blockDim.x) d.sv[(int64_t)b * d.nmax + c] = 0.0;
+}
+
+template <typename R>
+__global__ void k_unorm_scale(Dev<R> d, int v, int w, int B) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  int leg, n, k, m, du;
+  unorm_dims(d, b, v, w, leg, n, k, m, du);
+  if (k <= 0) return;
   double* sv = d.sv + (int64_t)b * d.nmax;
-  __shared__ double s_scale;
-  auto addr = [&](int i, int c) {
-    if (leg == 2) return i * k + c;
-    if (leg == 0) return c * m + i;
-    int l = i / du, u = i - l * du;
-    return (l * k + c) * du + u;
-  };
-  for (int c = warp; c < k; c += nwarps) {
-    double acc = 0.0;
-    for (int i = lane; i < m; i += 32) acc += (double)cabs2(T[addr(i, c)]);
-    acc = warp_sum(acc);
-    if (lane == 0) sv[c] = sqrt(acc);
+  double kept = 0.0;
+  for (int c = 0; c < k; ++c) {
+    kept += sv[c];
+    sv[c] = sqrt(sv[c]);
   }
-  __syncthreads();
-  if (tid == 0) {
-    double kept = 0.0;
-    for (int c = 0; c < k; ++c) kept += sv[c] * sv[c];
-    const double fro2 = d.frob[b];
-    double scale = 1.0;
-    if (d.trunc[b] && fro2 > 0.0 && kept > 0.0) {
-      const double dsc = fmax(0.0, 1.0 - kept / fro2);
-      d.disc[b] += dsc;
-      scale = sqrt(fro2 / kept);
-    }
-    if (!(kept > 0.0)) flag_err(d, b, ERR_ZERO_NORM);
-    s_scale = scale;
+  const double fro2 = d.frob[b];
+  double scale = 1.0;
+  if (d.trunc[b] && fro2 > 0.0 && kept > 0.0) {
+    d.disc[b] += fmax(0.0, 1.0 - kept / fro2);
+    scale = sqrt(fro2 / kept);
   }
-  __syncthreads();
-  for (int idx = tid; idx < m * k; idx += blockDim.x) {
-    const int c = idx / m, i = idx - c * m;
-    const double s = sv[c];
-    const int a = addr(i, c);
-    T[a] = cscale(T[a], s > 0.0 ? (R)(1.0 / s) : R(0));
+  if (!(kept > 0.0)) flag_err(d, b, ERR_ZERO_NORM);
+  d.frob[b] = scale;  // consumed by k_unorm_apply
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_unorm_apply(Dev<R> d, int v, int w) {
+  const int b = blockIdx.y;
+  int leg, n, k, m, du;
+  unorm_dims(d, b, v, w, leg, n, k, m, du);
+  if (k <= 0) return;
+  const double* sv = d.sv + (int64_t)b * d.nmax;
+  cx<R>* T = node_ptr(d, b, v);
+  const int64_t tot = (int64_t)m * k;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < tot; a += stride) {
+    const int c = leg == 2 ? (int)(a % k) : (leg == 0 ? (int)(a / m) : (int)((a / du) % k));
+    const double sc = sv[c];
+    T[a] = cscale(T[a], sc > 0.0 ? (R)(1.0 / sc) : R(0));
   }
   const cx<R>* Vk = d.G + (int64_t)b * d.vstride;
   cx<R>* Rm = d.Rm + (int64_t)b * d.vstride;
-  const R sc = (R)s_scale;
-  for (int idx = tid; idx < k * n; idx += blockDim.x) {
-    const int c = idx / n, x = idx - c * n;
+  const R scale = (R)d.frob[b];
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < (int64_t)k * n; idx += stride) {
+    const int c = (int)(idx / n), x = (int)(idx - (int64_t)c * n);
     const cx<R> vv = Vk[(int64_t)x * k + c];
-    const R s = (R)sv[c] * sc;
-    Rm[idx] = {s * vv.x, -s * vv.y};
+    const R sc = (R)sv[c] * scale;
+    Rm[idx] = {sc * vv.x, -sc * vv.y};
   }
 }
 
@@ -2380,7 +2417,13 @@ struct Engine {
               if (tc) k_form_u<R, true><<<gf, 256, 0, st>>>(dev, v, w);
               else k_form_u<R, false><<<gf, 256, 0, st>>>(dev, v, w);
             });
-            timed(KC_OTHER, [&] { k_unorm<R><<<nb, 256, 0, st>>>(dev, v, w); });
+            timed(KC_OTHER, [&] {
+              const int gx = (int)std::min<int64_t>(std::max<int64_t>(1, mmax * nmv / 4096), 512);
+              k_unorm_zero<R><<<nb, 256, 0, st>>>(dev, nb);
+              k_unorm_sums<R><<<dim3(gx, nb), 256, 0, st>>>(dev, v, w);
+              k_unorm_scale<R><<<ceil_div(nb, 128), 128, 0, st>>>(dev, v, w, nb);
+              k_unorm_apply<R><<<dim3(gx, nb), 256, 0, st>>>(dev, v, w);
+            });
           } else {
             timed(KC_SVD, [&] { k_svd_move<R><<<nb, 256, 0, st>>>(dev, v, w, s.c); });
           }
