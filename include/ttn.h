@@ -82,7 +82,11 @@ typedef struct {
   const double* theta_per_traj;  /* optional [n_traj], overrides theta    */
   const double* gamma_per_traj;  /* optional [n_traj], overrides gamma    */
   int32_t svd_mode;              /* factorisation of a centre move:
-                                    0 auto (FP32 bonds above 64: Gram),
+                                    0 auto (FP64: Jacobi; FP32: Gram for
+                                      bonds above 64 and, with the
+                                      tridiagonal eigensolver, for every
+                                      move of a tensor of 2^17 elements or
+                                      more),
                                     1 one-sided Jacobi on the tensor,
                                     2 Gram matrix; eigensolver two-sided
                                       Jacobi in shared memory up to 128 KB

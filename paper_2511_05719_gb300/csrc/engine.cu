@@ -148,6 +148,8 @@ static constexpr int EIG_SMEM_MAX = 131072;
 static constexpr int TRI_UNROLL = 16;  // loads in flight per thread in L2-resident sweeps
 static constexpr int TRI_NB = 8;       // reflectors per compact-WY block of the back-transformation
 static constexpr int TRI_INV_ITERS = 2;  // inverse-iteration / orthonormalisation rounds
+// Moves whose tensor capacity reaches this many elements count as large.
+static constexpr int64_t BIG_MOVE = (int64_t)1 << 17;
 template <typename R>
 constexpr int tri_smem_bytes() {
   return 512 * (5 * 2 * (int)sizeof(R) + 3 * (int)sizeof(R)) + 2 * TRI_NB * 512 * 2 * (int)sizeof(R);
@@ -2390,7 +2392,17 @@ struct Engine {
           const int v = s.a, w = s.b;
           const int bond = (w == v / 2) ? v : w;
           const int64_t nmv = 2 * (int64_t)bcap[bond];
-          const bool gram = dev.svd_mode >= 2 || (dev.svd_mode == 0 && sizeof(R) == 4 && nmv > 64);
+          // FP32 auto: the Gram path for bonds above 64 and for every move of a
+          // large tensor (there the one-sided Jacobi's FP32 orthogonality test
+          // is not reachable and its iteration stalls); FP64 auto: Jacobi.
+          const int lv0 = (w == 2 * v) ? 0 : ((w == 2 * v + 1) ? 1 : 2);
+          const int64_t cc3[3] = {2 * (int64_t)bcap[2 * v], 2 * (int64_t)bcap[2 * v + 1],
+                                  v == 1 ? 1 : 2 * (int64_t)bcap[v]};
+          int64_t mcap = 1;
+          for (int t = 0; t < 3; ++t)
+            if (t != lv0) mcap *= cc3[t];
+          const bool big = mcap * nmv >= BIG_MOVE;
+          const bool gram = dev.svd_mode >= 2 || (dev.svd_mode == 0 && sizeof(R) == 4 && (nmv > 64 || big));
           // contractions of this move on the tensor cores (FP32 only)
           const bool tc = sizeof(R) == 4 && (gemm_mode == 2 || (gemm_mode == 0 && gram));
           if (gram) {
@@ -2406,7 +2418,8 @@ struct Engine {
               if (tc) k_gram<R, true><<<dim3(tn, tn, nb), 256, 0, st>>>(dev, v, w);
               else k_gram<R, false><<<dim3(tn, tn, nb), 256, 0, st>>>(dev, v, w);
             });
-            if (dev.svd_mode != 3 && nmv * nmv * (int64_t)sizeof(cx<R>) <= EIG_SMEM_MAX) {
+            if (dev.svd_mode != 3 && !(dev.svd_mode == 0 && big) &&
+                nmv * nmv * (int64_t)sizeof(cx<R>) <= EIG_SMEM_MAX) {
               dev.eig_smem_bytes = (int)(nmv * nmv * (int64_t)sizeof(cx<R>));
               timed(KC_EIG, [&] { k_eig<R><<<nb, 512, dev.eig_smem_bytes, st>>>(dev, v, w, s.c); });
             } else {
