@@ -194,7 +194,7 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    B = a.batch if a.batch > 0 else (64 if a.distance >= 7 else 512)
+    B = a.batch if a.batch > 0 else (16 if a.distance >= 7 else 512)
     circ = P.Circuit(a.distance, a.rounds, layout="optimized")
     thetas = WL.theta_sweep_per_traj(B, WL.M3["thetas"])
     stream = torch.cuda.Stream()

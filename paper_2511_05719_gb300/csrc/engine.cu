@@ -1046,8 +1046,9 @@ __device__ void tri_reflector(cx<R>* A, int n, int c, cx<R>* vout, R* tau, cx<R>
 //  3. eigenvalues by bisection on Sturm counts (thread per eigenvalue);
 //  4. eigenvectors of the kept eigenvalues by inverse iteration on the
 //     pivoted LU factors of T - lambda I restricted to the eigenvalue's block
-//     (thread per vector), alternating with Cholesky QR applied twice, then
-//     a Rayleigh-Ritz step on the kept subspace;
+//     (thread per vector), alternating with classical Gram-Schmidt applied
+//     twice (as LAPACK's stein re-orthogonalises clusters), then a
+//     Rayleigh-Ritz step on the kept subspace;
 //  5. back-transformation by the stored reflectors.
 // (Golub & Van Loan, Matrix Computations, Ch. 8.)  Selection and output as in
 // k_eig: V_k (n x k, row-major) into G.
@@ -1268,11 +1269,13 @@ __global__ void __launch_bounds__(512) k_eig_tri(Dev<R> d, int v, int w, int cap
 
   // ---- 4. eigenvectors of the kept eigenvalues.  Inverse iteration (thread c
   // for kept column c, shift = its own eigenvalue perm[c], on that
-  // eigenvalue's block) alternates with Cholesky QR applied twice.  Vectors
-  // of eigenvalues closer than the arithmetic resolves (flat spectra of
-  // stabiliser-like states) come out as independent combinations spanning
-  // their invariant subspace, and a Rayleigh-Ritz step on the kept subspace
-  // (H = Z^T T Z = Q L Q^T by cyclic Jacobi, Z <- Z Q) diagonalises it.
+  // eigenvalue's block) alternates with classical Gram-Schmidt applied twice
+  // in column order; a column that loses almost all of its norm there
+  // restarts from a fresh vector.  Eigenvalues closer than the arithmetic
+  // resolves (flat spectra of stabiliser-like states) thus still get
+  // independent vectors spanning their invariant subspace, and a
+  // Rayleigh-Ritz step on the kept subspace (H = Z^T T Z = Q L Q^T by cyclic
+  // Jacobi, Z <- Z Q) diagonalises it.
   auto start_vec = [&](int c, int salt, int s0, int e0) {
     for (int i = tid; i < n; i += nth) {
       uint32_t h = (uint32_t)(i + 7919 * salt) * 0x9E3779B1u ^ ((uint32_t)c + 0x7F4A7C15u) * 0x85EBCA77u;
@@ -1288,6 +1291,7 @@ __global__ void __launch_bounds__(512) k_eig_tri(Dev<R> d, int v, int w, int cap
     start_vec(c, 0, bstart[jj], bend[jj]);
   }
   __syncthreads();
+  R* cf = reinterpret_cast<R*>(pp);  // Gram-Schmidt coefficients (k <= 512)
   const int warp_id = tid >> 5, lane_id = tid & 31, nwarp = nth >> 5;
   for (int iter = 0; iter < TRI_INV_ITERS; ++iter) {
     if (tid < k) {
@@ -1358,44 +1362,41 @@ __global__ void __launch_bounds__(512) k_eig_tri(Dev<R> d, int v, int w, int cap
       for (int i = s0; i < e0; ++i) zc[i] *= inv;
     }
     __syncthreads();
-    // Cholesky QR, twice: S = Z^T Z = L L^T (S, L in U1), Z <- Z L^-T
-    for (int rep = 0; rep < 2 && k > 1; ++rep) {
-      R* S = U1;
-      for (int e = warp_id; e < k * k; e += nwarp) {  // one warp per entry
-        const int p = e / k, q = e - p * k;
-        if (q > p) continue;
-        R acc = R(0);
-        const R* zp = Z + (int64_t)p * n;
-        const R* zq = Z + (int64_t)q * n;
-        for (int i = lane_id; i < n; i += 32) acc += zp[i] * zq[i];
-        acc = warp_sum(acc);
-        if (lane_id == 0) S[p * k + q] = acc;
-      }
-      __syncthreads();
-      for (int j = 0; j < k; ++j) {
-        R piv = S[j * k + j];
-        if (!(piv > R(1e-12))) piv = R(1e-12);
-        const R rj = sqrt(piv), irj = R(1) / rj;
-        __syncthreads();
-        if (tid == 0) S[j * k + j] = rj;
-        for (int p = j + 1 + tid; p < k; p += nth) S[p * k + j] *= irj;
-        __syncthreads();
-        const int t = k - j - 1;
-        for (int idx = tid; idx < t * t; idx += nth) {
-          const int p = j + 1 + idx / t, q = j + 1 + idx % t;
-          if (q > p) continue;
-          S[p * k + q] -= S[p * k + j] * S[q * k + j];
-        }
-        __syncthreads();
-      }
-      for (int i = tid; i < n; i += nth) {  // row i: y L^T = z
-        for (int q = 0; q < k; ++q) {
-          R y = Z[(int64_t)q * n + i];
-          for (int p = 0; p < q; ++p) y -= Z[(int64_t)p * n + i] * S[q * k + p];
-          Z[(int64_t)q * n + i] = y / S[q * k + q];
+    // classical Gram-Schmidt, twice, columns in order
+    for (int a = 0; a < k; ++a) {
+      const int jj = perm[a];
+      for (int rep = 0; rep < 2; ++rep) {
+        for (int attempt = 0; attempt < 2; ++attempt) {
+          // coefficients <z_b, z_a>: one warp per b, lanes over rows
+          for (int bb = warp_id; bb < a; bb += nwarp) {
+            R acc = R(0);
+            const R* zb = Z + (int64_t)bb * n;
+            const R* za = Z + (int64_t)a * n;
+            for (int i = lane_id; i < n; i += 32) acc += zb[i] * za[i];
+            acc = warp_sum(acc);
+            if (lane_id == 0) cf[bb] = acc;
+          }
+          __syncthreads();
+          double n0 = 0.0, n1 = 0.0;
+          for (int i = tid; i < n; i += nth) {
+            R z = Z[(int64_t)a * n + i];
+            n0 += (double)z * z;
+            for (int bb = 0; bb < a; ++bb) z -= cf[bb] * Z[(int64_t)bb * n + i];
+            Z[(int64_t)a * n + i] = z;
+            n1 += (double)z * z;
+          }
+          const double2 nn = block_sum2(n0, n1, red);
+          if (nn.y > 1e-6 * nn.x && nn.y > 0.0) {
+            const R sc1 = (R)(1.0 / sqrt(nn.y));
+            for (int i = tid; i < n; i += nth) Z[(int64_t)a * n + i] *= sc1;
+            __syncthreads();
+            break;
+          }
+          // dependent on the previous columns: restart from a fresh vector
+          start_vec(a, 1 + iter * 4 + rep * 2 + attempt, bstart[jj], bend[jj]);
+          __syncthreads();
         }
       }
-      __syncthreads();
     }
   }
   // Rayleigh-Ritz: TZ into U0 (column-major), H = Z^T (TZ) into U1 (k x k),
@@ -1431,7 +1432,7 @@ __global__ void __launch_bounds__(512) k_eig_tri(Dev<R> d, int v, int w, int cap
     __shared__ R rc[256], rs[256];
     __shared__ int rp[256], rq[256];
     const int ke = k + (k & 1), M1 = ke - 1, np2 = ke / 2;
-    const R rtol = sizeof(R) == 8 ? R(1e-14) : R(1e-7);
+    const R rtol = 8 * epsR;  // rotations below rounding are not needed
     for (int sweep = 0; sweep < 12; ++sweep) {
       int rotated = 0;
       for (int st = 0; st < M1; ++st) {
