@@ -86,7 +86,8 @@ typedef struct {
                                       bonds above 64 and, with the
                                       tridiagonal eigensolver, for every
                                       move of a tensor of 2^17 elements or
-                                      more),
+                                      more and of a circuit above 32
+                                      qubits),
                                     1 one-sided Jacobi on the tensor,
                                     2 Gram matrix; eigensolver two-sided
                                       Jacobi in shared memory up to 128 KB

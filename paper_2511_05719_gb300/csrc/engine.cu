@@ -148,8 +148,10 @@ static constexpr int EIG_SMEM_MAX = 131072;
 static constexpr int TRI_UNROLL = 16;  // loads in flight per thread in L2-resident sweeps
 static constexpr int TRI_NB = 8;       // reflectors per compact-WY block of the back-transformation
 static constexpr int TRI_INV_ITERS = 2;  // inverse-iteration / orthonormalisation rounds
-// Moves whose tensor capacity reaches this many elements count as large.
+// Moves whose tensor capacity reaches this many elements count as large, and
+// so does every move of a circuit above BIG_CIRCUIT_QUBITS qubits (d >= 5).
 static constexpr int64_t BIG_MOVE = (int64_t)1 << 17;
+static constexpr int BIG_CIRCUIT_QUBITS = 32;
 template <typename R>
 constexpr int tri_smem_bytes() {
   return 512 * (5 * 2 * (int)sizeof(R) + 3 * (int)sizeof(R)) + 2 * TRI_NB * 512 * 2 * (int)sizeof(R);
@@ -2402,7 +2404,7 @@ struct Engine {
           int64_t mcap = 1;
           for (int t = 0; t < 3; ++t)
             if (t != lv0) mcap *= cc3[t];
-          const bool big = mcap * nmv >= BIG_MOVE;
+          const bool big = c.N > BIG_CIRCUIT_QUBITS || mcap * nmv >= BIG_MOVE;
           const bool gram = dev.svd_mode >= 2 || (dev.svd_mode == 0 && sizeof(R) == 4 && (nmv > 64 || big));
           // contractions of this move on the tensor cores (FP32 only)
           const bool tc = sizeof(R) == 4 && (gemm_mode == 2 || (gemm_mode == 0 && gram));
