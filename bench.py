@@ -224,17 +224,12 @@ def main():
     for _ in range(a.warmup):
         step()
     torch.cuda.synchronize()
-    # roofline class: the kernel class with the most device time in one
-    # profiled warm-up pass per candidate is too costly at this size; the
-    # class is fixed by the launch-list profile (profiles/) unless given.
-    rclass = a.roofline_class if a.roofline_class != "auto" else (
-        "eig" if a.precision == "fp32" and a.chi > 32 else "svd_jacobi")
     clocks = ClockSampler(local)
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     clocks.start()
-    P.profile_begin(rclass)
+    P.profile_begin("all")   # device time of every launch, per kernel class (CUDA events)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -260,14 +255,16 @@ def main():
     e2e = {"value": world * B / e2e_s, "unit": "trajectories/s",
            "h2d_bytes_per_step": 8 * B,
            "d2h_bytes_per_step": B * (circ.n_record_bits + 1 + 8 + 8 + 4)}
-    # roofline of the dominant kernel class
+    # roofline of the dominant kernel class (most device time in the timed region)
+    cms = prof["class_ms"]
+    rclass = a.roofline_class if a.roofline_class != "auto" else max(cms, key=lambda c: cms[c])
     fl = prof["flops"][rclass]
     by = prof["bytes"][rclass]
-    tms = prof["timed_ms"]
+    tms = cms[rclass]
     achieved = fl / (tms / 1e3) / 1e12 if tms > 0 else 0.0
     roof = {"bound": "alu", "achieved": achieved, "peak": FP32_ALU_PEAK_TFLOPS,
             "unit": "TFLOP/s", "frac": achieved / FP32_ALU_PEAK_TFLOPS if achieved else 0.0,
-            "traffic": None, "kernel_class": rclass, "launches": prof["timed_launches"],
+            "traffic": None, "kernel_class": rclass, "launches": prof["launches"][rclass],
             "kernel_ms": tms, "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 x 2070 MHz"}
     if a.precision == "fp32" and rclass in TENSOR_CLASSES:
         pk, src = tensor_peak()
@@ -288,7 +285,8 @@ def main():
                        "l2": "working set per step far above L2 (no flush)"},
             "clocks": ck, "e2e": e2e, "gpu_launches": int(sum(prof["launches"].values())),
             "roofline": roof,
-            "ledger_tflop": {k: v / 1e12 for k, v in prof["flops"].items()}}
+            "ledger_tflop": {k: v / 1e12 for k, v in prof["flops"].items()},
+            "device_ms_by_class": {k: round(v, 1) for k, v in cms.items()}}
     if not a.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(a, a.cpu_seconds)
     print(json.dumps(line))
