@@ -247,6 +247,7 @@ def main():
         ms = float(t.item())
     traj = world * a.steps * B
     value = traj / (ms / 1e3)
+    lost = int((out["fail"] == 3).sum().item())   # of the last timed step (fail byte 3)
     # end to end: host buffers through the same call (one step)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -282,7 +283,8 @@ def main():
             "data": "synthetic",
             "config": {"workload": workload_name(a), "trajectories_per_step": B,
                        "rounds": a.rounds, "distance": a.distance, "chi": a.chi,
-                       "l2": "working set per step far above L2 (no flush)"},
+                       "l2": "working set per step far above L2 (no flush)",
+                       "lost_trajectories_last_step": lost},
             "clocks": ck, "e2e": e2e, "gpu_launches": int(sum(prof["launches"].values())),
             "roofline": roof,
             "ledger_tflop": {k: v / 1e12 for k, v in prof["flops"].items()},

@@ -131,7 +131,10 @@ ttn_status ttn_circuit_layout(const ttn_circuit* circuit, int32_t* leaf_of_qubit
  * whole circuit on the TTN, Born-sampled measurements, Kraus-branch or Pauli
  * draws from Philox4x32-10 keyed by (seed, trajectory, event), then decodes
  * (App. A.2).  Outputs (any may be NULL): records [n_traj][n_record_bits]
- * (u8 0/1), logical_fail [n_traj] (u8), log_prob [n_traj] (log p of the
+ * (u8 0/1), logical_fail [n_traj] (u8: 0/1 decoded logical outcome, 2 the
+ * decoder's bound was exceeded, 3 the trajectory's state lost its norm or
+ * became non-finite in the FP32 arithmetic -- such trajectories are kept out
+ * of p_L), log_prob [n_traj] (log p of the
  * sampled record and branches), discarded [n_traj] (sum of discarded
  * squared singular values), near_ties [n_traj] (draws with |u - p| < 1e-9
  * (FP64) or 1e-5 (FP32)).  Results depend only on (seed, trajectory index),
@@ -142,8 +145,9 @@ ttn_status ttn_run_trajectories(const ttn_circuit* circuit, const ttn_run_params
                                 double* log_prob, double* discarded, int32_t* near_ties,
                                 void* cuda_stream);
 
-/* Monte Carlo p_L = failures / shots (App. A.3, steps i-iii) with its
- * binomial standard error sigma = sqrt(p (1-p) / shots).  Host outputs. */
+/* Monte Carlo p_L = failures / valid shots (App. A.3, steps i-iii) with its
+ * binomial standard error sigma = sqrt(p (1-p) / valid shots); shots with a
+ * fail byte above 1 are not valid.  Host outputs. */
 ttn_status ttn_logical_error_rate(const ttn_circuit* circuit, const ttn_run_params* params,
                                   uint64_t shots, double* p_L, double* sigma, uint64_t* n_fail);
 

@@ -197,11 +197,15 @@ ttn_status ttn_logical_error_rate(const ttn_circuit* c, const ttn_run_params* p,
   std::vector<uint8_t> fail(shots);
   s = ttn_run_trajectories(c, p, shots, nullptr, fail.data(), nullptr, nullptr, nullptr, nullptr);
   if (s != TTN_OK) return s;
-  uint64_t nf = 0;
-  for (uint8_t f : fail) nf += f == 1;
-  double pl = (double)nf / (double)shots;
+  uint64_t nf = 0, nv = 0;
+  for (uint8_t f : fail) {
+    nf += f == 1;
+    nv += f <= 1;  // 2: decoder bound exceeded, 3: trajectory lost its norm
+  }
+  if (nv == 0) return fail_with(TTN_EOVERFLOW, "no valid shots");
+  double pl = (double)nf / (double)nv;
   if (p_L) *p_L = pl;
-  if (sigma) *sigma = std::sqrt(pl * (1.0 - pl) / (double)shots);
+  if (sigma) *sigma = std::sqrt(pl * (1.0 - pl) / (double)nv);
   if (n_fail) *n_fail = nf;
   return TTN_OK;
 }

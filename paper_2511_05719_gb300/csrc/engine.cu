@@ -2651,7 +2651,24 @@ static ttn_status run_impl(const ttn_circuit& c, const RunRequest& rq, RunOutput
     CK(cudaStreamSynchronize(st));
     eng.collect_profile();
     for (int i = 0; i < nb; ++i) out.err_flags |= err[i];
-    if (out.err_flags & (ERR_CAPACITY | ERR_ZERO_NORM | ERR_NAN)) {
+    // A trajectory whose state lost its norm (or became non-finite) is kept
+    // out of the statistics: its fail byte becomes 3 and the run goes on.
+    // Capacity overflows and failures in single-trajectory debug runs stay
+    // fatal.
+    bool fatal = (out.err_flags & ERR_CAPACITY) != 0 || (rq.debug_amps && (out.err_flags & (ERR_ZERO_NORM | ERR_NAN)));
+    if (!fatal && (out.err_flags & (ERR_ZERO_NORM | ERR_NAN))) {
+      static const uint8_t lost_byte = 3;
+      for (int i = 0; i < nb; ++i)
+        if (err[i] & (ERR_ZERO_NORM | ERR_NAN)) {
+          out.lost += 1;
+          if (out.fail)
+            CK(cudaMemcpyAsync(out.fail + t0 + i, &lost_byte, 1,
+                               out.on_device ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost, st));
+        }
+      CK(cudaStreamSynchronize(st));
+      out.err_flags &= ~(ERR_ZERO_NORM | ERR_NAN);
+    }
+    if (fatal) {
       // first failing trajectory: which step of the program raised it
       std::string where;
       for (int i = 0; i < nb; ++i)

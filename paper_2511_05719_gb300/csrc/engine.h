@@ -35,6 +35,7 @@ struct RunOutputs {
   int32_t* near_ties = nullptr;
   double* score = nullptr;       // host [n_traj], with grad_wrt >= 0
   int err_flags = 0;
+  uint64_t lost = 0;             // trajectories whose state lost its norm (fail byte 3)
   int batch = 0;
   size_t bytes_per_traj = 0;
   int decode_overflow = 0;
