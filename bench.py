@@ -134,21 +134,13 @@ def cpu_baseline(a, seconds):
     layout = P.Circuit(a.distance, a.rounds, layout="optimized").layout()
     thetas = WL.M3["thetas"]
     total = len(circ.ops)
-    lo, hi = 1, total
-    t0 = time.time()
     done = 0
-    # grow the op budget until the sample takes about `seconds`
-    budget = 200
-    elapsed = 0.0
-    while True:
-        t1 = time.time()
-        TT.run_trajectory(circ, SRX, thetas[3], 0.0, WL.M3["seed"], 0, chi=a.chi,
-                          leaf_of_qubit=list(layout), max_ops=budget)
-        elapsed = time.time() - t1
-        done = budget
-        if elapsed > seconds / 3 or budget >= total:
-            break
-        budget = min(total, budget * 4)
+    # one trajectory in program order, stopped after about `seconds`
+    t1 = time.time()
+    r = TT.run_trajectory(circ, SRX, thetas[3], 0.0, WL.M3["seed"], 0, chi=a.chi,
+                          leaf_of_qubit=list(layout), deadline=t1 + seconds)
+    elapsed = time.time() - t1
+    done = r["ops_done"]
     traj_s = (done / total) / elapsed if elapsed > 0 else 0.0
     cores = os.cpu_count()
     return {"value": traj_s, "unit": "trajectories/s", "cores": cores, "kind": "oracle",

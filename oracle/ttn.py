@@ -37,6 +37,8 @@ the same draws; chi = 1 keeps a product state; the discarded weight is
 zero when chi is large enough.
 """
 import math
+import time
+
 import numpy as np
 
 from . import philox
@@ -309,7 +311,10 @@ def apply_noise_ttn(tt, q, model, theta, gamma, u):
 
 
 def run_trajectory(circ, model, theta, gamma, seed, traj, chi, leaf_of_qubit=None,
-                   snapshot_layers=(), eps=1e-13, max_ops=None):
+                   snapshot_layers=(), eps=1e-13, max_ops=None, deadline=None):
+    """One trajectory on the numpy TTN.  max_ops / deadline (a time.time()
+    value) stop the run early, for bounded timing samples; `ops_done` in the
+    result counts the ops run."""
     N = circ.n_qubits
     if leaf_of_qubit is None:
         leaf_of_qubit = default_layout(N)
@@ -323,8 +328,10 @@ def run_trajectory(circ, model, theta, gamma, seed, traj, chi, leaf_of_qubit=Non
     events = [op[3] for op in circ.ops if op[3] >= 0]
     us = dict(zip(events, philox.uniforms(seed, [traj], events)[0])) if events else {}
     cur_layer = 0
+    ops_done = len(circ.ops)
     for i, (kind, a, b, e, r, layer) in enumerate(circ.ops):
-        if max_ops is not None and i >= max_ops:
+        if (max_ops is not None and i >= max_ops) or (deadline is not None and time.time() > deadline):
+            ops_done = i
             break
         if layer != cur_layer:
             if cur_layer in snap:
@@ -360,4 +367,4 @@ def run_trajectory(circ, model, theta, gamma, seed, traj, chi, leaf_of_qubit=Non
     if cur_layer in snap:
         states[cur_layer] = tt.amplitudes()
     return dict(rec=rec, logp=logp, margin=margin, states=states, ttn=tt,
-                discarded=tt.discarded)
+                discarded=tt.discarded, ops_done=ops_done)
