@@ -1088,6 +1088,7 @@ __global__ void __launch_bounds__(512) k_eig_tri(Dev<R> d, int v, int w, int cap
   R* bt = dg + 512;                                 // |sub-diagonal|
   R* tau = bt + 512;                                // reflector scalars
   __shared__ double red[64];
+  __shared__ double wx2[32], wt2[32], wvp[32];  // per-warp partial sums
   __shared__ double s_sc;
   __shared__ int bstart[512], bend[512];  // unreduced block [bstart, bend) of each row
 
@@ -1102,8 +1103,12 @@ __global__ void __launch_bounds__(512) k_eig_tri(Dev<R> d, int v, int w, int cap
     dg[1] = A[3].x;
   }
   if (n >= 3) {
+    // Five barriers per step: reductions (|x|^2 of the next reflector's
+    // column, v^H p) are per-warp partials written during the preceding
+    // pass and summed in warp order after its barrier (deterministic).
+    const int wid = tid >> 5, lid = tid & 31, nw = nth >> 5;
     tri_reflector(A, n, 0, vk, tau, ek, red);
-    {  // p_0 = tau_0 A[1:, 1:] v_0
+    {  // p_0 = tau_0 A[1:, 1:] v_0 and v_0^H p_0
       const int m = n - 1, G = nth / m, col = tid % m, g = tid / m;
       if (g < G) {
         cx<R> acc = {R(0), R(0)};
@@ -1112,38 +1117,89 @@ __global__ void __launch_bounds__(512) k_eig_tri(Dev<R> d, int v, int w, int cap
         pp[g * m + col] = acc;
       }
       __syncthreads();
+      double vp = 0.0;
       if (tid < m) {
         cx<R> acc = pp[tid];
         for (int gg = 1; gg < G; ++gg) acc = cadd(acc, pp[gg * m + tid]);
-        pp[tid] = cscale(acc, tau[0]);
+        acc = cscale(acc, tau[0]);
+        pp[tid] = acc;
+        vp = (double)vk[tid].x * acc.x + (double)vk[tid].y * acc.y;
       }
+      vp = warp_sum(vp);
+      if (lid == 0) wvp[wid] = vp;
       __syncthreads();
     }
     for (int k = 0; k + 3 <= n; ++k) {
       const int o = k + 1, m = n - o;  // trailing block rows/cols o..n-1
       // (a) K = tau/2 v^H p (real), w = p - K v
-      double kp = 0.0;
-      for (int r = tid; r < m; r += nth) kp += (double)vk[r].x * pp[r].x + (double)vk[r].y * pp[r].y;
-      const R K = (R)(0.5 * (double)tau[k] * block_sum2(kp, 0.0, red).x);
+      double vpsum = 0.0;
+      for (int i = 0; i < nw; ++i) vpsum += wvp[i];
+      const R K = (R)(0.5 * (double)tau[k] * vpsum);
       for (int r = tid; r < m; r += nth) wk[r] = {pp[r].x - K * vk[r].x, pp[r].y - K * vk[r].y};
-      __syncthreads();
-      // (b) column o of the trailing block
+      __syncthreads();  // B1
+      // (b) column o of the trailing block; partial norms of its rows o+1..
+      // (the next reflector's x) and of rows o+2.. (its tail)
       const cx<R> cw0 = {wk[0].x, -wk[0].y}, cv0 = {vk[0].x, -vk[0].y};
+      double x2 = 0.0, t2 = 0.0;
       for (int r = tid; r < m; r += nth) {
         cx<R> a = A[(int64_t)(o + r) * n + o];
-        const cx<R> t1 = cmul(vk[r], cw0), t2 = cmul(wk[r], cv0);
-        a = {a.x - t1.x - t2.x, a.y - t1.y - t2.y};
+        const cx<R> t1 = cmul(vk[r], cw0), tt = cmul(wk[r], cv0);
+        a = {a.x - t1.x - tt.x, a.y - t1.y - tt.y};
         A[(int64_t)(o + r) * n + o] = a;
         if (r == 0) dg[o] = a.x;
+        const double a2 = (double)a.x * a.x + (double)a.y * a.y;
+        if (r >= 1) x2 += a2;
+        if (r >= 2) t2 += a2;
       }
-      __syncthreads();
-      // (c) next reflector from the updated column o
+      x2 = warp_sum(x2);
+      t2 = warp_sum(t2);
+      if (lid == 0) {
+        wx2[wid] = x2;
+        wt2[wid] = t2;
+      }
+      __syncthreads();  // B2
+      // (c) next reflector of column o: H = I - tau v v^H, |v_0| = 1
       const bool has_next = (o + 3 <= n);
       if (has_next) {
-        tri_reflector(A, n, o, vn, tau, ek, red);
+        double X2 = 0.0, T2 = 0.0;
+        for (int i = 0; i < nw; ++i) {
+          X2 += wx2[i];
+          T2 += wt2[i];
+        }
+        const int mn = m - 1;  // length of the next reflector
+        const cx<R> x0 = A[(int64_t)(o + 1) * n + o];
+        if (T2 == 0.0) {  // already reduced: H = I
+          for (int r = tid; r < mn; r += nth) vn[r] = {R(0), R(0)};
+          if (tid == 0) {
+            tau[o] = R(0);
+            ek[o] = x0;
+          }
+        } else {
+          const double xn = sqrt(X2);
+          const double ax0 = sqrt((double)x0.x * x0.x + (double)x0.y * x0.y);
+          const double phr = ax0 > 0.0 ? x0.x / ax0 : 1.0, phi = ax0 > 0.0 ? x0.y / ax0 : 0.0;
+          const double den = ax0 + xn;  // |x_0 - alpha|
+          for (int r = tid; r < mn; r += nth) {
+            cx<R> vr;
+            if (r == 0) {
+              vr = {(R)phr, (R)phi};
+            } else {
+              const cx<R> x = A[(int64_t)(o + 1 + r) * n + o];
+              vr = {(R)(x.x / den), (R)(x.y / den)};
+            }
+            vn[r] = vr;
+          }
+          if (tid == 0) {
+            tau[o] = (R)(2.0 / (1.0 + T2 / (den * den)));
+            ek[o] = {(R)(-phr * xn), (R)(-phi * xn)};  // alpha = -phase(x_0) |x|
+          }
+        }
       } else if (tid == 0) {
         ek[o] = A[(int64_t)(n - 1) * n + o];
       }
+      __syncthreads();  // B3: vn, tau[o] visible; x0 read by everyone
+      if (has_next)  // v stored below the diagonal of column o
+        for (int r = tid; r < m - 1; r += nth) A[(int64_t)(o + 1 + r) * n + o] = vn[r];
       // (d) rank-2 update of rows/cols o+1.. fused with p_next = A' v_next
       const int mp = m - 1;
       if (mp > 0) {
@@ -1164,8 +1220,8 @@ __global__ void __launch_bounds__(512) k_eig_tri(Dev<R> d, int v, int w, int cap
             for (int u = 0; u < TRI_UNROLL; ++u) {
               const int j = j0 + u * G;
               if (j < mp) {
-                const cx<R> t1 = cmul(vk[1 + j], cwi), t2 = cmul(wk[1 + j], cvi);
-                a[u] = {a[u].x - t1.x - t2.x, a[u].y - t1.y - t2.y};
+                const cx<R> t1 = cmul(vk[1 + j], cwi), tt = cmul(wk[1 + j], cvi);
+                a[u] = {a[u].x - t1.x - tt.x, a[u].y - t1.y - tt.y};
                 colp[(int64_t)j * n] = a[u];
                 if (has_next) acc = cadd(acc, cmulc(a[u], vn[j]));
               }
@@ -1173,15 +1229,20 @@ __global__ void __launch_bounds__(512) k_eig_tri(Dev<R> d, int v, int w, int cap
           }
           if (has_next) pp[g * mp + col] = acc;
         }
-        __syncthreads();
+        __syncthreads();  // B4
         if (has_next) {
+          double vp = 0.0;
           if (tid < mp) {
             cx<R> acc = pp[tid];
             for (int gg = 1; gg < G; ++gg) acc = cadd(acc, pp[gg * mp + tid]);
-            pp[tid] = cscale(acc, tau[o]);
+            acc = cscale(acc, tau[o]);
+            pp[tid] = acc;
+            vp = (double)vn[tid].x * acc.x + (double)vn[tid].y * acc.y;
           }
+          vp = warp_sum(vp);
+          if (lid == 0) wvp[wid] = vp;
           for (int r = tid; r < mp; r += nth) vk[r] = vn[r];
-          __syncthreads();
+          __syncthreads();  // B5
         }
       }
     }
