@@ -218,6 +218,11 @@ ttn_status ttn_profile_begin(int32_t timed_class);
 ttn_status ttn_profile_end(double* timed_ms, uint64_t* timed_launches, double* flops,
                            double* bytes, uint64_t* launches);
 ttn_status ttn_profile_class_ms(double* class_ms);
+/* SM clock cycles of the tridiagonal eigensolver's phases in the current (or
+ * last) profile, summed over trajectories (thread 0 of each CTA): tridiagonal
+ * reduction, phases/split, bisection, eigenvectors (inverse iteration and
+ * Gram-Schmidt), Rayleigh-Ritz, back-transformation.  Host [6]. */
+ttn_status ttn_profile_eig_phases(double* cycles);
 
 const char* ttn_status_string(ttn_status status);
 const char* ttn_last_error(void);

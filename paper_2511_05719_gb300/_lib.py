@@ -40,7 +40,7 @@ class TTNError(RuntimeError):
 EXPORTS = ["ttn_build_circuit", "ttn_free_circuit", "ttn_circuit_info", "ttn_circuit_ops",
            "ttn_circuit_layout", "ttn_run_trajectories", "ttn_logical_error_rate", "ttn_decode",
            "ttn_debug_state", "ttn_philox_uniforms", "ttn_profile_begin", "ttn_profile_end",
-           "ttn_grad", "ttn_decode_noalloc", "ttn_profile_class_ms",
+           "ttn_grad", "ttn_decode_noalloc", "ttn_profile_class_ms", "ttn_profile_eig_phases",
            "ttn_status_string", "ttn_last_error"]
 
 
@@ -77,6 +77,7 @@ def load_library():
                              ctypes.c_double, c_dblp, c_dblp, c_dblp, c_dblp]
     lib.ttn_profile_begin.argtypes = [ctypes.c_int32]
     lib.ttn_profile_class_ms.argtypes = [c_dblp]
+    lib.ttn_profile_eig_phases.argtypes = [c_dblp]
     lib.ttn_profile_end.argtypes = [c_dblp, c_u64p, c_dblp, c_dblp, c_u64p]
     lib.ttn_status_string.restype = ctypes.c_char_p
     lib.ttn_status_string.argtypes = [ctypes.c_int]
@@ -252,6 +253,7 @@ def philox_uniforms(seed, trajs, events):
 
 
 KERNEL_CLASSES = ["svd_jacobi", "gram", "eig", "form_u", "absorb", "copy", "other", "local"]
+EIG_PHASES = ["tridiagonalise", "split", "bisection", "eigenvectors", "rayleigh_ritz", "back_transform"]
 
 
 def profile_begin(timed_class=-1):
@@ -272,9 +274,12 @@ def profile_end():
     lib = load_library()
     _check(lib.ttn_profile_end(ctypes.byref(ms), ctypes.byref(nl), fl, by, la))
     _check(lib.ttn_profile_class_ms(cm))
+    ep = (ctypes.c_double * 6)()
+    _check(lib.ttn_profile_eig_phases(ep))
     return dict(timed_ms=ms.value, timed_launches=nl.value,
                 flops=dict(zip(KERNEL_CLASSES, list(fl))), bytes=dict(zip(KERNEL_CLASSES, list(by))),
-                launches=dict(zip(KERNEL_CLASSES, list(la))), class_ms=dict(zip(KERNEL_CLASSES, list(cm))))
+                launches=dict(zip(KERNEL_CLASSES, list(la))), class_ms=dict(zip(KERNEL_CLASSES, list(cm))),
+                eig_phase_cycles=dict(zip(EIG_PHASES, list(ep))))
 
 
 def grad(circuit, shots, wrt="theta", noise="srx", theta=0.0, gamma=0.0, chi=16, precision="fp64",

@@ -327,6 +327,13 @@ ttn_status ttn_profile_end(double* timed_ms, uint64_t* timed_launches, double* f
   return TTN_OK;
 }
 
+ttn_status ttn_profile_eig_phases(double* cycles) {
+  if (!cycles) return fail_with(TTN_EINVAL, "null argument");
+  const Profile& p = profile();
+  for (int i = 0; i < EIG_PHASES; ++i) cycles[i] = p.eig_phase_cycles[i];
+  return TTN_OK;
+}
+
 ttn_status ttn_profile_class_ms(double* class_ms) {
   if (!class_ms) return fail_with(TTN_EINVAL, "null argument");
   const Profile& p = profile();

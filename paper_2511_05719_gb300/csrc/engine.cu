@@ -121,7 +121,7 @@ struct Dev {
   double eps_gram, tol_gram, tol_abs_gram;
   int svd_mode;
   int eig_smem_bytes;    // dynamic shared memory of k_eig launches
-  unsigned long long* ledger;  // [2 * NCLASS] algorithmic flops, bytes (or null)
+  unsigned long long* ledger;  // [LEDGER_WORDS] algorithmic flops, bytes, eigensolver phase cycles (or null)
   uint8_t* choice;       // [B][n_events] sampled outcome of every stochastic event
   int n_events;
   int forced;            // 1: replay the recorded choices instead of sampling
@@ -148,6 +148,9 @@ static constexpr int EIG_SMEM_MAX = 131072;
 static constexpr int TRI_UNROLL = 16;  // loads in flight per thread in L2-resident sweeps
 static constexpr int TRI_NB = 8;       // reflectors per compact-WY block of the back-transformation
 static constexpr int TRI_INV_ITERS = 2;  // inverse-iteration / orthonormalisation rounds
+// profiling ledger: flops and bytes per class, then SM cycles per phase of
+// the tridiagonal eigensolver (summed over trajectories, thread 0's clock)
+static constexpr int LEDGER_WORDS = 2 * NCLASS + EIG_PHASES;
 // Moves whose tensor capacity reaches this many elements count as large, and
 // so does every move of a circuit above BIG_CIRCUIT_QUBITS qubits (d >= 5).
 static constexpr int64_t BIG_MOVE = (int64_t)1 << 17;
@@ -1095,6 +1098,14 @@ __global__ void __launch_bounds__(512) k_eig_tri(Dev<R> d, int v, int w, int cap
   double trp = 0.0;
   for (int j = tid; j < n; j += nth) trp += (double)A[(int64_t)j * n + j].x;
   const double trace = block_sum2(trp, 0.0, red).x;
+  long long clk0 = clock64();
+  auto phase_mark = [&](int ph) {  // cycles of the phase that just ended
+    if (tid == 0 && d.ledger) {
+      const long long c1 = clock64();
+      atomicAdd(&d.ledger[2 * NCLASS + ph], (unsigned long long)(c1 - clk0));
+      clk0 = c1;
+    }
+  };
 
   // ---- 1. tridiagonalisation
   if (tid == 0) dg[0] = A[0].x;
@@ -1249,6 +1260,7 @@ __global__ void __launch_bounds__(512) k_eig_tri(Dev<R> d, int v, int w, int cap
     if (tid == 0) dg[n - 1] = A[(int64_t)(n - 1) * n + n - 1].x;
   }
   __syncthreads();
+  phase_mark(0);
 
   // ---- 2. phases D (T = D T_real D^H), scale to |T| <= 1, split
   R* b2 = reinterpret_cast<R*>(vn);
@@ -1297,6 +1309,7 @@ __global__ void __launch_bounds__(512) k_eig_tri(Dev<R> d, int v, int w, int cap
   }
   __syncthreads();
 
+  phase_mark(1);
   // ---- 3. bisection: thread j finds eigenvalue number j - s (ascending) of
   // the block [s, e) that holds row j
   if (tid < n) {
@@ -1322,6 +1335,7 @@ __global__ void __launch_bounds__(512) k_eig_tri(Dev<R> d, int v, int w, int cap
     sv[j] = (double)l * sc;
   }
   __syncthreads();
+  phase_mark(2);
   // singular values below sqrt(eps) s_max are not resolved by a Gram matrix
   // in this precision
   const double eps_keep = fmax(d.eps_gram, sqrt((double)epsR));
@@ -1462,6 +1476,7 @@ __global__ void __launch_bounds__(512) k_eig_tri(Dev<R> d, int v, int w, int cap
       }
     }
   }
+  phase_mark(3);
   // Rayleigh-Ritz: TZ into U0 (column-major), H = Z^T (TZ) into U1 (k x k),
   // Q into U2
   R* TZ = U0;
@@ -1562,6 +1577,7 @@ __global__ void __launch_bounds__(512) k_eig_tri(Dev<R> d, int v, int w, int cap
   for (int idx = tid; idx < n * k; idx += nth) Z[idx] = TZ[idx];
   __syncthreads();
 
+  phase_mark(4);
   // ---- 5. back-transformation V_k = H_0 ... H_{n-3} D Z_k (n x k in Vk),
   // TRI_NB reflectors at a time in compact WY form (Schreiber & Van Loan):
   // H_j0 ... H_j1 = I - Vb Tb Vb^H, so Vk <- Vk - Vb (Tb (Vb^H Vk)).
@@ -1666,6 +1682,7 @@ __global__ void __launch_bounds__(512) k_eig_tri(Dev<R> d, int v, int w, int cap
     __syncthreads();
   }
   for (int idx = tid; idx < n * k; idx += nth) A[idx] = Vk[idx];
+  phase_mark(5);
 }
 
 // Exact singular values of the kept columns: Y = M V_k was written into T_v;
@@ -2305,12 +2322,14 @@ struct Engine {
     }
     events.clear();
     event_class.clear();
-    unsigned long long h[2 * NCLASS] = {0};
-    if (dLedger && cudaMemcpy(h, dLedger, sizeof(h), cudaMemcpyDeviceToHost) == cudaSuccess)
+    unsigned long long h[LEDGER_WORDS] = {0};
+    if (dLedger && cudaMemcpy(h, dLedger, sizeof(h), cudaMemcpyDeviceToHost) == cudaSuccess) {
       for (int c = 0; c < NCLASS; ++c) {
         pf.flops[c] += (double)h[2 * c];
         pf.bytes[c] += (double)h[2 * c + 1];
       }
+      for (int ph = 0; ph < EIG_PHASES; ++ph) pf.eig_phase_cycles[ph] += (double)h[2 * NCLASS + ph];
+    }
     for (int c = 0; c < NCLASS; ++c) {
       pf.class_launches[c] += class_launches[c];
       class_launches[c] = 0;
@@ -2375,8 +2394,8 @@ struct Engine {
     CK(cudaMalloc(&dTrunc, sizeof(int32_t) * B));
     CK(cudaMalloc(&dChoice, (size_t)std::max(1, c.n_events) * B));
     if (profile().active) {
-      CK(cudaMalloc(&dLedger, sizeof(unsigned long long) * 2 * NCLASS));
-      CK(cudaMemset(dLedger, 0, sizeof(unsigned long long) * 2 * NCLASS));
+      CK(cudaMalloc(&dLedger, sizeof(unsigned long long) * LEDGER_WORDS));
+      CK(cudaMemset(dLedger, 0, sizeof(unsigned long long) * LEDGER_WORDS));
     }
     CK(cudaMalloc(&dLeafdim, sizeof(int32_t) * c.L));
     CK(cudaMalloc(&dOp1, sizeof(Op1) * std::max<size_t>(1, prog.op1.size())));

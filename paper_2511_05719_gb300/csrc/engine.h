@@ -44,6 +44,10 @@ struct RunOutputs {
 // Kernel classes of the profiling ledger.
 enum KernelClass { KC_SVD = 0, KC_GRAM = 1, KC_EIG = 2, KC_FORMU = 3, KC_ABSORB = 4, KC_COPY = 5,
                    KC_OTHER = 6, KC_LOCAL = 7, NCLASS = 8 };
+// Phases of the tridiagonal eigensolver timed by the ledger: tridiagonalise,
+// phases/split, bisection, eigenvectors (inverse iteration + Gram-Schmidt),
+// Rayleigh-Ritz, back-transformation.
+static constexpr int EIG_PHASES = 6;
 
 // Process-wide profiling state: while active, every run adds algorithmic
 // flops/bytes per class to `ledger`, and launches of class `timed_class`
@@ -58,6 +62,7 @@ struct Profile {
   double bytes[NCLASS] = {0};
   uint64_t class_launches[NCLASS] = {0};
   double class_ms[NCLASS] = {0};
+  double eig_phase_cycles[EIG_PHASES] = {0};
 };
 Profile& profile();
 
