@@ -32,3 +32,20 @@ def test_chi_one_is_product_state():
     assert out["ttn"].max_bond() <= 2
     psi = out["ttn"].amplitudes()
     assert np.linalg.norm(psi) == pytest.approx(1.0, abs=1e-12)
+
+
+def test_run_stops_at_op_budget_and_deadline():
+    """The bounded-sample controls used by the CPU timing baseline: an op
+    budget stops after exactly that many ops, a past deadline before the
+    first op, and a full run reports every op."""
+    import time as _time
+    from oracle.circuit import build_circuit
+    from oracle import ttn as TT
+    from oracle.channels import SRX
+    circ = build_circuit(3, 1)
+    full = TT.run_trajectory(circ, SRX, 0.05, 0.0, 1, 0, chi=64)
+    assert full["ops_done"] == len(circ.ops)
+    part = TT.run_trajectory(circ, SRX, 0.05, 0.0, 1, 0, chi=64, max_ops=17)
+    assert part["ops_done"] == 17
+    none = TT.run_trajectory(circ, SRX, 0.05, 0.0, 1, 0, chi=64, deadline=_time.time() - 1.0)
+    assert none["ops_done"] == 0
