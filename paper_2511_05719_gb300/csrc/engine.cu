@@ -90,6 +90,7 @@ template <typename R>
 struct Dev {
   cx<R>* T;              // node tensors, trajectory b at T + b * tstride + off[v]
   const int64_t* off;    // [L]
+  const int64_t* ncap;   // [L] slot capacity of node v (elements)
   int64_t tstride;
   int32_t* dims;         // [B][2L] bond (x, parent(x)) dimension
   int ds;                // 2L
@@ -204,7 +205,7 @@ __global__ void k_init(Dev<R> d, const int32_t* leafdim, int B) {
 // Centre move v -> w (neighbour) across their bond.  M = T_v with the bond as
 // column index (m x n).  One-sided Jacobi (Hestenes) orthogonalises the
 // columns of M V; s_j = |(M V)_j|; keep k singular triplets (s > eps s_max,
-// at most chi when capped); T_v <- U_k, R = S_k V_k^dag (renormalised after a
+// at most kcap); T_v <- U_k, R = S_k V_k^dag (renormalised after a
 // truncation) is left in d.Rm for the neighbour.
 template <typename R>
 __device__ __forceinline__ R warp_sum(R v) {
@@ -214,7 +215,7 @@ __device__ __forceinline__ R warp_sum(R v) {
 }
 
 template <typename R>
-__global__ void __launch_bounds__(256) k_svd_move(Dev<R> d, int v, int w, int capped) {
+__global__ void __launch_bounds__(256) k_svd_move(Dev<R> d, int v, int w, int kcap) {
   const int b = blockIdx.x;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
   int* D = d.dims + b * d.ds;
@@ -379,13 +380,13 @@ __global__ void __launch_bounds__(256) k_svd_move(Dev<R> d, int v, int w, int ca
     if (k < 1) k = 1;
     double scale = 1.0;
     if (smax == 0.0) flag_err(d, b, ERR_ZERO_NORM);
-    if (capped && k > d.chi) {
+    if (k > kcap) {
       double dsc = 0.0;
-      for (int i = d.chi; i < n; ++i) dsc += sv[perm[i]] * sv[perm[i]];
+      for (int i = kcap; i < n; ++i) dsc += sv[perm[i]] * sv[perm[i]];
       dsc = tot > 0.0 ? dsc / tot : 0.0;
       d.disc[b] += dsc;
       scale = dsc < 1.0 ? 1.0 / sqrt(1.0 - dsc) : 1.0;
-      k = d.chi;
+      k = kcap;
     }
     s_k = k;
     s_scale = scale;
@@ -432,7 +433,10 @@ __global__ void k_copy_back(Dev<R> d, int v) {
   const int b = blockIdx.y;
   const int* D = d.dims + b * d.ds;
   const int64_t cnt = (int64_t)D[2 * v] * D[2 * v + 1] * D[v];
-  if (cnt > d.wstride) return;
+  if (cnt > d.wstride || cnt > d.ncap[v]) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) flag_err(d, b, ERR_CAPACITY);
+    return;
+  }
   if (blockIdx.x == 0 && threadIdx.x == 0) ledger_add(d.ledger, KC_COPY, 0.0, 2.0 * sizeof(cx<R>) * cnt);
   cx<R>* T = node_ptr(d, b, v);
   const cx<R>* W = d.W + (int64_t)b * d.wstride;
@@ -775,10 +779,10 @@ __global__ void __launch_bounds__(256) k_gram(Dev<R> d, int v, int w) {
 
 // Selection shared by the Gram eigensolvers: eigenvalues (sv[j], any order)
 // -> singular values, perm = descending order, kept rank k (s > eps_keep
-// s_max, at most chi when capped), bond dimension update.  Returns k to every
+// s_max, at most kcap), bond dimension update.  Returns k to every
 // thread.
 template <typename R>
-__device__ int eig_select(Dev<R>& d, int b, int v, int w, int capped, int n, double trace,
+__device__ int eig_select(Dev<R>& d, int b, int v, int w, int kcap, int n, double trace,
                           double eps_keep) {
   const int tid = threadIdx.x, nth = blockDim.x;
   int* D = d.dims + b * d.ds;
@@ -813,8 +817,8 @@ __device__ int eig_select(Dev<R>& d, int b, int v, int w, int capped, int n, dou
     if (k < 1) k = 1;
     if (smax == 0.0) flag_err(d, b, ERR_ZERO_NORM);
     int trunc = 0;
-    if (capped && k > d.chi) {
-      k = d.chi;
+    if (k > kcap) {
+      k = kcap;
       trunc = 1;
     }
     s_kk = k;
@@ -831,9 +835,9 @@ __device__ int eig_select(Dev<R>& d, int b, int v, int w, int capped, int n, dou
 
 // Jacobi tail: V (row-major n x n eigenvectors) -> V_k into G.
 template <typename R>
-__device__ void eig_select_tail(Dev<R>& d, int b, int v, int w, int capped, int n, const cx<R>* V,
+__device__ void eig_select_tail(Dev<R>& d, int b, int v, int w, int kcap, int n, const cx<R>* V,
                                 cx<R>* Gglob, double trace) {
-  const int k = eig_select(d, b, v, w, capped, n, trace, d.eps_gram);
+  const int k = eig_select(d, b, v, w, kcap, n, trace, d.eps_gram);
   const int32_t* perm = d.perm + (int64_t)b * d.nmax;
   // V_k (n x k, row-major, columns in descending eigenvalue order) into G
   for (int idx = threadIdx.x; idx < n * k; idx += blockDim.x) {
@@ -845,7 +849,7 @@ __device__ void eig_select_tail(Dev<R>& d, int b, int v, int w, int capped, int 
 // Eigen-decomposition of G by cyclic two-sided Jacobi; then the kept rank,
 // V_k S_k^-1 (into G) and R = S_k V_k^H (into Rm).
 template <typename R>
-__global__ void __launch_bounds__(512) k_eig(Dev<R> d, int v, int w, int capped) {
+__global__ void __launch_bounds__(512) k_eig(Dev<R> d, int v, int w, int kcap) {
   const int b = blockIdx.x;
   const int tid = threadIdx.x, nth = blockDim.x;
   int* D = d.dims + b * d.ds;
@@ -962,7 +966,7 @@ __global__ void __launch_bounds__(512) k_eig(Dev<R> d, int v, int w, int capped)
   }
   for (int j = tid; j < n; j += nth) sv[j] = (double)G[(int64_t)j * n + j].x;  // eigenvalues
   __syncthreads();
-  eig_select_tail(d, b, v, w, capped, n, V, Gglob, s_tr);
+  eig_select_tail(d, b, v, w, kcap, n, V, Gglob, s_tr);
 }
 
 // Block-wide sums (blockDim.x a multiple of 32); red holds 64 doubles.
@@ -1058,7 +1062,7 @@ __device__ void tri_reflector(cx<R>* A, int n, int c, cx<R>* vout, R* tau, cx<R>
 // (Golub & Van Loan, Matrix Computations, Ch. 8.)  Selection and output as in
 // k_eig: V_k (n x k, row-major) into G.
 template <typename R>
-__global__ void __launch_bounds__(512) k_eig_tri(Dev<R> d, int v, int w, int capped) {
+__global__ void __launch_bounds__(512) k_eig_tri(Dev<R> d, int v, int w, int kcap) {
   const int b = blockIdx.x;
   const int tid = threadIdx.x, nth = blockDim.x;
   const int* D = d.dims + b * d.ds;
@@ -1339,7 +1343,7 @@ __global__ void __launch_bounds__(512) k_eig_tri(Dev<R> d, int v, int w, int cap
   // singular values below sqrt(eps) s_max are not resolved by a Gram matrix
   // in this precision
   const double eps_keep = fmax(d.eps_gram, sqrt((double)epsR));
-  const int k = eig_select(d, b, v, w, capped, n, trace, eps_keep);
+  const int k = eig_select(d, b, v, w, kcap, n, trace, eps_keep);
   if (tid == 0)
     ledger_add(d.ledger, KC_EIG, 16.0 / 3.0 * (double)n * n * n + 8.0 * (double)n * n * k,
                (double)sizeof(cx<R>) * ((double)n * n + (double)n * k));
@@ -2374,7 +2378,7 @@ struct Engine {
     CK(cudaMalloc(&dR, sizeof(cx<R>) * (size_t)vstride * B));
     CK(cudaMalloc(&dG, sizeof(cx<R>) * (size_t)vstride * B));
     CK(cudaMalloc(&dTs, sizeof(cx<R>) * (size_t)vstride * 2 * B));
-    CK(cudaMalloc(&dOff, sizeof(int64_t) * c.L));
+    CK(cudaMalloc(&dOff, sizeof(int64_t) * 2 * c.L));  // off, then ncap
     CK(cudaMalloc(&dDims, sizeof(int32_t) * 2 * c.L * B));
     CK(cudaMalloc(&dSv, sizeof(double) * nmax * B));
     CK(cudaMalloc(&dPerm, sizeof(int32_t) * nmax * B));
@@ -2401,6 +2405,7 @@ struct Engine {
     CK(cudaMalloc(&dOp1, sizeof(Op1) * std::max<size_t>(1, prog.op1.size())));
     CK(cudaMalloc(&dGroups, sizeof(Group1) * std::max<size_t>(1, prog.groups.size())));
     CK(cudaMemcpy(dOff, off.data(), sizeof(int64_t) * c.L, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(dOff + c.L, ncap.data(), sizeof(int64_t) * c.L, cudaMemcpyHostToDevice));
     std::vector<int32_t> leafdim(c.L, 1);
     for (int q = 0; q < c.N; ++q) leafdim[c.leaf_of_qubit[q]] = 2;
     CK(cudaMemcpy(dLeafdim, leafdim.data(), sizeof(int32_t) * c.L, cudaMemcpyHostToDevice));
@@ -2411,6 +2416,7 @@ struct Engine {
                     cudaMemcpyHostToDevice));
     dev.T = dT;
     dev.off = dOff;
+    dev.ncap = dOff + c.L;
     dev.tstride = tstride;
     dev.dims = dDims;
     dev.ds = 2 * c.L;
@@ -2475,6 +2481,14 @@ struct Engine {
           const int v = s.a, w = s.b;
           const int bond = (w == v / 2) ? v : w;
           const int64_t nmv = 2 * (int64_t)bcap[bond];
+          // largest rank this move may keep: the bond's structural cap
+          // (min(chi, 2^{qubits on the smaller side})) on truncating moves,
+          // twice that while a gate's operator index rides on the bond.  In
+          // FP32 the Gram matrix's rounding puts spurious singular values
+          // near 1e-3 s_max, above the kept-rank floor; without this cap they
+          // would keep small bonds above their structural rank and the next
+          // gate would grow the node past its slot.
+          const int kcap = s.c ? bcap[bond] : 2 * bcap[bond];
           // FP32 auto: the Gram path for bonds above 64 and for every move of a
           // large tensor (there the one-sided Jacobi's FP32 orthogonality test
           // is not reachable and its iteration stalls); FP64 auto: Jacobi.
@@ -2504,9 +2518,9 @@ struct Engine {
             if (dev.svd_mode != 3 && !(dev.svd_mode == 0 && big) &&
                 nmv * nmv * (int64_t)sizeof(cx<R>) <= EIG_SMEM_MAX) {
               dev.eig_smem_bytes = (int)(nmv * nmv * (int64_t)sizeof(cx<R>));
-              timed(KC_EIG, [&] { k_eig<R><<<nb, 512, dev.eig_smem_bytes, st>>>(dev, v, w, s.c); });
+              timed(KC_EIG, [&] { k_eig<R><<<nb, 512, dev.eig_smem_bytes, st>>>(dev, v, w, kcap); });
             } else {
-              timed(KC_EIG, [&] { k_eig_tri<R><<<nb, 512, tri_smem_bytes<R>(), st>>>(dev, v, w, s.c); });
+              timed(KC_EIG, [&] { k_eig_tri<R><<<nb, 512, tri_smem_bytes<R>(), st>>>(dev, v, w, kcap); });
             }
             timed(KC_FORMU, [&] {
               const dim3 gf(std::max(1, ceil_div(mmax, 64)), tn, nb);
@@ -2521,7 +2535,7 @@ struct Engine {
               k_unorm_apply<R><<<dim3(gx, nb), 256, 0, st>>>(dev, v, w);
             });
           } else {
-            timed(KC_SVD, [&] { k_svd_move<R><<<nb, 256, 0, st>>>(dev, v, w, s.c); });
+            timed(KC_SVD, [&] { k_svd_move<R><<<nb, 256, 0, st>>>(dev, v, w, kcap); });
           }
           // neighbour absorbs R: grid from capacities
           const int lw = (v == 2 * w) ? 0 : ((v == 2 * w + 1) ? 1 : 2);
