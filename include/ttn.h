@@ -145,6 +145,34 @@ ttn_status ttn_run_trajectories(const ttn_circuit* circuit, const ttn_run_params
                                 double* log_prob, double* discarded, int32_t* near_ties,
                                 void* cuda_stream);
 
+/* Mixed batch (the paper runs one (d, chi) configuration at a time; this
+ * serves sweeps that mix distances, bond dimensions and noise strengths, with
+ * each item's trajectories independent of the others as in Sec. III.C).
+ * Item i runs n_traj[i] trajectories of circuits[i] under params[i] (its
+ * own noise model, strengths, chi, precision, seed and first_traj; per-
+ * trajectory strengths as in ttn_run_trajectories) and writes their fail
+ * bytes (meaning as in ttn_run_trajectories) to logical_fail[i]
+ * ([n_traj[i]] u8; may be NULL for an item with n_traj[i] == 0) and, when
+ * log_prob and log_prob[i] are non-NULL, the log-probabilities of the
+ * sampled records to log_prob[i] ([n_traj[i]] double).  Outputs are DEVICE
+ * pointers when cuda_stream is non-NULL, else host.  Every item's results equal
+ * those of ttn_run_trajectories with the same arguments.  All items are in
+ * flight at once, each on its own stream created by the library (from one
+ * host thread per item), so that items whose kernels fill few SMs overlap;
+ * they start after the work queued on cuda_stream and are complete when the
+ * call returns.  The device budget (80 % of free memory) is split over the
+ * items in proportion to n_traj[i] x the item's bytes per trajectory when
+ * they do not all fit, and each item runs in chunks within its share.  While
+ * the profiler is active the items run one after another.  n_items in
+ * [1, TTN_MIXED_MAX_ITEMS].  Returns the lowest-index item's failure (its
+ * message prefixed with "item i"), EOVERFLOW only if no item failed
+ * otherwise; EINVAL on a bad item before anything runs. */
+#define TTN_MIXED_MAX_ITEMS 64
+ttn_status ttn_run_mixed(int32_t n_items, const ttn_circuit* const* circuits,
+                         const ttn_run_params* params, const uint64_t* n_traj,
+                         uint8_t* const* logical_fail, double* const* log_prob,
+                         void* cuda_stream);
+
 /* Monte Carlo p_L = failures / valid shots (App. A.3, steps i-iii) with its
  * binomial standard error sigma = sqrt(p (1-p) / valid shots); shots with a
  * fail byte above 1 are not valid.  Host outputs. */

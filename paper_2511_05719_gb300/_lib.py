@@ -41,7 +41,7 @@ EXPORTS = ["ttn_build_circuit", "ttn_free_circuit", "ttn_circuit_info", "ttn_cir
            "ttn_circuit_layout", "ttn_run_trajectories", "ttn_logical_error_rate", "ttn_decode",
            "ttn_debug_state", "ttn_philox_uniforms", "ttn_profile_begin", "ttn_profile_end",
            "ttn_grad", "ttn_decode_noalloc", "ttn_profile_class_ms", "ttn_profile_eig_phases",
-           "ttn_status_string", "ttn_last_error"]
+           "ttn_run_mixed", "ttn_status_string", "ttn_last_error"]
 
 
 def library_path():
@@ -65,6 +65,7 @@ def load_library():
     lib.ttn_circuit_layout.argtypes = [vp, c_i32p]
     lib.ttn_run_trajectories.argtypes = [vp, ctypes.POINTER(RunParams), ctypes.c_uint64, vp, vp, vp,
                                          vp, vp, vp]
+    lib.ttn_run_mixed.argtypes = [ctypes.c_int32, vp, vp, vp, vp, vp, vp]
     lib.ttn_logical_error_rate.argtypes = [vp, ctypes.POINTER(RunParams), ctypes.c_uint64, c_dblp,
                                            c_dblp, c_u64p]
     lib.ttn_decode.argtypes = [vp, ctypes.c_uint64, vp, vp, vp, vp, vp]
@@ -203,6 +204,55 @@ def run_trajectories(circuit, n_traj, noise="srx", theta=0.0, gamma=0.0, chi=16,
                                     _ptr(out.get("records")), _ptr(out.get("fail")),
                                     _ptr(out.get("log_prob")), _ptr(out.get("discarded")),
                                     _ptr(out.get("near_ties")), st))
+    del keep
+    return out
+
+
+def run_mixed(items, out=None, stream=None):
+    """Mixed batch: `items` is a list of dicts, each with `circuit` and
+    `n_traj` plus any keyword of run_trajectories (noise, theta, gamma, chi,
+    precision, seed, first_traj, svd_eps, theta_per_traj, gamma_per_traj,
+    svd_mode, gemm_mode).  All items are in flight at once (ttn_run_mixed).
+    With `out=None` returns a list of host dicts {fail, log_prob}; with `out`
+    a list of dicts of torch CUDA tensors (`fail` uint8, optional `log_prob`
+    float64) and `stream` a CUDA stream handle (int), writes them on the
+    device."""
+    lib = load_library()
+    n = len(items)
+    circs = (ctypes.c_void_p * max(1, n))()
+    params = (RunParams * max(1, n))()
+    counts = (ctypes.c_uint64 * max(1, n))()
+    fails = (ctypes.c_void_p * max(1, n))()
+    lps = (ctypes.c_void_p * max(1, n))()
+    keep = []
+    opts = ("noise", "theta", "gamma", "chi", "precision", "seed", "first_traj", "svd_eps",
+            "theta_per_traj", "gamma_per_traj", "svd_mode", "gemm_mode")
+    defaults = dict(noise="srx", theta=0.0, gamma=0.0, chi=16, precision="fp64", seed=0,
+                    first_traj=0, svd_eps=0.0, theta_per_traj=None, gamma_per_traj=None,
+                    svd_mode="auto", gemm_mode="auto")
+    if out is None:
+        out = [dict(fail=np.zeros(int(it["n_traj"]), dtype=np.uint8),
+                    log_prob=np.zeros(int(it["n_traj"]))) for it in items]
+        st = None
+    else:
+        if stream is None:
+            raise ValueError("device outputs need a CUDA stream handle")
+        st = ctypes.c_void_p(int(stream))
+    for i, it in enumerate(items):
+        unknown = set(it) - set(opts) - {"circuit", "n_traj"}
+        if unknown:
+            raise ValueError("unknown item keys: %s" % sorted(unknown))
+        kw = dict(defaults)
+        kw.update({k: it[k] for k in opts if k in it})
+        p, kp = _run_params(**kw)
+        keep.extend(kp)
+        params[i] = p
+        circs[i] = it["circuit"].handle.value
+        counts[i] = int(it["n_traj"])
+        fp, lp = _ptr(out[i].get("fail")), _ptr(out[i].get("log_prob"))
+        fails[i] = fp.value if fp is not None else None
+        lps[i] = lp.value if lp is not None else None
+    _check(lib.ttn_run_mixed(n, circs, params, counts, fails, lps, st))
     del keep
     return out
 

@@ -5,6 +5,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -157,35 +158,131 @@ static RunRequest make_request(const ttn_run_params* p, uint64_t n_traj, void* s
   return rq;
 }
 
-ttn_status ttn_run_trajectories(const ttn_circuit* c, const ttn_run_params* p, uint64_t n_traj,
-                                uint8_t* records, uint8_t* logical_fail, double* log_prob,
-                                double* discarded, int32_t* near_ties, void* cuda_stream) {
-  ttn_status s = check_params(c, p);
-  if (s != TTN_OK) return s;
-  if (n_traj == 0) return TTN_OK;
-  RunRequest rq = make_request(p, n_traj, cuda_stream);
-  if (cuda_stream && (p->theta_per_traj || p->gamma_per_traj)) {
+}  // extern "C"
+
+// One run on `stream` (device outputs when on_device); max_bytes bounds the
+// device arena (0: 80 % of free memory).
+static ttn_status run_one(const ttn_circuit* c, const ttn_run_params* p, uint64_t n_traj,
+                          uint8_t* records, uint8_t* logical_fail, double* log_prob, double* discarded,
+                          int32_t* near_ties, void* stream, bool on_device, size_t max_bytes) {
+  RunRequest rq = make_request(p, n_traj, stream);
+  rq.max_device_bytes = max_bytes;
+  if (p->theta_per_traj || p->gamma_per_traj) {
     // per-trajectory strengths are read on the host
     cudaPointerAttributes at{};
     const double* probe = p->theta_per_traj ? p->theta_per_traj : p->gamma_per_traj;
     if (cudaPointerGetAttributes(&at, probe) == cudaSuccess && at.type == cudaMemoryTypeDevice)
       return fail_with(TTN_EINVAL, "theta_per_traj / gamma_per_traj must be host arrays");
+    cudaGetLastError();
   }
   RunOutputs out;
-  out.on_device = cuda_stream != nullptr;
-  out.fail_on_device = out.on_device;
+  out.on_device = on_device;
+  out.fail_on_device = on_device;
   out.records = records;
   out.fail = logical_fail;
   out.log_prob = log_prob;
   out.discarded = discarded;
   out.near_ties = near_ties;
-  s = run_trajectories_device(*c, rq, out);
+  ttn_status s = run_trajectories_device(*c, rq, out);
   if (s != TTN_OK) return s;
   if (out.decode_overflow > 0) {
     set_error("decoder: " + std::to_string(out.decode_overflow) +
               " shot(s) exceeded the matching bound (fail byte 2)");
     return TTN_EOVERFLOW;
   }
+  return TTN_OK;
+}
+
+extern "C" {
+
+ttn_status ttn_run_trajectories(const ttn_circuit* c, const ttn_run_params* p, uint64_t n_traj,
+                                uint8_t* records, uint8_t* logical_fail, double* log_prob,
+                                double* discarded, int32_t* near_ties, void* cuda_stream) {
+  ttn_status s = check_params(c, p);
+  if (s != TTN_OK) return s;
+  if (n_traj == 0) return TTN_OK;
+  return run_one(c, p, n_traj, records, logical_fail, log_prob, discarded, near_ties, cuda_stream,
+                 cuda_stream != nullptr, 0);
+}
+
+ttn_status ttn_run_mixed(int32_t n_items, const ttn_circuit* const* circuits, const ttn_run_params* params,
+                         const uint64_t* n_traj, uint8_t* const* logical_fail, double* const* log_prob,
+                         void* cuda_stream) {
+  if (n_items < 1 || n_items > TTN_MIXED_MAX_ITEMS)
+    return fail_with(TTN_EINVAL, "n_items must be in [1, " + std::to_string(TTN_MIXED_MAX_ITEMS) + "]");
+  if (!circuits || !params || !n_traj || !logical_fail) return fail_with(TTN_EINVAL, "null argument");
+  for (int i = 0; i < n_items; ++i) {
+    ttn_status s = check_params(circuits[i], &params[i]);
+    if (s != TTN_OK) return fail_with(s, "item " + std::to_string(i) + ": " + ttn_last_error());
+    if (n_traj[i] > 0 && !logical_fail[i])
+      return fail_with(TTN_EINVAL, "item " + std::to_string(i) + ": null logical_fail");
+  }
+  // Split the device budget over the items in proportion to what each would
+  // hold with all its trajectories resident.
+  size_t freeb = 0, totb = 0;
+  if (cudaMemGetInfo(&freeb, &totb) != cudaSuccess)
+    return fail_with(TTN_ECUDA, std::string("cudaMemGetInfo: ") + cudaGetErrorString(cudaGetLastError()));
+  const double budget = 0.80 * (double)freeb;
+  std::vector<double> need(n_items, 0.0);
+  double total = 0.0;
+  for (int i = 0; i < n_items; ++i) {
+    RunRequest rq = make_request(&params[i], n_traj[i], nullptr);
+    need[i] = (double)n_traj[i] * (double)run_bytes_per_traj(*circuits[i], rq);
+    total += need[i];
+  }
+  std::vector<size_t> share(n_items, 0);
+  for (int i = 0; i < n_items; ++i)
+    share[i] = (size_t)(total <= budget ? budget : budget * need[i] / total);
+  // Item streams start after the work already queued on the caller's stream.
+  std::vector<cudaStream_t> streams(n_items, nullptr);
+  cudaEvent_t ready = nullptr;
+  auto cleanup = [&]() {
+    for (cudaStream_t st : streams)
+      if (st) cudaStreamDestroy(st);
+    if (ready) cudaEventDestroy(ready);
+  };
+  for (int i = 0; i < n_items; ++i)
+    if (cudaStreamCreateWithFlags(&streams[i], cudaStreamNonBlocking) != cudaSuccess) {
+      cleanup();
+      return fail_with(TTN_ECUDA, "cudaStreamCreateWithFlags failed");
+    }
+  if (cuda_stream) {
+    if (cudaEventCreateWithFlags(&ready, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventRecord(ready, (cudaStream_t)cuda_stream) != cudaSuccess) {
+      cleanup();
+      return fail_with(TTN_ECUDA, "event on the caller's stream failed");
+    }
+    for (int i = 0; i < n_items; ++i) cudaStreamWaitEvent(streams[i], ready, 0);
+  }
+  int device = 0;
+  cudaGetDevice(&device);
+  std::vector<ttn_status> status(n_items, TTN_OK);
+  std::vector<std::string> msg(n_items);
+  auto work = [&](int i) {
+    if (n_traj[i] == 0) return;
+    cudaSetDevice(device);  // the current device is per host thread
+    status[i] = run_one(circuits[i], &params[i], n_traj[i], nullptr, logical_fail[i],
+                        log_prob ? log_prob[i] : nullptr, nullptr, nullptr, streams[i],
+                        cuda_stream != nullptr, share[i]);
+    if (status[i] != TTN_OK) msg[i] = ttn_last_error();
+  };
+  if (profile().active || n_items == 1) {
+    // the profiler accumulates on the host: keep it on one thread
+    for (int i = 0; i < n_items; ++i) work(i);
+  } else {
+    std::vector<std::thread> th;
+    th.reserve(n_items);
+    for (int i = 0; i < n_items; ++i) th.emplace_back(work, i);
+    for (std::thread& t : th) t.join();
+  }
+  cleanup();
+  // report the lowest-index failure; decoder overflow (fail byte 2) last
+  for (int pass = 0; pass < 2; ++pass)
+    for (int i = 0; i < n_items; ++i) {
+      const bool over = status[i] == TTN_EOVERFLOW;
+      if (status[i] != TTN_OK && over == (pass == 1))
+        return fail_with(status[i], "item " + std::to_string(i) + ": " + msg[i]);
+    }
   return TTN_OK;
 }
 

@@ -2365,7 +2365,7 @@ struct Engine {
   }
 
   size_t bytes_per_traj() const {
-    return sizeof(cx<R>) * (size_t)(tstride + wstride + 3 * vstride) +
+    return sizeof(cx<R>) * (size_t)(tstride + wstride + 5 * vstride) +  // V, Rm, G, Ts (2)
            sizeof(int32_t) * (2 * c.L + 2 * nmax + 4) + sizeof(double) * (nmax + 5) + c.n_rec + c.N +
            c.n_events + 64;
   }
@@ -2790,6 +2790,12 @@ static ttn_status run_impl(const ttn_circuit& c, const RunRequest& rq, RunOutput
   }
   eng.release();
   return TTN_OK;
+}
+
+size_t run_bytes_per_traj(const ttn_circuit& c, const RunRequest& rq) {
+  Program prog = compile_program(c, rq.noise, -1);
+  if (rq.precision == TTN_PREC_FP64) return Engine<double>(c, prog, rq.chi, rq.noise, nullptr).bytes_per_traj();
+  return Engine<float>(c, prog, rq.chi, rq.noise, nullptr).bytes_per_traj();
 }
 
 ttn_status run_trajectories_device(const ttn_circuit& c, const RunRequest& rq, RunOutputs& out) {

@@ -68,6 +68,10 @@ Profile& profile();
 
 ttn_status run_trajectories_device(const ttn_circuit& c, const RunRequest& rq, RunOutputs& out);
 
+// Device bytes one trajectory of this circuit and request occupies (host-side
+// sizing only; no CUDA call).
+size_t run_bytes_per_traj(const ttn_circuit& c, const RunRequest& rq);
+
 // Decodes nb records that live on the device; fail/color/score are device
 // pointers when on_device, else host pointers.
 ttn_status decode_device(const ttn_circuit& c, int nb, const uint8_t* d_records, uint8_t* fail,

@@ -68,3 +68,33 @@ def test_invalid_arguments():
         P.Circuit(3, 1, leaf_of_qubit=list(range(4, 17)))  # leaf 16 is outside 16 leaves
     c = P.Circuit(3, 1, leaf_of_qubit=list(range(13)))
     assert np.array_equal(c.layout(), np.arange(13))
+
+
+def test_run_mixed_rejects_bad_items_before_any_device_work():
+    _lib = _lib_or_skip()
+    import paper_2511_05719_gb300 as P
+    lib = _lib.load_library()
+    # n_items outside [1, 64] and null arrays
+    for n in (0, 65):
+        assert lib.ttn_run_mixed(n, None, None, None, None, None, None) == 1
+    assert lib.ttn_run_mixed(1, None, None, None, None, None, None) == 1
+    c3 = P.Circuit(3, 1)
+    items = [dict(circuit=c3, n_traj=2, chi=8), dict(circuit=c3, n_traj=2, chi=0)]
+    with pytest.raises(P.TTNError) as e:
+        P.run_mixed(items)
+    assert e.value.status == 1 and "item 1" in str(e.value)
+    items = [dict(circuit=c3, n_traj=2, noise="bogus")]
+    with pytest.raises(KeyError):
+        P.run_mixed(items)
+    with pytest.raises(ValueError):
+        P.run_mixed([dict(circuit=c3, n_traj=1, rounds=3)])
+    # an item with trajectories needs an output array
+    lib2 = ctypes.CDLL(_lib.library_path())
+    lib2.ttn_run_mixed.argtypes = [ctypes.c_int32] + [ctypes.c_void_p] * 6
+    p = _lib.RunParams()
+    p.noise, p.chi, p.precision = 1, 8, 0
+    circs = (ctypes.c_void_p * 1)(c3.handle.value)
+    cnt = (ctypes.c_uint64 * 1)(3)
+    fails = (ctypes.c_void_p * 1)(None)
+    assert lib2.ttn_run_mixed(1, circs, ctypes.byref(p), cnt, fails, None, None) == 1
+    assert b"logical_fail" in lib.ttn_last_error()
