@@ -11,11 +11,12 @@ Draw rule of the simulator: the uniform of event `e` of trajectory `t` under
 the first two output words w0, w1,
     u = ((w0 >> 5) * 2^26 + (w1 >> 6)) * 2^-53     (53 random bits, in [0,1)).
 
-Parity: pinned by statistical tests (uniform moments, Kolmogorov-Smirnov,
-independence of neighbouring counters) in tests/test_oracle_rng.py; the bit
-pattern itself is not pinned against an external source (parity unpinned
-for the exact bit stream; only agreement with the device generator is
-tested).
+Parity: the block function is pinned to the published known-answer vectors
+of Philox4x32-10 (Random123's known-answer tests; tests/golden/
+philox4x32_10_kat.txt), and the derived uniforms by statistical tests
+(moments, Kolmogorov-Smirnov, independence of neighbouring counters) in
+tests/test_oracle_rng.py.  The device generator is compared with this one
+bit for bit.
 """
 import numpy as np
 
