@@ -2567,6 +2567,8 @@ struct Engine {
           timed(KC_LOCAL, [&] {
             k_thread_node<R><<<dim3(std::max(1, ceil_div(ncap[s.a], 256)), nb), 256, 0, st>>>(
                 dev, s.a, s.b);
+            // same dims update as the leaf step: only the node's up bond
+            // doubles here (its child bond doubled when the child was threaded)
             k_thread_dims_leaf<R><<<ceil_div(nb, 128), 128, 0, st>>>(dev, s.a, nb);
           });
           timed(KC_COPY, [&] {
@@ -2612,10 +2614,6 @@ struct Engine {
     return TTN_OK;
   }
 };
-
-// Thread dims doubling for the node steps uses the same kernel as the leaf
-// (only the up bond of the node doubles; the child bond was doubled when the
-// child was threaded).
 
 template <typename R>
 static ttn_status run_impl(const ttn_circuit& c, const RunRequest& rq, RunOutputs& out) {
