@@ -192,6 +192,47 @@ ttn_status ttn_grad(const ttn_circuit* circuit, const ttn_run_params* params, ui
                     int32_t wrt, double h, double* p_L, double* dpL, double* dpL_sigma,
                     double* score);
 
+/* Threshold crossing (Sec. IV.A: thresholds are read off where the p_L
+ * curves of different distances cross; the paper then fits Eq. 4).  The
+ * paper has no search; this locates one crossing directly.
+ *
+ * ttn_newton_crossing: safeguarded Newton iteration for a root of f(x),
+ * whose estimates come from `eval` (called with the point and the
+ * 0-based evaluation index; it returns f, its standard error, f' and its
+ * standard error, and TTN_OK, or a status that aborts the search and is
+ * returned).  The iterate stays in [x_lo, x_hi]; once two evaluations differ
+ * in sign their interval is kept as a bracket and a Newton step that leaves
+ * it, or a slope within twice its error, is replaced by bisection.  The
+ * search stops when a step is below max(x_tol, 2 sigma_x), sigma_x =
+ * sigma_f / |f'|, or at max_iter evaluations.  Outputs: x_star (the last
+ * Newton or bisection point), x_sigma (sigma_x at the last evaluation; +inf
+ * if its slope was not resolved), iters (evaluations made), converged
+ * (1 if a stopping rule fired), trace [max_iter][5] (x, f, sigma_f, f',
+ * sigma_f' per evaluation).  Any output but x_star may be NULL.  With neither
+ * a resolved slope nor a bracket the search stops, not converged.  EINVAL on
+ * x_lo >= x_hi, x0 outside, max_iter outside [1, 1000], x_tol <= 0, or
+ * non-finite evaluator output. */
+typedef ttn_status (*ttn_crossing_eval)(void* ctx, double x, int32_t iter, double* f,
+                                        double* f_sigma, double* df, double* df_sigma);
+ttn_status ttn_newton_crossing(ttn_crossing_eval eval, void* ctx, double x0, double x_lo,
+                               double x_hi, int32_t max_iter, double x_tol, double* x_star,
+                               double* x_sigma, int32_t* iters, int32_t* converged,
+                               double* trace);
+
+/* The crossing of the p_L(x) curves of circuits a and b (e.g. d = 5 and
+ * d = 7), x = theta (wrt 0) or gamma (wrt 1), the other parameters from
+ * params: ttn_newton_crossing on f(x) = ln p_L^a(x) - ln p_L^b(x), where
+ * each evaluation runs ttn_grad on both circuits with `shots` fresh
+ * trajectories (first_traj advances by shots per evaluation), f' = the
+ * score-function estimates of d ln p_L / dx, and the errors follow by the
+ * delta method.  The logarithm makes power-law failure curves nearly
+ * linear near the crossing.  EINVAL as ttn_grad and ttn_newton_crossing, or
+ * when a circuit shows no logical failure at an evaluated point. */
+ttn_status ttn_crossing(const ttn_circuit* a, const ttn_circuit* b, const ttn_run_params* params,
+                        uint64_t shots, int32_t wrt, double h, double x0, double x_lo,
+                        double x_hi, int32_t max_iter, double x_tol, double* x_star,
+                        double* x_sigma, int32_t* iters, int32_t* converged, double* trace);
+
 /* Decodes n records ([n][n_record_bits] u8) with the concatenated MWPM
  * decoder (App. A.2) on the device.  fail [n] u8, color [n] int32 (winning
  * colour), score [n] int64 (total matching weight).  color/score may be NULL. */

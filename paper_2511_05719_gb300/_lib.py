@@ -41,7 +41,12 @@ EXPORTS = ["ttn_build_circuit", "ttn_free_circuit", "ttn_circuit_info", "ttn_cir
            "ttn_circuit_layout", "ttn_run_trajectories", "ttn_logical_error_rate", "ttn_decode",
            "ttn_debug_state", "ttn_philox_uniforms", "ttn_profile_begin", "ttn_profile_end",
            "ttn_grad", "ttn_decode_noalloc", "ttn_profile_class_ms", "ttn_profile_eig_phases",
-           "ttn_run_mixed", "ttn_status_string", "ttn_last_error"]
+           "ttn_run_mixed", "ttn_newton_crossing", "ttn_crossing", "ttn_status_string",
+           "ttn_last_error"]
+
+# f(x) evaluator of ttn_newton_crossing: (ctx, x, iter, *f, *f_sigma, *df, *df_sigma) -> status
+CROSSING_EVAL = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_double, ctypes.c_int32,
+                                 c_dblp, c_dblp, c_dblp, c_dblp)
 
 
 def library_path():
@@ -66,6 +71,13 @@ def load_library():
     lib.ttn_run_trajectories.argtypes = [vp, ctypes.POINTER(RunParams), ctypes.c_uint64, vp, vp, vp,
                                          vp, vp, vp]
     lib.ttn_run_mixed.argtypes = [ctypes.c_int32, vp, vp, vp, vp, vp, vp]
+    lib.ttn_newton_crossing.argtypes = [CROSSING_EVAL, vp, ctypes.c_double, ctypes.c_double,
+                                        ctypes.c_double, ctypes.c_int32, ctypes.c_double, c_dblp,
+                                        c_dblp, c_i32p, c_i32p, c_dblp]
+    lib.ttn_crossing.argtypes = [vp, vp, ctypes.POINTER(RunParams), ctypes.c_uint64, ctypes.c_int32,
+                                 ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                 ctypes.c_int32, ctypes.c_double, c_dblp, c_dblp, c_i32p, c_i32p,
+                                 c_dblp]
     lib.ttn_logical_error_rate.argtypes = [vp, ctypes.POINTER(RunParams), ctypes.c_uint64, c_dblp,
                                            c_dblp, c_u64p]
     lib.ttn_decode.argtypes = [vp, ctypes.c_uint64, vp, vp, vp, vp, vp]
@@ -255,6 +267,59 @@ def run_mixed(items, out=None, stream=None):
     _check(lib.ttn_run_mixed(n, circs, params, counts, fails, lps, st))
     del keep
     return out
+
+
+def _crossing_out(max_iter):
+    return (ctypes.c_double(), ctypes.c_double(), ctypes.c_int32(), ctypes.c_int32(),
+            np.zeros((max_iter, 5)))
+
+
+def _crossing_result(xs, sx, it, cv, tr):
+    n = it.value
+    return dict(x=xs.value, sigma=sx.value, iters=n, converged=bool(cv.value), trace=tr[:n].copy())
+
+
+def newton_crossing(f, x0, x_lo, x_hi, max_iter=20, x_tol=1e-4):
+    """ttn_newton_crossing with a Python evaluator f(x, iter) -> (f, f_sigma,
+    df, df_sigma).  Returns {x, sigma, iters, converged, trace}."""
+    lib = load_library()
+    errors = []
+
+    def cb(ctx, x, it, pf, psf, pdf, psdf):
+        try:
+            v = f(x, it)
+            pf[0], psf[0], pdf[0], psdf[0] = [float(t) for t in v]
+            return 0
+        except Exception as e:  # reported after the call
+            errors.append(e)
+            return 1
+
+    cfn = CROSSING_EVAL(cb)
+    xs, sx, it, cv, tr = _crossing_out(max_iter)
+    st = lib.ttn_newton_crossing(cfn, None, x0, x_lo, x_hi, max_iter, x_tol, ctypes.byref(xs),
+                                 ctypes.byref(sx), ctypes.byref(it), ctypes.byref(cv),
+                                 tr.ctypes.data_as(c_dblp))
+    if errors:
+        raise errors[0]
+    _check(st)
+    return _crossing_result(xs, sx, it, cv, tr)
+
+
+def crossing(circuit_a, circuit_b, shots, x0, x_lo, x_hi, wrt="theta", noise="srx", theta=0.0,
+             gamma=0.0, chi=16, precision="fp64", seed=0, first_traj=0, svd_eps=0.0, h=0.0,
+             max_iter=10, x_tol=1e-4, svd_mode="auto", gemm_mode="auto"):
+    """ttn_crossing: the crossing of the p_L(x) curves of two circuits,
+    x = theta or gamma.  Returns {x, sigma, iters, converged, trace}."""
+    lib = load_library()
+    p, keep = _run_params(noise, theta, gamma, chi, precision, seed, first_traj, svd_eps,
+                          svd_mode=svd_mode, gemm_mode=gemm_mode)
+    w = {"theta": 0, "gamma": 1}[wrt] if isinstance(wrt, str) else int(wrt)
+    xs, sx, it, cv, tr = _crossing_out(max_iter)
+    _check(lib.ttn_crossing(circuit_a.handle, circuit_b.handle, ctypes.byref(p), shots, w, h, x0, x_lo,
+                            x_hi, max_iter, x_tol, ctypes.byref(xs), ctypes.byref(sx), ctypes.byref(it),
+                            ctypes.byref(cv), tr.ctypes.data_as(c_dblp)))
+    del keep
+    return _crossing_result(xs, sx, it, cv, tr)
 
 
 def logical_error_rate(circuit, shots, noise="srx", theta=0.0, gamma=0.0, chi=16,

@@ -356,6 +356,150 @@ ttn_status ttn_grad(const ttn_circuit* c, const ttn_run_params* p, uint64_t shot
   return TTN_OK;
 }
 
+ttn_status ttn_newton_crossing(ttn_crossing_eval eval, void* ctx, double x0, double x_lo, double x_hi,
+                               int32_t max_iter, double x_tol, double* x_star, double* x_sigma,
+                               int32_t* iters, int32_t* converged, double* trace) {
+  if (!eval || !x_star) return fail_with(TTN_EINVAL, "null argument");
+  if (!(x_lo < x_hi) || !std::isfinite(x_lo) || !std::isfinite(x_hi))
+    return fail_with(TTN_EINVAL, "need finite x_lo < x_hi");
+  if (!(x0 >= x_lo && x0 <= x_hi)) return fail_with(TTN_EINVAL, "x0 must lie in [x_lo, x_hi]");
+  if (max_iter < 1 || max_iter > 1000) return fail_with(TTN_EINVAL, "max_iter must be in [1, 1000]");
+  if (!(x_tol > 0.0)) return fail_with(TTN_EINVAL, "x_tol must be > 0");
+  // Safeguarded Newton on f(x) = 0.  A bracket [blo, bhi] with f of opposite
+  // signs at its ends is kept once two evaluations differ in sign; a Newton
+  // step that leaves it, or a slope not resolved above twice its error,
+  // falls back to bisection.  Stops when the step is below
+  // max(x_tol, 2 sigma_x), sigma_x = sigma_f / |f'| (the estimate is then
+  // within its own noise), or when f is exactly zero with nonzero error.
+  bool bracketed = false;
+  double blo = x_lo, bhi = x_hi, px = 0.0;
+  int slo = 0, ps = 0;  // sign of f at blo; sign at the previous point
+  double x = x0, est = x0, sig = HUGE_VAL;
+  int conv = 0, it = 0;
+  while (it < max_iter) {
+    double f = 0, sf = 0, df = 0, sdf = 0;
+    ttn_status s = eval(ctx, x, it, &f, &sf, &df, &sdf);
+    if (s != TTN_OK) {
+      if (iters) *iters = it;
+      return s;
+    }
+    if (!std::isfinite(f) || !std::isfinite(df) || !(sf >= 0.0) || !(sdf >= 0.0)) {
+      if (iters) *iters = it;
+      return fail_with(TTN_EINVAL, "crossing evaluator returned non-finite values");
+    }
+    if (trace) {
+      double* t = trace + 5 * (size_t)it;
+      t[0] = x, t[1] = f, t[2] = sf, t[3] = df, t[4] = sdf;
+    }
+    ++it;
+    const bool slope_ok = df != 0.0 && std::fabs(df) > 2.0 * sdf;
+    sig = slope_ok ? sf / std::fabs(df) : HUGE_VAL;
+    if (f == 0.0 && sf > 0.0) {  // statistically at the crossing
+      est = x;
+      conv = 1;
+      break;
+    }
+    const int sg = f > 0.0 ? 1 : (f < 0.0 ? -1 : 0);
+    if (sg != 0) {
+      if (bracketed) {
+        if (x > blo && x < bhi) {
+          if (sg == slo) blo = x;
+          else bhi = x;
+        }
+      } else if (ps != 0 && sg != ps) {
+        bracketed = true;
+        blo = std::min(x, px);
+        bhi = std::max(x, px);
+        slo = x < px ? sg : ps;
+      }
+      px = x;
+      ps = sg;
+    }
+    double xn;
+    if (slope_ok) xn = x - f / df;
+    else if (bracketed) xn = 0.5 * (blo + bhi);
+    else {  // neither a slope nor a bracket: no step to take
+      est = x;
+      break;
+    }
+    if (bracketed && !(xn > blo && xn < bhi)) xn = 0.5 * (blo + bhi);
+    xn = std::min(x_hi, std::max(x_lo, xn));
+    est = xn;
+    if (std::fabs(xn - x) <= std::max(x_tol, 2.0 * sig)) {
+      conv = 1;
+      break;
+    }
+    x = xn;
+  }
+  *x_star = est;
+  if (x_sigma) *x_sigma = sig;
+  if (iters) *iters = it;
+  if (converged) *converged = conv;
+  return TTN_OK;
+}
+
+}  // extern "C"
+
+namespace {
+// f(x) = ln p_L^a(x) - ln p_L^b(x) from two ttn_grad runs of fresh
+// trajectories (first_traj advances by `shots` per evaluation).
+struct CrossingCtx {
+  const ttn_circuit* a;
+  const ttn_circuit* b;
+  ttn_run_params p;
+  uint64_t shots;
+  int32_t wrt;
+  double h;
+};
+
+ttn_status crossing_eval(void* vctx, double x, int32_t iter, double* f, double* f_sigma, double* df,
+                         double* df_sigma) {
+  const CrossingCtx& c = *static_cast<const CrossingCtx*>(vctx);
+  ttn_run_params q = c.p;
+  if (c.wrt == 0) q.theta = x;
+  else q.gamma = x;
+  q.first_traj = c.p.first_traj + (uint64_t)iter * c.shots;
+  double pl[2], g[2], sg[2];
+  const ttn_circuit* circ[2] = {c.a, c.b};
+  for (int i = 0; i < 2; ++i) {
+    ttn_status s = ttn_grad(circ[i], &q, c.shots, c.wrt, c.h, &pl[i], &g[i], &sg[i], nullptr);
+    if (s != TTN_OK && s != TTN_EOVERFLOW) return s;  // EOVERFLOW: those shots are not counted
+    if (!(pl[i] > 0.0))
+      return fail_with(TTN_EINVAL, std::string("no logical failures on circuit ") + (i ? "b" : "a") +
+                                       " at x = " + std::to_string(x) + ": raise shots or move x0");
+  }
+  const double n = (double)c.shots;
+  *f = std::log(pl[0]) - std::log(pl[1]);
+  // delta method: var(ln p) = (1 - p) / (n p); d ln p / dx = p' / p
+  *f_sigma = std::sqrt((1.0 - pl[0]) / (n * pl[0]) + (1.0 - pl[1]) / (n * pl[1]));
+  *df = g[0] / pl[0] - g[1] / pl[1];
+  *df_sigma = std::sqrt((sg[0] / pl[0]) * (sg[0] / pl[0]) + (sg[1] / pl[1]) * (sg[1] / pl[1]));
+  return TTN_OK;
+}
+}  // namespace
+
+extern "C" {
+
+ttn_status ttn_crossing(const ttn_circuit* a, const ttn_circuit* b, const ttn_run_params* params,
+                        uint64_t shots, int32_t wrt, double h, double x0, double x_lo, double x_hi,
+                        int32_t max_iter, double x_tol, double* x_star, double* x_sigma, int32_t* iters,
+                        int32_t* converged, double* trace) {
+  ttn_status s = check_params(a, params);
+  if (s != TTN_OK) return s;
+  s = check_params(b, params);
+  if (s != TTN_OK) return s;
+  if (shots < 2) return fail_with(TTN_EINVAL, "shots must be >= 2");
+  if (wrt != 0 && wrt != 1) return fail_with(TTN_EINVAL, "wrt must be 0 (theta) or 1 (gamma)");
+  if (params->theta_per_traj || params->gamma_per_traj)
+    return fail_with(TTN_EINVAL, "ttn_crossing takes one theta and one gamma");
+  if (h <= 0.0) h = 1e-4;
+  if (wrt == 1 && (x_lo - h < 0.0 || x_hi + h > 1.0))
+    return fail_with(TTN_EINVAL, "gamma +- h must stay in [0, 1] over [x_lo, x_hi]");
+  CrossingCtx ctx{a, b, *params, shots, wrt, h};
+  return ttn_newton_crossing(crossing_eval, &ctx, x0, x_lo, x_hi, max_iter, x_tol, x_star, x_sigma, iters,
+                             converged, trace);
+}
+
 ttn_status ttn_decode(const ttn_circuit* c, uint64_t n, const uint8_t* records, uint8_t* fail,
                       int32_t* color, int64_t* score, void* cuda_stream) {
   if (!c || !records || !fail) return fail_with(TTN_EINVAL, "null argument");
