@@ -233,6 +233,20 @@ ttn_status ttn_crossing(const ttn_circuit* a, const ttn_circuit* b, const ttn_ru
                         double x_hi, int32_t max_iter, double x_tol, double* x_star,
                         double* x_sigma, int32_t* iters, int32_t* converged, double* trace);
 
+/* Threshold fit of Eq. 4 (Sec. IV.A): p_fail = A + B x + C x^2 with
+ * x = (p_err - tau) d^(1/nu), by weighted least squares over n points
+ * (distance d[i], strength p_err[i], failure rate p_fail[i], its standard
+ * error sigma[i] > 0; host arrays).  Levenberg-Marquardt from (tau0, nu0),
+ * with A, B, C first solved linearly at that start; stops when an accepted
+ * step lowers chi^2 by less than 1e-14 relative, or after max_iter steps.
+ * Outputs (host): params[5] = (A, B, C, tau, nu); cov[25] = (J^T W J)^-1 at
+ * the optimum, row-major (may be NULL); chi2 (may be NULL); iters (may be
+ * NULL).  EINVAL on n < 6, a single distance, d < 2, sigma <= 0,
+ * non-finite input, nu0 <= 0, or a singular fit. */
+ttn_status ttn_threshold_fit(int32_t n, const int32_t* d, const double* p_err, const double* p_fail,
+                             const double* sigma, double tau0, double nu0, int32_t max_iter,
+                             double* params, double* cov, double* chi2, int32_t* iters);
+
 /* Decodes n records ([n][n_record_bits] u8) with the concatenated MWPM
  * decoder (App. A.2) on the device.  fail [n] u8, color [n] int32 (winning
  * colour), score [n] int64 (total matching weight).  color/score may be NULL. */

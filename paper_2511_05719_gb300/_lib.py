@@ -41,7 +41,8 @@ EXPORTS = ["ttn_build_circuit", "ttn_free_circuit", "ttn_circuit_info", "ttn_cir
            "ttn_circuit_layout", "ttn_run_trajectories", "ttn_logical_error_rate", "ttn_decode",
            "ttn_debug_state", "ttn_philox_uniforms", "ttn_profile_begin", "ttn_profile_end",
            "ttn_grad", "ttn_decode_noalloc", "ttn_profile_class_ms", "ttn_profile_eig_phases",
-           "ttn_run_mixed", "ttn_newton_crossing", "ttn_crossing", "ttn_status_string",
+           "ttn_run_mixed", "ttn_newton_crossing", "ttn_crossing", "ttn_threshold_fit",
+           "ttn_status_string",
            "ttn_last_error"]
 
 # f(x) evaluator of ttn_newton_crossing: (ctx, x, iter, *f, *f_sigma, *df, *df_sigma) -> status
@@ -78,6 +79,8 @@ def load_library():
                                  ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                  ctypes.c_int32, ctypes.c_double, c_dblp, c_dblp, c_i32p, c_i32p,
                                  c_dblp]
+    lib.ttn_threshold_fit.argtypes = [ctypes.c_int32, c_i32p, c_dblp, c_dblp, c_dblp, ctypes.c_double,
+                                      ctypes.c_double, ctypes.c_int32, c_dblp, c_dblp, c_dblp, c_i32p]
     lib.ttn_logical_error_rate.argtypes = [vp, ctypes.POINTER(RunParams), ctypes.c_uint64, c_dblp,
                                            c_dblp, c_u64p]
     lib.ttn_decode.argtypes = [vp, ctypes.c_uint64, vp, vp, vp, vp, vp]
@@ -320,6 +323,23 @@ def crossing(circuit_a, circuit_b, shots, x0, x_lo, x_hi, wrt="theta", noise="sr
                             ctypes.byref(cv), tr.ctypes.data_as(c_dblp)))
     del keep
     return _crossing_result(xs, sx, it, cv, tr)
+
+
+def threshold_fit(d, p_err, p_fail, sigma, tau0, nu0=1.0, max_iter=500):
+    """Eq. 4 fit (ttn_threshold_fit): {A, B, C, tau, nu, cov (5x5), chi2, iters}."""
+    lib = load_library()
+    d = np.ascontiguousarray(d, dtype=np.int32)
+    x = [np.ascontiguousarray(a, dtype=np.float64) for a in (p_err, p_fail, sigma)]
+    n = d.size
+    if any(a.size != n for a in x):
+        raise ValueError("d, p_err, p_fail and sigma must have the same length")
+    prm, cov = np.zeros(5), np.zeros((5, 5))
+    c2, it = ctypes.c_double(), ctypes.c_int32()
+    _check(lib.ttn_threshold_fit(n, d.ctypes.data_as(c_i32p), *[a.ctypes.data_as(c_dblp) for a in x],
+                                 tau0, nu0, max_iter, prm.ctypes.data_as(c_dblp),
+                                 cov.ctypes.data_as(c_dblp), ctypes.byref(c2), ctypes.byref(it)))
+    return dict(A=prm[0], B=prm[1], C=prm[2], tau=prm[3], nu=prm[4], cov=cov, chi2=c2.value,
+                iters=it.value)
 
 
 def logical_error_rate(circuit, shots, noise="srx", theta=0.0, gamma=0.0, chi=16,

@@ -1,6 +1,7 @@
 // extern "C" boundary of the library (declared in include/ttn.h).  Argument
 // checking, circuit handles and marshalling; all simulation work runs in the
 // CUDA engine and decoder.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -498,6 +499,165 @@ ttn_status ttn_crossing(const ttn_circuit* a, const ttn_circuit* b, const ttn_ru
   CrossingCtx ctx{a, b, *params, shots, wrt, h};
   return ttn_newton_crossing(crossing_eval, &ctx, x0, x_lo, x_hi, max_iter, x_tol, x_star, x_sigma, iters,
                              converged, trace);
+}
+
+}  // extern "C"
+
+namespace {
+// Solves the k x k system M z = v in place by Gaussian elimination with
+// partial pivoting; false if M is singular to working precision.
+bool solve_small(int k, std::vector<double> M, std::vector<double> v, std::vector<double>& z) {
+  for (int c = 0; c < k; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < k; ++r)
+      if (std::fabs(M[r * k + c]) > std::fabs(M[piv * k + c])) piv = r;
+    if (!(std::fabs(M[piv * k + c]) > 1e-300)) return false;
+    if (piv != c) {
+      for (int j = 0; j < k; ++j) std::swap(M[c * k + j], M[piv * k + j]);
+      std::swap(v[c], v[piv]);
+    }
+    for (int r = c + 1; r < k; ++r) {
+      const double m = M[r * k + c] / M[c * k + c];
+      for (int j = c; j < k; ++j) M[r * k + j] -= m * M[c * k + j];
+      v[r] -= m * v[c];
+    }
+  }
+  z.assign(k, 0.0);
+  for (int r = k - 1; r >= 0; --r) {
+    double t = v[r];
+    for (int j = r + 1; j < k; ++j) t -= M[r * k + j] * z[j];
+    z[r] = t / M[r * k + r];
+  }
+  return true;
+}
+
+// Eq. 4 residuals r_i = (A + B x_i + C x_i^2 - y_i) / sigma_i, x_i =
+// (p_i - tau) d_i^(1/nu), and their Jacobian [n][5] in (A, B, C, tau, nu).
+double eq4_residuals(const double* q, int n, const int32_t* d, const double* p, const double* y,
+                     const double* sg, std::vector<double>& r, std::vector<double>* J) {
+  double chi2 = 0.0;
+  r.resize(n);
+  if (J) J->resize((size_t)5 * n);
+  for (int i = 0; i < n; ++i) {
+    const double ld = std::log((double)d[i]);
+    const double s = std::exp(ld / q[4]);  // d^(1/nu)
+    const double x = (p[i] - q[3]) * s;
+    r[i] = (q[0] + q[1] * x + q[2] * x * x - y[i]) / sg[i];
+    chi2 += r[i] * r[i];
+    if (J) {
+      const double dmdx = q[1] + 2.0 * q[2] * x;
+      double* Ji = J->data() + (size_t)5 * i;
+      Ji[0] = 1.0 / sg[i];
+      Ji[1] = x / sg[i];
+      Ji[2] = x * x / sg[i];
+      Ji[3] = -dmdx * s / sg[i];
+      Ji[4] = -dmdx * x * ld / (q[4] * q[4]) / sg[i];
+    }
+  }
+  return chi2;
+}
+}  // namespace
+
+extern "C" {
+
+ttn_status ttn_threshold_fit(int32_t n, const int32_t* d, const double* p_err, const double* p_fail,
+                             const double* sigma, double tau0, double nu0, int32_t max_iter, double* params,
+                             double* cov, double* chi2_out, int32_t* iters) {
+  if (!d || !p_err || !p_fail || !sigma || !params) return fail_with(TTN_EINVAL, "null argument");
+  if (n < 6) return fail_with(TTN_EINVAL, "need at least 6 points for 5 parameters");
+  if (max_iter < 1 || max_iter > 100000) return fail_with(TTN_EINVAL, "max_iter must be in [1, 100000]");
+  if (!(nu0 > 0.0) || !std::isfinite(tau0)) return fail_with(TTN_EINVAL, "need finite tau0 and nu0 > 0");
+  bool two_d = false;
+  for (int i = 0; i < n; ++i) {
+    if (d[i] < 2) return fail_with(TTN_EINVAL, "distances must be >= 2");
+    if (!(sigma[i] > 0.0) || !std::isfinite(p_err[i]) || !std::isfinite(p_fail[i]))
+      return fail_with(TTN_EINVAL, "need finite points and sigma > 0");
+    if (d[i] != d[0]) two_d = true;
+  }
+  if (!two_d) return fail_with(TTN_EINVAL, "need at least two distances");
+  // start: (A, B, C) by weighted linear least squares at (tau0, nu0)
+  double q[5] = {0.0, 0.0, 0.0, tau0, nu0};
+  std::vector<double> r, J;
+  eq4_residuals(q, n, d, p_err, p_fail, sigma, r, &J);
+  {
+    std::vector<double> M(9, 0.0), v(3, 0.0), z;
+    for (int i = 0; i < n; ++i) {
+      const double* Ji = J.data() + (size_t)5 * i;
+      const double yi = p_fail[i] / sigma[i];
+      for (int a = 0; a < 3; ++a) {
+        v[a] += Ji[a] * yi;
+        for (int b = 0; b < 3; ++b) M[a * 3 + b] += Ji[a] * Ji[b];
+      }
+    }
+    if (!solve_small(3, M, v, z)) return fail_with(TTN_EINVAL, "points do not determine A, B, C at the start");
+    q[0] = z[0], q[1] = z[1], q[2] = z[2];
+  }
+  // Levenberg-Marquardt (Marquardt's diagonal scaling)
+  double chi2 = eq4_residuals(q, n, d, p_err, p_fail, sigma, r, &J);
+  double lambda = 1e-3;
+  int it = 0;
+  std::vector<double> JTJ(25), g(5), step;
+  for (; it < max_iter; ++it) {
+    std::fill(JTJ.begin(), JTJ.end(), 0.0);
+    std::fill(g.begin(), g.end(), 0.0);
+    for (int i = 0; i < n; ++i) {
+      const double* Ji = J.data() + (size_t)5 * i;
+      for (int a = 0; a < 5; ++a) {
+        g[a] -= Ji[a] * r[i];
+        for (int b = 0; b < 5; ++b) JTJ[a * 5 + b] += Ji[a] * Ji[b];
+      }
+    }
+    bool improved = false;
+    double gain = 0.0;
+    for (int tries = 0; tries < 40 && !improved; ++tries) {
+      std::vector<double> M = JTJ;
+      for (int a = 0; a < 5; ++a) M[a * 5 + a] += lambda * std::max(JTJ[a * 5 + a], 1e-300);
+      if (!solve_small(5, M, g, step)) {
+        lambda *= 10.0;
+        continue;
+      }
+      double qn[5];
+      for (int a = 0; a < 5; ++a) qn[a] = q[a] + step[a];
+      if (!(qn[4] > 0.0)) {
+        lambda *= 10.0;
+        continue;
+      }
+      std::vector<double> rn;
+      const double c2 = eq4_residuals(qn, n, d, p_err, p_fail, sigma, rn, nullptr);
+      if (std::isfinite(c2) && c2 < chi2) {
+        gain = chi2 - c2;
+        std::copy(qn, qn + 5, q);
+        chi2 = eq4_residuals(q, n, d, p_err, p_fail, sigma, r, &J);
+        lambda = std::max(lambda / 10.0, 1e-12);
+        improved = true;
+      } else {
+        lambda *= 10.0;
+      }
+    }
+    if (!improved || gain <= 1e-14 * std::max(chi2, 1e-300)) {
+      ++it;
+      break;
+    }
+  }
+  for (int a = 0; a < 5; ++a) params[a] = q[a];
+  if (chi2_out) *chi2_out = chi2;
+  if (iters) *iters = it;
+  if (cov) {
+    // covariance (J^T W J)^-1 at the optimum, column by column
+    std::fill(JTJ.begin(), JTJ.end(), 0.0);
+    for (int i = 0; i < n; ++i) {
+      const double* Ji = J.data() + (size_t)5 * i;
+      for (int a = 0; a < 5; ++a)
+        for (int b = 0; b < 5; ++b) JTJ[a * 5 + b] += Ji[a] * Ji[b];
+    }
+    for (int c = 0; c < 5; ++c) {
+      std::vector<double> e(5, 0.0), z;
+      e[c] = 1.0;
+      if (!solve_small(5, JTJ, e, z)) return fail_with(TTN_EINVAL, "singular normal matrix at the optimum");
+      for (int a = 0; a < 5; ++a) cov[a * 5 + c] = z[a];
+    }
+  }
+  return TTN_OK;
 }
 
 ttn_status ttn_decode(const ttn_circuit* c, uint64_t n, const uint8_t* records, uint8_t* fail,
