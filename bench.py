@@ -251,9 +251,12 @@ def main():
     t0 = time.perf_counter()
     step(device_out=False)
     e2e_s = time.perf_counter() - t0
+    # bytes the call copies per step: theta, gamma and trajectory index in
+    # (8 B each per trajectory); records, fail byte, log-probability,
+    # discarded weight, near-tie count, error word and two error-step words out
     e2e = {"value": world * B / e2e_s, "unit": "trajectories/s",
-           "h2d_bytes_per_step": 8 * B,
-           "d2h_bytes_per_step": B * (circ.n_record_bits + 1 + 8 + 8 + 4)}
+           "h2d_bytes_per_step": 24 * B,
+           "d2h_bytes_per_step": B * (circ.n_record_bits + 1 + 8 + 8 + 4 + 4 + 8)}
     # roofline of the dominant kernel class (most device time in the timed region)
     cms = prof["class_ms"]
     rclass = a.roofline_class if a.roofline_class != "auto" else max(cms, key=lambda c: cms[c])
