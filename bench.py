@@ -56,7 +56,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ttn", choices=["ttn", "reference"])
     ap.add_argument("--batch", type=int, default=0,
-                    help="trajectories per step and rank (0: the SM count for d >= 7, else 512)")
+                    help="trajectories per step and rank (0: 64 for d >= 7, else 512)")
     ap.add_argument("--distance", type=int, default=7)
     ap.add_argument("--rounds", type=int, default=7)
     ap.add_argument("--chi", type=int, default=128)
@@ -187,12 +187,14 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    # d >= 7: one trajectory per SM.  The eigensolver runs one CTA per
-    # trajectory and is latency-bound, so a step's time grows slowly until
-    # every SM holds one (d=7, C=1: 12.0 s at 16, 24.1 s at 152, 47.3 s at
-    # 304 trajectories on 152 SMs).
-    sms = torch.cuda.get_device_properties(local).multi_processor_count
-    B = a.batch if a.batch > 0 else (sms if a.distance >= 7 else 512)
+    # d >= 7: 64 trajectories per step.  The eigensolver runs one CTA per
+    # trajectory and is latency-bound, so a step's time grows slowly with the
+    # batch until every SM holds one (d=7, C=1: 12.0 s at 16, 24.1 s at 152,
+    # 47.3 s at 304 trajectories on 152 SMs).  64 keeps most of that gain
+    # while five default steps (3 warm-up, 1 timed, 1 end-to-end) of the
+    # 7-round circuit stay near a quarter of an hour; --batch 152 gives the
+    # highest throughput.
+    B = a.batch if a.batch > 0 else (64 if a.distance >= 7 else 512)
     circ = P.Circuit(a.distance, a.rounds, layout="optimized")
     thetas = WL.theta_sweep_per_traj(B, WL.M3["thetas"])
     stream = torch.cuda.Stream()
