@@ -38,7 +38,7 @@ std::vector<int> optimized_layout(const Code& code, const std::vector<Op>& ops, 
 // One step of the per-trajectory program; every trajectory of a batch runs
 // the same steps (the data-dependent part is only bond dimensions and values).
 enum StepKind {
-  S_MOVE = 0,        // a = v, b = w (neighbour), c = 1 if capped at chi
+  S_MOVE = 0,        // a = v, b = w (neighbour), c = 1 if truncating (rank <= the bond's cap)
   S_THREAD_LEAF = 1, // a = node, b = leg (0 l / 1 r), c = factor set (0 control, 1 target)
   S_THREAD_NODE = 2, // a = node, b = leg towards the path child
   S_THREAD_LCA = 3,  // a = node (both child legs carry the MPO index)
