@@ -247,6 +247,19 @@ ttn_status ttn_threshold_fit(int32_t n, const int32_t* d, const double* p_err, c
                              const double* sigma, double tau0, double nu0, int32_t max_iter,
                              double* params, double* cov, double* chi2, int32_t* iters);
 
+/* The sums behind ttn_grad, for combining shards run on several ranks (each
+ * rank its own first_traj range; the paper's shots are independent, Sec.
+ * III.C): over the valid shots (fail byte <= 1) their number n_valid, the
+ * failures n_fail, sum_fs = sum of fail * score and sum_fs2 = sum of
+ * (fail * score)^2, the score being ttn_grad's d/dx log p.  Then p_L =
+ * n_fail / n_valid, dp_L/dx = sum_fs / n_valid and its standard error
+ * sqrt((sum_fs2 / n - (sum_fs / n)^2) / (n - 1)), n = n_valid, exactly as
+ * ttn_grad forms them.  Arguments and errors as ttn_grad; outputs are host
+ * scalars. */
+ttn_status ttn_grad_sums(const ttn_circuit* circuit, const ttn_run_params* params, uint64_t shots,
+                         int32_t wrt, double h, uint64_t* n_valid, uint64_t* n_fail,
+                         double* sum_fs, double* sum_fs2);
+
 /* Decodes n records ([n][n_record_bits] u8) with the concatenated MWPM
  * decoder (App. A.2) on the device.  fail [n] u8, color [n] int32 (winning
  * colour), score [n] int64 (total matching weight).  color/score may be NULL. */

@@ -41,7 +41,7 @@ EXPORTS = ["ttn_build_circuit", "ttn_free_circuit", "ttn_circuit_info", "ttn_cir
            "ttn_circuit_layout", "ttn_run_trajectories", "ttn_logical_error_rate", "ttn_decode",
            "ttn_debug_state", "ttn_philox_uniforms", "ttn_profile_begin", "ttn_profile_end",
            "ttn_grad", "ttn_decode_noalloc", "ttn_profile_class_ms", "ttn_profile_eig_phases",
-           "ttn_run_mixed", "ttn_newton_crossing", "ttn_crossing", "ttn_threshold_fit",
+           "ttn_run_mixed", "ttn_newton_crossing", "ttn_crossing", "ttn_threshold_fit", "ttn_grad_sums",
            "ttn_status_string",
            "ttn_last_error"]
 
@@ -81,6 +81,8 @@ def load_library():
                                  c_dblp]
     lib.ttn_threshold_fit.argtypes = [ctypes.c_int32, c_i32p, c_dblp, c_dblp, c_dblp, ctypes.c_double,
                                       ctypes.c_double, ctypes.c_int32, c_dblp, c_dblp, c_dblp, c_i32p]
+    lib.ttn_grad_sums.argtypes = [vp, ctypes.POINTER(RunParams), ctypes.c_uint64, ctypes.c_int32,
+                                  ctypes.c_double, c_u64p, c_u64p, c_dblp, c_dblp]
     lib.ttn_logical_error_rate.argtypes = [vp, ctypes.POINTER(RunParams), ctypes.c_uint64, c_dblp,
                                            c_dblp, c_u64p]
     lib.ttn_decode.argtypes = [vp, ctypes.c_uint64, vp, vp, vp, vp, vp]
@@ -432,6 +434,23 @@ def grad(circuit, shots, wrt="theta", noise="srx", theta=0.0, gamma=0.0, chi=16,
     if return_score:
         return pl.value, g.value, sg.value, score
     return pl.value, g.value, sg.value
+
+
+def grad_sums(circuit, shots, wrt="theta", noise="srx", theta=0.0, gamma=0.0, chi=16,
+              precision="fp64", seed=0, first_traj=0, h=1e-4, svd_eps=0.0, svd_mode="auto",
+              gemm_mode="auto"):
+    """ttn_grad_sums: (n_valid, n_fail, sum_fs, sum_fs2) of the score-function estimator."""
+    lib = load_library()
+    p, keep = _run_params(noise, theta, gamma, chi, precision, seed, first_traj, svd_eps,
+                          svd_mode=svd_mode, gemm_mode=gemm_mode)
+    nv, nf = ctypes.c_uint64(), ctypes.c_uint64()
+    s1, s2 = ctypes.c_double(), ctypes.c_double()
+    st = lib.ttn_grad_sums(circuit.handle, ctypes.byref(p), shots, 0 if wrt == "theta" else 1, h,
+                           ctypes.byref(nv), ctypes.byref(nf), ctypes.byref(s1), ctypes.byref(s2))
+    if st not in (0, 6):      # 6: some shots exceeded the decoder's bound and were not counted
+        _check(st)
+    del keep
+    return nv.value, nf.value, s1.value, s2.value
 
 
 def logical_error_rate_fn(circuit, shots, **kw):

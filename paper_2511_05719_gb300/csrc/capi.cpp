@@ -308,8 +308,20 @@ ttn_status ttn_logical_error_rate(const ttn_circuit* c, const ttn_run_params* p,
   return TTN_OK;
 }
 
-ttn_status ttn_grad(const ttn_circuit* c, const ttn_run_params* p, uint64_t shots, int32_t wrt,
-                    double h, double* p_L, double* dpL, double* dpL_sigma, double* score) {
+}  // extern "C"
+
+namespace {
+// Runs `shots` trajectories with the score replay and accumulates, over the
+// valid shots (fail byte <= 1), their count, failures, sum of fail * score
+// and of its square.  EOVERFLOW (after the sums) if some shots exceeded the
+// decoder's bound.
+struct GradSums {
+  uint64_t n = 0, n_fail = 0;
+  double s1 = 0.0, s2 = 0.0;
+};
+
+ttn_status grad_run(const ttn_circuit* c, const ttn_run_params* p, uint64_t shots, int32_t wrt, double h,
+                    GradSums& g, double* score) {
   ttn_status s = check_params(c, p);
   if (s != TTN_OK) return s;
   if (shots < 2) return fail_with(TTN_EINVAL, "shots must be >= 2");
@@ -336,7 +348,7 @@ ttn_status ttn_grad(const ttn_circuit* c, const ttn_run_params* p, uint64_t shot
   // score-function estimator: dp_L/dx = E[fail * d/dx log p(trajectory)]
   double n = 0, nf = 0, m1 = 0, m2 = 0;
   for (uint64_t i = 0; i < shots; ++i) {
-    if (fail[i] > 1) continue;  // decoder bound exceeded: not counted
+    if (fail[i] > 1) continue;  // decoder bound exceeded or state lost: not counted
     const double f = fail[i];
     const double x = f * sc[i];
     n += 1;
@@ -344,11 +356,10 @@ ttn_status ttn_grad(const ttn_circuit* c, const ttn_run_params* p, uint64_t shot
     m1 += x;
     m2 += x * x;
   }
-  if (n < 2) return fail_with(TTN_EOVERFLOW, "no decodable shots");
-  const double mean = m1 / n, var = fmax(0.0, m2 / n - mean * mean);
-  if (p_L) *p_L = nf / n;
-  if (dpL) *dpL = mean;
-  if (dpL_sigma) *dpL_sigma = std::sqrt(var / (n - 1));
+  g.n = (uint64_t)n;
+  g.n_fail = (uint64_t)nf;
+  g.s1 = m1;
+  g.s2 = m2;
   if (score) std::memcpy(score, sc.data(), sizeof(double) * shots);
   if (out.decode_overflow > 0) {
     set_error("decoder: some shots exceeded the matching bound and were not counted");
@@ -356,6 +367,38 @@ ttn_status ttn_grad(const ttn_circuit* c, const ttn_run_params* p, uint64_t shot
   }
   return TTN_OK;
 }
+}  // namespace
+
+extern "C" {
+
+ttn_status ttn_grad(const ttn_circuit* c, const ttn_run_params* p, uint64_t shots, int32_t wrt,
+                    double h, double* p_L, double* dpL, double* dpL_sigma, double* score) {
+  GradSums g;
+  ttn_status s = grad_run(c, p, shots, wrt, h, g, score);
+  if (s != TTN_OK && s != TTN_EOVERFLOW) return s;
+  const double n = (double)g.n;
+  if (n < 2) return fail_with(TTN_EOVERFLOW, "no decodable shots");
+  const double mean = g.s1 / n, var = fmax(0.0, g.s2 / n - mean * mean);
+  if (p_L) *p_L = (double)g.n_fail / n;
+  if (dpL) *dpL = mean;
+  if (dpL_sigma) *dpL_sigma = std::sqrt(var / (n - 1));
+  return s;
+}
+
+ttn_status ttn_grad_sums(const ttn_circuit* c, const ttn_run_params* p, uint64_t shots, int32_t wrt,
+                         double h, uint64_t* n_valid, uint64_t* n_fail, double* sum_fs,
+                         double* sum_fs2) {
+  if (!n_valid || !n_fail || !sum_fs || !sum_fs2) return fail_with(TTN_EINVAL, "null argument");
+  GradSums g;
+  ttn_status s = grad_run(c, p, shots, wrt, h, g, nullptr);
+  if (s != TTN_OK && s != TTN_EOVERFLOW) return s;
+  *n_valid = g.n;
+  *n_fail = g.n_fail;
+  *sum_fs = g.s1;
+  *sum_fs2 = g.s2;
+  return s;
+}
+
 
 ttn_status ttn_newton_crossing(ttn_crossing_eval eval, void* ctx, double x0, double x_lo, double x_hi,
                                int32_t max_iter, double x_tol, double* x_star, double* x_sigma,

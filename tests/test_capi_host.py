@@ -100,3 +100,19 @@ def test_run_mixed_rejects_bad_items_before_any_device_work():
     fails = (ctypes.c_void_p * 1)(None)
     assert lib2.ttn_run_mixed(1, circs, ctypes.byref(p), cnt, fails, None, None) == 1
     assert b"logical_fail" in lib.ttn_last_error()
+
+
+def test_grad_sums_argument_checks_before_device_work():
+    _lib = _lib_or_skip()
+    import paper_2511_05719_gb300 as P
+    c = P.Circuit(3, 1)
+    for kw in (dict(shots=1), dict(shots=10, wrt="gamma"), dict(shots=10, chi=0),
+               dict(shots=10, noise="ad", wrt="theta", gamma=0.1)):
+        shots = kw.pop("shots")
+        with pytest.raises(P.TTNError) as e:
+            P.grad_sums(c, shots, **kw)
+        assert e.value.status == 1, kw
+    lib = _lib.load_library()
+    p = _lib.RunParams()
+    p.noise, p.chi, p.theta = 1, 8, 0.1
+    assert lib.ttn_grad_sums(c.handle, ctypes.byref(p), 10, 0, 0.0, None, None, None, None) == 1

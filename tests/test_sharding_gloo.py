@@ -72,3 +72,65 @@ def test_gloo_two_ranks_sum_counts():
         assert abs(p_l - nf / nv) < 1e-15
     spans = sorted((a, b) for _, a, b, _ in out)
     assert spans[0][0] == 0 and spans[-1][1] == n_total and spans[0][1] == spans[1][0]
+
+
+def _fake_score(traj):
+    # host stand-in for a trajectory's d/dx log p: depends only on the index
+    x = ((traj + 17) * 0x85EBCA77) & 0xFFFFFFFF
+    return (x / 2.0 ** 32 - 0.5) * 40.0
+
+
+def _grad_sums(a, b):
+    f = np.array([_fake_fail(t) for t in range(a, b)])
+    s = np.array([_fake_score(t) for t in range(a, b)])
+    ok = f <= 1
+    fs = f[ok] * s[ok]
+    return int(ok.sum()), int(f[ok].sum()), float(fs.sum()), float((fs * fs).sum())
+
+
+def _grad_worker(rank, world, port, n_total, q):
+    import torch.distributed as dist
+    from paper_2511_05719_gb300.sharding import combine_grad_sums
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    a, b = trajectory_range(n_total, rank, world)
+    q.put((rank, combine_grad_sums(*_grad_sums(a, b))))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_gloo_two_ranks_combine_gradient_sums():
+    """The sharded score-function gradient equals the single-process one,
+    formed as ttn_grad forms it: p_L = n_fail / n, mean of fail * score, its
+    standard error sqrt((E[x^2] - E[x]^2) / (n - 1))."""
+    import torch.multiprocessing as mp
+    n_total, world = 1001, 2
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_grad_worker, args=(r, world, port, n_total, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    out = [q.get(timeout=120) for _ in range(world)]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    f = np.array([_fake_fail(t) for t in range(n_total)])
+    s = np.array([_fake_score(t) for t in range(n_total)])
+    ok = f <= 1
+    x = f[ok] * s[ok]
+    n = ok.sum()
+    ref = (f[ok].sum() / n, x.mean(), np.sqrt(max(0.0, (x * x).mean() - x.mean() ** 2) / (n - 1)), n)
+    for rank, (p_l, g, sg, nv) in out:
+        assert nv == ref[3]
+        assert abs(p_l - ref[0]) < 1e-15
+        assert abs(g - ref[1]) < 1e-12 * max(1.0, abs(ref[1]))
+        assert abs(sg - ref[2]) < 1e-12 * max(1.0, ref[2])
+
+
+def test_combine_grad_sums_without_a_process_group():
+    from paper_2511_05719_gb300.sharding import combine_grad_sums
+    p, g, sg, n = combine_grad_sums(*_grad_sums(0, 500))
+    assert n > 2 and 0 < p < 1 and sg > 0
+    assert np.isnan(combine_grad_sums(1, 0, 0.0, 0.0)[1])
