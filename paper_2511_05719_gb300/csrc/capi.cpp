@@ -271,9 +271,16 @@ ttn_status ttn_run_mixed(int32_t n_items, const ttn_circuit* const* circuits, co
     // the profiler accumulates on the host: keep it on one thread
     for (int i = 0; i < n_items; ++i) work(i);
   } else {
+    // no exception may leave the C ABI: items whose thread cannot be
+    // created run on the calling thread after the others are started
     std::vector<std::thread> th;
-    th.reserve(n_items);
-    for (int i = 0; i < n_items; ++i) th.emplace_back(work, i);
+    int started = 0;
+    try {
+      th.reserve(n_items);
+      for (; started < n_items; ++started) th.emplace_back(work, started);
+    } catch (...) {
+    }
+    for (int i = started; i < n_items; ++i) work(i);
     for (std::thread& t : th) t.join();
   }
   cleanup();
