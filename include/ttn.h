@@ -260,6 +260,24 @@ ttn_status ttn_grad_sums(const ttn_circuit* circuit, const ttn_run_params* param
                          int32_t wrt, double h, uint64_t* n_valid, uint64_t* n_fail,
                          double* sum_fs, double* sum_fs2);
 
+/* Host-only check of the device memory layout (no GPU needed).  Each node
+ * of the tree has a fixed slot of 4 cl cr cu elements, c the structural caps
+ * min(chi, 2^{qubits on the smaller side}) of its three bonds.  This replays
+ * the circuit's step program with every centre move keeping the largest
+ * rank its kernels allow (min(n, cap) for the n-column bond matrix, even
+ * where rounding exceeds the exact rank; cap = the bond's structural cap
+ * when the move truncates, twice that while a gate's operator index rides
+ * on the bond) and every threading step doubling bonds as the kernels do,
+ * and reports the largest node size / slot ratio seen (worst_fill; <= 1
+ * means no trajectory, whatever its rounding, can overflow a slot), where
+ * (worst_node, worst_step; -1 = the initial state) and how many truncating
+ * moves have a structural cap below both chi and n (binding_moves: moves
+ * where a cap at chi alone would keep more).  Outputs other than worst_fill
+ * may be NULL. */
+ttn_status ttn_slot_check(const ttn_circuit* circuit, int32_t noise, int32_t chi,
+                          double* worst_fill, int32_t* worst_node, int32_t* worst_step,
+                          int64_t* binding_moves);
+
 /* Decodes n records ([n][n_record_bits] u8) with the concatenated MWPM
  * decoder (App. A.2) on the device.  fail [n] u8, color [n] int32 (winning
  * colour), score [n] int64 (total matching weight).  color/score may be NULL. */

@@ -42,6 +42,7 @@ EXPORTS = ["ttn_build_circuit", "ttn_free_circuit", "ttn_circuit_info", "ttn_cir
            "ttn_debug_state", "ttn_philox_uniforms", "ttn_profile_begin", "ttn_profile_end",
            "ttn_grad", "ttn_decode_noalloc", "ttn_profile_class_ms", "ttn_profile_eig_phases",
            "ttn_run_mixed", "ttn_newton_crossing", "ttn_crossing", "ttn_threshold_fit", "ttn_grad_sums",
+           "ttn_slot_check",
            "ttn_status_string",
            "ttn_last_error"]
 
@@ -83,6 +84,7 @@ def load_library():
                                       ctypes.c_double, ctypes.c_int32, c_dblp, c_dblp, c_dblp, c_i32p]
     lib.ttn_grad_sums.argtypes = [vp, ctypes.POINTER(RunParams), ctypes.c_uint64, ctypes.c_int32,
                                   ctypes.c_double, c_u64p, c_u64p, c_dblp, c_dblp]
+    lib.ttn_slot_check.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, c_dblp, c_i32p, c_i32p, c_i64p]
     lib.ttn_logical_error_rate.argtypes = [vp, ctypes.POINTER(RunParams), ctypes.c_uint64, c_dblp,
                                            c_dblp, c_u64p]
     lib.ttn_decode.argtypes = [vp, ctypes.c_uint64, vp, vp, vp, vp, vp]
@@ -451,6 +453,17 @@ def grad_sums(circuit, shots, wrt="theta", noise="srx", theta=0.0, gamma=0.0, ch
         _check(st)
     del keep
     return nv.value, nf.value, s1.value, s2.value
+
+
+def slot_check(circuit, noise="srx", chi=16):
+    """ttn_slot_check: {worst_fill, worst_node, worst_step, binding_moves}."""
+    lib = load_library()
+    wf, wn, ws, nb = ctypes.c_double(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
+    _check(lib.ttn_slot_check(circuit.handle, NOISE[noise] if isinstance(noise, str) else int(noise),
+                              chi, ctypes.byref(wf), ctypes.byref(wn), ctypes.byref(ws),
+                              ctypes.byref(nb)))
+    return dict(worst_fill=wf.value, worst_node=wn.value, worst_step=ws.value,
+                binding_moves=nb.value)
 
 
 def logical_error_rate_fn(circuit, shots, **kw):

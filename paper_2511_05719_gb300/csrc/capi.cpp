@@ -710,6 +710,22 @@ ttn_status ttn_threshold_fit(int32_t n, const int32_t* d, const double* p_err, c
   return TTN_OK;
 }
 
+ttn_status ttn_slot_check(const ttn_circuit* c, int32_t noise, int32_t chi, double* worst_fill,
+                          int32_t* worst_node, int32_t* worst_step, int64_t* binding_moves) {
+  if (!c || !worst_fill) return fail_with(TTN_EINVAL, "null argument");
+  if (noise < TTN_NOISE_NONE || noise > TTN_NOISE_SRX_AD) return fail_with(TTN_EINVAL, "unknown noise model");
+  if (chi < 1 || chi > 4096) return fail_with(TTN_EINVAL, "chi must be in [1, 4096]");
+  double wf = 0.0;
+  int wn = -1, ws = -1;
+  int64_t nb = 0;
+  slot_check(*c, noise, chi, &wf, &wn, &ws, &nb);
+  *worst_fill = wf;
+  if (worst_node) *worst_node = wn;
+  if (worst_step) *worst_step = ws;
+  if (binding_moves) *binding_moves = nb;
+  return TTN_OK;
+}
+
 ttn_status ttn_decode(const ttn_circuit* c, uint64_t n, const uint8_t* records, uint8_t* fail,
                       int32_t* color, int64_t* score, void* cuda_stream) {
   if (!c || !records || !fail) return fail_with(TTN_EINVAL, "null argument");

@@ -2796,6 +2796,65 @@ size_t run_bytes_per_traj(const ttn_circuit& c, const RunRequest& rq) {
   return Engine<float>(c, prog, rq.chi, rq.noise, nullptr).bytes_per_traj();
 }
 
+// Worst case of the node-slot fill over the step program: every move keeps
+// the largest rank its kernels allow, min(n, cap) for an m x n matrix (cap =
+// the bond's structural cap on truncating moves and twice that otherwise, as
+// S_MOVE launches it; rounding can keep more than the exact rank min(m, n):
+// an FP32 Gram matrix turns the n - m zero eigenvalues of a wide M into
+// values near the kept-rank floor), threading doubles bonds as its kernels
+// do, and every node's element count is compared with its slot after each
+// step.  fill <= 1 means no trajectory can overflow a slot, whatever its
+// rounding.  binding counts truncating moves whose structural cap is below
+// chi and below n: there a cap at chi alone would keep more.
+void slot_check(const ttn_circuit& c, int noise, int chi, double* worst_fill, int* worst_node,
+                int* worst_step, int64_t* binding) {
+  Program prog = compile_program(c, noise, -1);
+  Engine<float> eng(c, prog, chi, noise, nullptr);  // capacities only
+  const int L = c.L;
+  std::vector<int64_t> D(2 * L, 1);
+  for (int q = 0; q < c.N; ++q) D[L + c.leaf_of_qubit[q]] = 2;
+  auto size = [&](int v) { return D[2 * v] * D[2 * v + 1] * (v == 1 ? 1 : D[v]); };
+  double wf = 0.0;
+  int wn = -1, ws = -1;
+  int64_t nb = 0;
+  auto check = [&](int v, int si) {
+    const double f = (double)size(v) / (double)eng.ncap[v];
+    if (f > wf) wf = f, wn = v, ws = si;
+  };
+  for (int v = 1; v < L; ++v) check(v, -1);
+  for (int si = 0; si < (int)prog.steps.size(); ++si) {
+    const Step& s = prog.steps[si];
+    switch (s.kind) {
+      case S_THREAD_LEAF:
+      case S_THREAD_NODE:
+        D[s.a] *= 2;
+        check(s.a, si);
+        break;
+      case S_THREAD_LCA:
+        check(s.a, si);
+        break;
+      case S_MOVE: {
+        const int v = s.a, w = s.b;
+        const int bond = (w == v / 2) ? v : w;
+        const int64_t n = D[bond], m = size(v) / n;  // M is m x n
+        const int64_t cap = s.c ? eng.bcap[bond] : 2 * (int64_t)eng.bcap[bond];
+        (void)m;
+        if (s.c && eng.bcap[bond] < chi && n > eng.bcap[bond]) ++nb;
+        D[bond] = std::min(n, cap);
+        check(v, si);
+        check(w, si);
+        break;
+      }
+      default:
+        break;
+    }
+  }
+  *worst_fill = wf;
+  *worst_node = wn;
+  *worst_step = ws;
+  *binding = nb;
+}
+
 ttn_status run_trajectories_device(const ttn_circuit& c, const RunRequest& rq, RunOutputs& out) {
   if (rq.precision == TTN_PREC_FP64) return run_impl<double>(c, rq, out);
   return run_impl<float>(c, rq, out);

@@ -72,6 +72,10 @@ ttn_status run_trajectories_device(const ttn_circuit& c, const RunRequest& rq, R
 // sizing only; no CUDA call).
 size_t run_bytes_per_traj(const ttn_circuit& c, const RunRequest& rq);
 
+// Worst-case node-slot fill over the step program (host only; see engine.cu).
+void slot_check(const ttn_circuit& c, int noise, int chi, double* worst_fill, int* worst_node,
+                int* worst_step, int64_t* binding);
+
 // Decodes nb records that live on the device; fail/color/score are device
 // pointers when on_device, else host pointers.
 ttn_status decode_device(const ttn_circuit& c, int nb, const uint8_t* d_records, uint8_t* fail,
