@@ -71,6 +71,24 @@ def workload_name(a):
     return "d%d_C%d_srx_theta_sweep8_chi%d_%s" % (a.distance, a.rounds, a.chi, a.precision)
 
 
+def default_batch(a):
+    # d >= 7: 64 trajectories per step.  The eigensolver runs one CTA per
+    # trajectory and is latency-bound, so a step's time grows slowly with the
+    # batch until every SM holds one (d=7, C=1: 12.0 s at 16, 24.1 s at 152,
+    # 47.3 s at 304 trajectories on 152 SMs).  64 keeps most of that gain
+    # while five default steps (3 warm-up, 1 timed, 1 end-to-end) of the
+    # 7-round circuit stay near a quarter of an hour; --batch 152 gives the
+    # highest throughput.
+    return a.batch if a.batch > 0 else (64 if a.distance >= 7 else 512)
+
+
+def run_config(a, B):
+    """The workload both arms report (the same keys and values)."""
+    return {"workload": workload_name(a), "trajectories_per_step": B, "rounds": a.rounds,
+            "distance": a.distance, "chi": a.chi,
+            "l2": "working set per step far above L2 (no flush)"}
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
 
@@ -165,7 +183,7 @@ def run_reference(a):
     line = {"impl": "reference", "metric": METRIC, "value": v,
             "unit": "trajectories/s", "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
-            "data": "synthetic", "config": {"workload": workload_name(a)},
+            "data": "synthetic", "config": run_config(a, default_batch(a)),
             "cpu_baseline": cb,
             "e2e": {"value": v, "unit": "trajectories/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
@@ -187,14 +205,7 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    # d >= 7: 64 trajectories per step.  The eigensolver runs one CTA per
-    # trajectory and is latency-bound, so a step's time grows slowly with the
-    # batch until every SM holds one (d=7, C=1: 12.0 s at 16, 24.1 s at 152,
-    # 47.3 s at 304 trajectories on 152 SMs).  64 keeps most of that gain
-    # while five default steps (3 warm-up, 1 timed, 1 end-to-end) of the
-    # 7-round circuit stay near a quarter of an hour; --batch 152 gives the
-    # highest throughput.
-    B = a.batch if a.batch > 0 else (64 if a.distance >= 7 else 512)
+    B = default_batch(a)
     circ = P.Circuit(a.distance, a.rounds, layout="optimized")
     thetas = WL.theta_sweep_per_traj(B, WL.M3["thetas"])
     stream = torch.cuda.Stream()
@@ -284,10 +295,7 @@ def main():
             "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "c64" if a.precision == "fp32" else "c128",
             "data": "synthetic",
-            "config": {"workload": workload_name(a), "trajectories_per_step": B,
-                       "rounds": a.rounds, "distance": a.distance, "chi": a.chi,
-                       "l2": "working set per step far above L2 (no flush)",
-                       "lost_trajectories_last_step": lost},
+            "config": dict(run_config(a, B), lost_trajectories_last_step=lost),
             "clocks": ck, "e2e": e2e, "gpu_launches": int(sum(prof["launches"].values())),
             "roofline": roof,
             "ledger_tflop": {k: v / 1e12 for k, v in prof["flops"].items()},
