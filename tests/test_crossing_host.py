@@ -125,3 +125,19 @@ def test_crossing_argument_checks_before_device_work():
         with pytest.raises(P.TTNError) as e:
             P.crossing(a, b, **kw)
         assert e.value.status == 1, c
+
+
+def test_iteration_limit_and_exact_zero():
+    _lib_or_skip()
+    # slow convergence with a tight tolerance: stops at max_iter, not converged
+    r = P.newton_crossing(lambda x, it: (x ** 3, 0.0, 3 * x ** 2, 0.0), 0.9, -1.0, 1.0,
+                          max_iter=4, x_tol=1e-15)
+    assert r["iters"] == 4 and not r["converged"]
+    assert r["trace"].shape == (4, 5) and np.all(np.diff(r["trace"][:, 0]) < 0)
+    # f exactly zero with a nonzero error: at the crossing within noise
+    r = P.newton_crossing(lambda x, it: (0.0, 0.1, 1.0, 0.01), 0.3, 0.0, 1.0)
+    assert r["converged"] and r["x"] == 0.3 and r["iters"] == 1
+    assert r["sigma"] == pytest.approx(0.1)
+    # f exactly zero with zero error carries no information: no slope step stops it unconverged
+    r = P.newton_crossing(lambda x, it: (0.0, 0.0, 0.0, 0.0), 0.3, 0.0, 1.0)
+    assert not r["converged"] and r["iters"] == 1
