@@ -116,3 +116,23 @@ def test_grad_sums_argument_checks_before_device_work():
     p = _lib.RunParams()
     p.noise, p.chi, p.theta = 1, 8, 0.1
     assert lib.ttn_grad_sums(c.handle, ctypes.byref(p), 10, 0, 0.0, None, None, None, None) == 1
+
+
+def test_header_is_plain_c():
+    """include/ttn.h compiles as C99 (pedantic) and as C++17: the ABI has no
+    C++ types or constructs."""
+    import shutil
+    import subprocess
+    import tempfile
+    src = ('#include "ttn.h"\nint main(void) { ttn_crossing_eval f = 0; (void)f;\n'
+           '  return TTN_MIXED_MAX_ITEMS > 0 ? 0 : 1; }\n')
+    for cc, std, lang in (("gcc", "-std=c99", "c"), ("g++", "-std=c++17", "c++")):
+        if not shutil.which(cc):
+            pytest.skip("%s not available" % cc)
+        with tempfile.NamedTemporaryFile("w", suffix=".c", delete=False) as f:
+            f.write(src)
+        r = subprocess.run([cc, std, "-Wall", "-Wextra", "-pedantic", "-Werror", "-fsyntax-only",
+                            "-I", os.path.join(ROOT, "include"), "-x", lang, f.name],
+                           capture_output=True, text=True)
+        os.unlink(f.name)
+        assert r.returncode == 0, r.stderr
