@@ -57,8 +57,21 @@ typedef enum { TTN_PREC_FP64 = 0, TTN_PREC_FP32 = 1 } ttn_precision;
 
 /* Qubit -> TTN leaf assignment (App. B).  DEFAULT: qubit i on leaf i.
  * OPTIMIZED: recursive spectral bisection of the gate-similarity graph
- * (Eq. 9).  EXPLICIT: the caller's leaf_of_qubit array. */
-typedef enum { TTN_LAYOUT_DEFAULT = 0, TTN_LAYOUT_OPTIMIZED = 1, TTN_LAYOUT_EXPLICIT = 2 } ttn_layout;
+ * (Eq. 9).  EXPLICIT: the caller's leaf_of_qubit array.  SEARCH: OPTIMIZED
+ * and TTN_LAYOUT_SEARCH_CANDIDATES - 1 clusterings of perturbed
+ * similarities (off-diagonal entries scaled by seeded factors in
+ * [0.95, 1.05]); the one with the smallest noise-free bond dimension
+ * (ttn_layout_noise_free_chi) is kept, the earlier on ties (App. B samples
+ * candidates and keeps the smallest chi_exact; this cost needs no
+ * simulation of the noisy circuit).  Costs under a second of host time at
+ * d = 7, C = 7. */
+typedef enum {
+  TTN_LAYOUT_DEFAULT = 0,
+  TTN_LAYOUT_OPTIMIZED = 1,
+  TTN_LAYOUT_EXPLICIT = 2,
+  TTN_LAYOUT_SEARCH = 3
+} ttn_layout;
+#define TTN_LAYOUT_SEARCH_CANDIDATES 16
 
 typedef struct {
   int32_t distance;              /* code distance d: odd, 3..11          */
@@ -123,6 +136,15 @@ ttn_status ttn_circuit_info(const ttn_circuit* circuit, int32_t* n_qubits, int32
  * MEAS_X 4, NOISE 5), a (qubit / control), b (target / location id), event id
  * (-1 if none), record bit (-1 if none), layer.  ops: host [n_ops][6]. */
 ttn_status ttn_circuit_ops(const ttn_circuit* circuit, int32_t* ops);
+
+/* Bond dimension the noise-free circuit needs on a layout (host only, no
+ * GPU): the largest Schmidt rank across any tree bond after any layer,
+ * from a stabilizer tableau of the circuit without its noise operations
+ * (the noise-free limit of chi_exact, App. B, Table III).  leaf_of_qubit:
+ * host [n_qubits] distinct leaves, or NULL for the circuit's own layout.
+ * chi: host scalar (INT64_MAX if above 2^61). */
+ttn_status ttn_layout_noise_free_chi(const ttn_circuit* circuit, const int32_t* leaf_of_qubit,
+                                     int64_t* chi);
 
 /* The qubit -> leaf map in use.  leaf_of_qubit: host [n_qubits]. */
 ttn_status ttn_circuit_layout(const ttn_circuit* circuit, int32_t* leaf_of_qubit);

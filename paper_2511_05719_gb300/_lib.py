@@ -9,7 +9,7 @@ _LIB = None
 
 NOISE = {"none": 0, "srx": 1, "ad": 2, "srx_pta": 3, "ad_pta": 4, "srx_ad": 5}
 PRECISION = {"fp64": 0, "fp32": 1}
-LAYOUT = {"default": 0, "optimized": 1, "explicit": 2}
+LAYOUT = {"default": 0, "optimized": 1, "explicit": 2, "search": 3}
 
 c_i32p = ctypes.POINTER(ctypes.c_int32)
 c_dblp = ctypes.POINTER(ctypes.c_double)
@@ -42,7 +42,7 @@ EXPORTS = ["ttn_build_circuit", "ttn_free_circuit", "ttn_circuit_info", "ttn_cir
            "ttn_debug_state", "ttn_philox_uniforms", "ttn_profile_begin", "ttn_profile_end",
            "ttn_grad", "ttn_decode_noalloc", "ttn_profile_class_ms", "ttn_profile_eig_phases",
            "ttn_run_mixed", "ttn_newton_crossing", "ttn_crossing", "ttn_threshold_fit", "ttn_grad_sums",
-           "ttn_slot_check",
+           "ttn_slot_check", "ttn_layout_noise_free_chi",
            "ttn_status_string",
            "ttn_last_error"]
 
@@ -84,6 +84,7 @@ def load_library():
                                       ctypes.c_double, ctypes.c_int32, c_dblp, c_dblp, c_dblp, c_i32p]
     lib.ttn_grad_sums.argtypes = [vp, ctypes.POINTER(RunParams), ctypes.c_uint64, ctypes.c_int32,
                                   ctypes.c_double, c_u64p, c_u64p, c_dblp, c_dblp]
+    lib.ttn_layout_noise_free_chi.argtypes = [vp, c_i32p, c_i64p]
     lib.ttn_slot_check.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, c_dblp, c_i32p, c_i32p, c_i64p]
     lib.ttn_logical_error_rate.argtypes = [vp, ctypes.POINTER(RunParams), ctypes.c_uint64, c_dblp,
                                            c_dblp, c_u64p]
@@ -162,6 +163,15 @@ class Circuit:
         out = np.zeros((self.n_ops, 6), dtype=np.int32)
         _check(load_library().ttn_circuit_ops(self._h, out.ctypes.data_as(c_i32p)))
         return out
+
+    def noise_free_chi(self, leaf_of_qubit=None):
+        """Bond dimension the noise-free circuit needs on a layout (this
+        circuit's own when leaf_of_qubit is None); host only."""
+        out = ctypes.c_int64()
+        lay = None if leaf_of_qubit is None else np.ascontiguousarray(leaf_of_qubit, dtype=np.int32)
+        _check(load_library().ttn_layout_noise_free_chi(
+            self._h, None if lay is None else lay.ctypes.data_as(c_i32p), ctypes.byref(out)))
+        return out.value
 
     def layout(self):
         out = np.zeros(self.n_qubits, dtype=np.int32)

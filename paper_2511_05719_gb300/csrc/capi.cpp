@@ -2,6 +2,7 @@
 // checking, circuit handles and marshalling; all simulation work runs in the
 // CUDA engine and decoder.
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -49,7 +50,7 @@ ttn_status ttn_build_circuit(const ttn_circuit_params* p, ttn_circuit** out) {
   if (p->distance < 3 || p->distance > 11 || p->distance % 2 == 0)
     return fail_with(TTN_EINVAL, "distance must be odd and in [3, 11]");
   if (p->rounds < 1 || p->rounds > 64) return fail_with(TTN_EINVAL, "rounds must be in [1, 64]");
-  if (p->layout < TTN_LAYOUT_DEFAULT || p->layout > TTN_LAYOUT_EXPLICIT)
+  if (p->layout < TTN_LAYOUT_DEFAULT || p->layout > TTN_LAYOUT_SEARCH)
     return fail_with(TTN_EINVAL, "unknown layout");
   ttn_circuit* c = new (std::nothrow) ttn_circuit();
   if (!c) return fail_with(TTN_ENOMEM, "host allocation failed");
@@ -69,6 +70,8 @@ ttn_status ttn_build_circuit(const ttn_circuit_params* p, ttn_circuit** out) {
     for (int q = 0; q < c->N; ++q) c->leaf_of_qubit[q] = q;
   } else if (p->layout == TTN_LAYOUT_OPTIMIZED) {
     c->leaf_of_qubit = optimized_layout(c->code, c->ops, c->N, c->L);
+  } else if (p->layout == TTN_LAYOUT_SEARCH) {
+    c->leaf_of_qubit = searched_layout(c->code, c->ops, c->N, c->L, TTN_LAYOUT_SEARCH_CANDIDATES);
   } else {
     if (!p->leaf_of_qubit) {
       delete c;
@@ -118,6 +121,23 @@ ttn_status ttn_circuit_ops(const ttn_circuit* c, int32_t* ops) {
     r[4] = o.rec;
     r[5] = o.layer;
   }
+  return TTN_OK;
+}
+
+ttn_status ttn_layout_noise_free_chi(const ttn_circuit* c, const int32_t* leaf_of_qubit, int64_t* chi) {
+  if (!c || !chi) return fail_with(TTN_EINVAL, "null argument");
+  std::vector<int> lay(c->leaf_of_qubit.begin(), c->leaf_of_qubit.end());
+  if (leaf_of_qubit) {
+    std::vector<int> seen(c->L, 0);
+    for (int q = 0; q < c->N; ++q) {
+      const int l = leaf_of_qubit[q];
+      if (l < 0 || l >= c->L || seen[l]) return fail_with(TTN_EINVAL, "leaf_of_qubit must hold distinct leaves in [0, 2^D)");
+      seen[l] = 1;
+      lay[q] = l;
+    }
+  }
+  const int bits = noise_free_bond_bits(c->ops, c->N, c->L, lay);
+  *chi = bits >= 62 ? INT64_MAX : ((int64_t)1 << bits);
   return TTN_OK;
 }
 

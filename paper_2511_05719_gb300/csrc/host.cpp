@@ -214,8 +214,7 @@ static void split_rec(const std::vector<int>& Q, int lo, int height, const std::
   split_rec(B, lo + half, height - 1, S, N, leaf_of);
 }
 
-std::vector<int> optimized_layout(const Code& code, const std::vector<Op>& ops, int N,
-                                  int n_leaves) {
+static std::vector<double> gate_similarity(const std::vector<Op>& ops, int N) {
   std::vector<double> shared((size_t)N * N, 0.0);
   std::vector<int> deg(N, 0);
   for (const Op& op : ops)
@@ -232,13 +231,180 @@ std::vector<int> optimized_layout(const Code& code, const std::vector<Op>& ops, 
         int dsum = deg[i] + deg[j];
         S[(size_t)i * N + j] = shared[(size_t)i * N + j] + (dsum > 0 ? 1.0 / dsum : 0.0);
       }
+  return S;
+}
+
+static std::vector<int> layout_from_similarity(const std::vector<double>& S, int N, int n_leaves) {
   int height = 0;
   while ((1 << height) < n_leaves) ++height;
   std::vector<int> Q(N), leaf_of(N, -1);
   std::iota(Q.begin(), Q.end(), 0);
   split_rec(Q, 0, height, S, N, leaf_of);
-  (void)code;
   return leaf_of;
+}
+
+std::vector<int> optimized_layout(const Code& code, const std::vector<Op>& ops, int N,
+                                  int n_leaves) {
+  (void)code;
+  return layout_from_similarity(gate_similarity(ops, N), N, n_leaves);
+}
+
+// ---------------------------------------------------------------- layout search
+// Noise-free bond dimension of a layout.  Without noise the extraction
+// circuit is Clifford with Z/X measurements, so its state is a stabilizer
+// state at every layer: N generators in binary symplectic form (x | z bit
+// rows; signs do not affect entanglement), updated per H (swap x_q, z_q),
+// CNOT c->t (x_t ^= x_c, z_c ^= z_t) and Z measurement (a generator with
+// x_q = 1 is multiplied into the others with x_q = 1 and replaced by Z_q;
+// none: deterministic, unchanged) after Aaronson and Gottesman (2004).
+// Across the bond above a tree node, A = the qubits of its subtree, the
+// entanglement is rank_GF2(generators restricted to A) - |A| bits (Fattal et
+// al., quant-ph/0406168) and the Schmidt rank 2^that.  PREP finds its qubit
+// in a Z eigenstate (initial or just measured): PREP_Z changes nothing,
+// PREP_X is H; MEAS_X is H then a Z measurement.
+namespace {
+struct Tableau {
+  int n, W;
+  std::vector<uint64_t> x, z;  // [n][W] bit rows
+  explicit Tableau(int n_) : n(n_), W((n_ + 63) / 64), x((size_t)n_ * W, 0), z((size_t)n_ * W, 0) {
+    for (int i = 0; i < n; ++i) z[(size_t)i * W + i / 64] |= 1ull << (i % 64);
+  }
+  bool bit(const std::vector<uint64_t>& m, int r, int q) const {
+    return (m[(size_t)r * W + q / 64] >> (q % 64)) & 1ull;
+  }
+  void h(int q) {
+    const uint64_t msk = 1ull << (q % 64);
+    for (int r = 0; r < n; ++r) {
+      uint64_t& xw = x[(size_t)r * W + q / 64];
+      uint64_t& zw = z[(size_t)r * W + q / 64];
+      const uint64_t d = (xw ^ zw) & msk;
+      xw ^= d;
+      zw ^= d;
+    }
+  }
+  void cnot(int c, int t) {
+    for (int r = 0; r < n; ++r) {
+      if (bit(x, r, c)) x[(size_t)r * W + t / 64] ^= 1ull << (t % 64);
+      if (bit(z, r, t)) z[(size_t)r * W + c / 64] ^= 1ull << (c % 64);
+    }
+  }
+  void measure_z(int q) {
+    int p = -1;
+    for (int r = 0; r < n; ++r) {
+      if (!bit(x, r, q)) continue;
+      if (p < 0) {
+        p = r;
+        continue;
+      }
+      for (int w = 0; w < W; ++w) {
+        x[(size_t)r * W + w] ^= x[(size_t)p * W + w];
+        z[(size_t)r * W + w] ^= z[(size_t)p * W + w];
+      }
+    }
+    if (p < 0) return;
+    for (int w = 0; w < W; ++w) x[(size_t)p * W + w] = z[(size_t)p * W + w] = 0;
+    z[(size_t)p * W + q / 64] |= 1ull << (q % 64);
+  }
+  // entanglement (bits) between the qubits in A and the rest
+  int entropy(const std::vector<int>& A) const {
+    const int a = (int)A.size();
+    if (a == 0 || a == n) return 0;
+    const int cols = 2 * a, CW = (cols + 63) / 64;
+    std::vector<uint64_t> M((size_t)n * CW, 0);
+    for (int r = 0; r < n; ++r)
+      for (int j = 0; j < a; ++j) {
+        if (bit(x, r, A[j])) M[(size_t)r * CW + j / 64] |= 1ull << (j % 64);
+        if (bit(z, r, A[j])) M[(size_t)r * CW + (a + j) / 64] |= 1ull << ((a + j) % 64);
+      }
+    int rank = 0;
+    for (int c = 0; c < cols && rank < n; ++c) {
+      const uint64_t msk = 1ull << (c % 64);
+      int piv = -1;
+      for (int r = rank; r < n; ++r)
+        if (M[(size_t)r * CW + c / 64] & msk) {
+          piv = r;
+          break;
+        }
+      if (piv < 0) continue;
+      if (piv != rank)
+        for (int w = 0; w < CW; ++w) std::swap(M[(size_t)piv * CW + w], M[(size_t)rank * CW + w]);
+      for (int r = rank + 1; r < n; ++r)
+        if (M[(size_t)r * CW + c / 64] & msk)
+          for (int w = 0; w < CW; ++w) M[(size_t)r * CW + w] ^= M[(size_t)rank * CW + w];
+      ++rank;
+    }
+    return rank - a;
+  }
+};
+
+uint64_t splitmix64(uint64_t v) {
+  v += 0x9E3779B97F4A7C15ull;
+  v = (v ^ (v >> 30)) * 0xBF58476D1CE4E5B9ull;
+  v = (v ^ (v >> 27)) * 0x94D049BB133111EBull;
+  return v ^ (v >> 31);
+}
+}  // namespace
+
+int noise_free_bond_bits(const std::vector<Op>& ops, int N, int n_leaves, const std::vector<int>& leaf_of) {
+  const int L = n_leaves;
+  std::vector<std::vector<int>> under(2 * L);
+  for (int q = 0; q < N; ++q)
+    for (int x = L + leaf_of[q]; x >= 1; x /= 2) under[x].push_back(q);
+  Tableau t(N);
+  int cur = ops.empty() ? 0 : ops[0].layer, worst = 0;
+  auto snap = [&]() {
+    for (int v = 2; v < L; ++v) worst = std::max(worst, t.entropy(under[v]));
+  };
+  for (const Op& op : ops) {
+    if (op.layer != cur) {
+      snap();
+      cur = op.layer;
+    }
+    switch (op.kind) {
+      case PREP_X: t.h(op.a); break;
+      case CNOT: t.cnot(op.a, op.b); break;
+      case MEAS_Z: t.measure_z(op.a); break;
+      case MEAS_X:
+        t.h(op.a);
+        t.measure_z(op.a);
+        break;
+      default: break;  // PREP_Z, NOISE: no change of entanglement
+    }
+  }
+  snap();
+  return worst;
+}
+
+// Candidate layouts from the clustering (App. B: the clustering is a
+// heuristic, so candidates are sampled and the best is kept): candidate 0 is
+// optimized_layout, candidate c > 0 splits a similarity whose off-diagonal
+// entries are scaled by independent factors in [0.95, 1.05] (seeded by c),
+// which moves the Fiedler cuts where they are close.  The kept candidate has
+// the smallest noise-free bond dimension (a cost evaluated without
+// simulating the noisy circuit); ties keep the earlier candidate.
+std::vector<int> searched_layout(const Code& code, const std::vector<Op>& ops, int N, int n_leaves,
+                                 int candidates) {
+  (void)code;
+  const std::vector<double> S = gate_similarity(ops, N);
+  std::vector<int> best = layout_from_similarity(S, N, n_leaves);
+  int best_bits = noise_free_bond_bits(ops, N, n_leaves, best);
+  std::vector<double> Sc(S.size());
+  for (int c = 1; c < candidates; ++c) {
+    for (int i = 0; i < N; ++i)
+      for (int j = i + 1; j < N; ++j) {
+        const uint64_t h = splitmix64(((uint64_t)c << 40) ^ ((uint64_t)i << 20) ^ (uint64_t)j);
+        const double f = 1.0 + 0.1 * ((double)(h >> 11) * (1.0 / 9007199254740992.0) - 0.5);
+        Sc[(size_t)i * N + j] = Sc[(size_t)j * N + i] = S[(size_t)i * N + j] * f;
+      }
+    for (int i = 0; i < N; ++i) Sc[(size_t)i * N + i] = 0.0;
+    std::vector<int> lay = layout_from_similarity(Sc, N, n_leaves);
+    const int bits = noise_free_bond_bits(ops, N, n_leaves, lay);
+    if (bits < best_bits) {
+      best_bits = bits;
+      best.swap(lay);
+    }
+  }
+  return best;
 }
 
 // ---------------------------------------------------------------- step program

@@ -33,6 +33,13 @@ std::vector<Op> build_ops(const Code& code, int rounds, int* n_layers, int* n_ev
                           int* n_locations);
 std::vector<int> optimized_layout(const Code& code, const std::vector<Op>& ops, int n_qubits,
                                   int n_leaves);
+// optimized_layout post-selected among `candidates` perturbed clusterings by
+// the noise-free bond dimension; noise_free_bond_bits = log2 of that
+// dimension for a layout (stabilizer tableau, host only).
+std::vector<int> searched_layout(const Code& code, const std::vector<Op>& ops, int n_qubits,
+                                 int n_leaves, int candidates);
+int noise_free_bond_bits(const std::vector<Op>& ops, int n_qubits, int n_leaves,
+                         const std::vector<int>& leaf_of_qubit);
 
 // ---------------------------------------------------------------- device program
 // One step of the per-trajectory program; every trajectory of a batch runs
