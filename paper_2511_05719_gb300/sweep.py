@@ -25,6 +25,7 @@ def parse(argv):
                     help="comma-separated theta (srx models) or gamma (ad models) values")
     ap.add_argument("--theta", type=float, default=0.0, help="fixed theta for srx_ad gamma sweeps")
     ap.add_argument("--chi", type=int, default=64)
+    ap.add_argument("--layout", default="optimized", choices=["default", "optimized", "search"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--shots", type=int, default=10000)
     ap.add_argument("--batch", type=int, default=4096)
@@ -55,7 +56,7 @@ def main(argv=None, run=None, circuit=None, fit=None, out=sys.stdout):
     pts = []
     for d in a.distances:
         C = d if a.rounds == "d" else int(a.rounds)
-        circ = circuit(d, C)
+        circ = circuit(d, C, layout=a.layout)
         for x in a.strengths:
             kw = dict(noise=a.noise, chi=a.chi, precision=a.precision, seed=a.seed)
             if wrt == "gamma":

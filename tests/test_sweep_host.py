@@ -18,8 +18,8 @@ def model_p(d, x):
 
 
 class C:
-    def __init__(self, d, r):
-        self.distance, self.rounds = d, r
+    def __init__(self, d, r, layout="optimized"):
+        self.distance, self.rounds, self.layout = d, r, layout
 
 
 class Runner:
