@@ -375,11 +375,163 @@ int noise_free_bond_bits(const std::vector<Op>& ops, int N, int n_leaves, const 
   return worst;
 }
 
+// Algorithm 1 (App. B) as a seeded candidate generator.  At each tree level
+// the unassigned qubits are clustered into k = 2, 3, ... groups by spectral
+// clustering (rows of the k lowest Laplacian eigenvectors of the Eq. 9
+// similarity, normalised, then k-means from a seeded k-means++ start); the
+// clusters are merged into two groups by size, largest first into the
+// smaller group (reading of the balanced agglomeration the algorithm names);
+// the first k whose two groups fit the two subtrees is taken, else a seeded
+// random even split; each group then fills one subtree.
+namespace {
+struct Rng {
+  uint64_t s;
+  double uniform() {
+    s = splitmix64(s);
+    return (double)(s >> 11) * (1.0 / 9007199254740992.0);
+  }
+};
+
+std::vector<int> kmeans_labels(const std::vector<double>& X, int m, int dim, int k, Rng& rng) {
+  std::vector<double> cen((size_t)k * dim);
+  std::vector<double> dist(m, 0.0);
+  // k-means++ start
+  int first = std::min(m - 1, (int)(rng.uniform() * m));
+  for (int t = 0; t < dim; ++t) cen[t] = X[(size_t)first * dim + t];
+  for (int c = 1; c < k; ++c) {
+    double tot = 0.0;
+    for (int i = 0; i < m; ++i) {
+      double best = 1e300;
+      for (int cc = 0; cc < c; ++cc) {
+        double d2 = 0.0;
+        for (int t = 0; t < dim; ++t) {
+          const double e = X[(size_t)i * dim + t] - cen[(size_t)cc * dim + t];
+          d2 += e * e;
+        }
+        best = std::min(best, d2);
+      }
+      dist[i] = best;
+      tot += best;
+    }
+    int pick = m - 1;
+    double u = rng.uniform() * tot, acc = 0.0;
+    for (int i = 0; i < m; ++i) {
+      acc += dist[i];
+      if (acc >= u && dist[i] > 0.0) {
+        pick = i;
+        break;
+      }
+    }
+    for (int t = 0; t < dim; ++t) cen[(size_t)c * dim + t] = X[(size_t)pick * dim + t];
+  }
+  std::vector<int> lab(m, 0);
+  for (int it = 0; it < 100; ++it) {
+    bool changed = false;
+    for (int i = 0; i < m; ++i) {
+      int arg = 0;
+      double best = 1e300;
+      for (int c = 0; c < k; ++c) {
+        double d2 = 0.0;
+        for (int t = 0; t < dim; ++t) {
+          const double e = X[(size_t)i * dim + t] - cen[(size_t)c * dim + t];
+          d2 += e * e;
+        }
+        if (d2 < best) best = d2, arg = c;
+      }
+      if (lab[i] != arg) lab[i] = arg, changed = true;
+    }
+    std::vector<double> sum((size_t)k * dim, 0.0);
+    std::vector<int> cnt(k, 0);
+    for (int i = 0; i < m; ++i) {
+      cnt[lab[i]]++;
+      for (int t = 0; t < dim; ++t) sum[(size_t)lab[i] * dim + t] += X[(size_t)i * dim + t];
+    }
+    for (int c = 0; c < k; ++c)
+      if (cnt[c] > 0)
+        for (int t = 0; t < dim; ++t) cen[(size_t)c * dim + t] = sum[(size_t)c * dim + t] / cnt[c];
+    if (!changed && it > 0) break;
+  }
+  return lab;
+}
+
+void alg1_rec(const std::vector<int>& Q, int lo, int height, const std::vector<double>& S, int N, Rng& rng,
+              std::vector<int>& leaf_of) {
+  if (Q.empty()) return;
+  const int half = height > 0 ? 1 << (height - 1) : 0;
+  if (height == 0) {
+    leaf_of[Q[0]] = lo;
+    return;
+  }
+  if ((int)Q.size() <= 2) {
+    alg1_rec({Q[0]}, lo, height - 1, S, N, rng, leaf_of);
+    if (Q.size() == 2) alg1_rec({Q[1]}, lo + half, height - 1, S, N, rng, leaf_of);
+    return;
+  }
+  const int m = (int)Q.size();
+  std::vector<double> Lap((size_t)m * m, 0.0);
+  for (int i = 0; i < m; ++i)
+    for (int j = 0; j < m; ++j)
+      if (i != j) {
+        const double sv = S[(size_t)Q[i] * N + Q[j]];
+        Lap[(size_t)i * m + j] = -sv;
+        Lap[(size_t)i * m + i] += sv;
+      }
+  std::vector<double> w, V;
+  sym_eig(m, Lap, w, V);
+  std::vector<int> A, B;
+  for (int k = 2; k <= m && A.empty(); ++k) {
+    std::vector<double> X((size_t)m * k);
+    for (int i = 0; i < m; ++i) {
+      double nrm = 0.0;
+      for (int t = 0; t < k; ++t) nrm += V[(size_t)i * m + t] * V[(size_t)i * m + t];
+      nrm = nrm > 0.0 ? 1.0 / std::sqrt(nrm) : 1.0;
+      for (int t = 0; t < k; ++t) X[(size_t)i * k + t] = V[(size_t)i * m + t] * nrm;
+    }
+    std::vector<int> lab = kmeans_labels(X, m, k, k, rng);
+    std::vector<std::vector<int>> cl(k);
+    for (int i = 0; i < m; ++i) cl[lab[i]].push_back(Q[i]);
+    std::vector<int> order(k);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cl[a].size() > cl[b].size(); });
+    std::vector<int> g0, g1;
+    for (int c : order) {
+      std::vector<int>& g = g0.size() <= g1.size() ? g0 : g1;
+      g.insert(g.end(), cl[c].begin(), cl[c].end());
+    }
+    if ((int)g0.size() <= half && (int)g1.size() <= half && !g0.empty() && !g1.empty()) {
+      A.swap(g0);
+      B.swap(g1);
+    }
+    if (k >= 12) break;  // beyond a dozen clusters the merge is a balanced random split anyway
+  }
+  if (A.empty()) {  // random even split
+    std::vector<int> P(Q);
+    for (int i = m - 1; i > 0; --i) std::swap(P[i], P[(int)(rng.uniform() * (i + 1)) % (i + 1)]);
+    A.assign(P.begin(), P.begin() + m / 2);
+    B.assign(P.begin() + m / 2, P.end());
+  }
+  alg1_rec(A, lo, height - 1, S, N, rng, leaf_of);
+  alg1_rec(B, lo + half, height - 1, S, N, rng, leaf_of);
+}
+}  // namespace
+
+static std::vector<int> alg1_layout(const std::vector<double>& S, int N, int n_leaves, uint64_t seed) {
+  int height = 0;
+  while ((1 << height) < n_leaves) ++height;
+  std::vector<int> Q(N), leaf_of(N, -1);
+  std::iota(Q.begin(), Q.end(), 0);
+  Rng rng{seed};
+  alg1_rec(Q, 0, height, S, N, rng, leaf_of);
+  return leaf_of;
+}
+
 // Candidate layouts from the clustering (App. B: the clustering is a
 // heuristic, so candidates are sampled and the best is kept): candidate 0 is
-// optimized_layout, candidate c > 0 splits a similarity whose off-diagonal
-// entries are scaled by independent factors in [0.95, 1.05] (seeded by c),
-// which moves the Fiedler cuts where they are close.  The kept candidate has
+// optimized_layout; candidates 1 .. candidates/2 - 1 split a similarity
+// whose off-diagonal entries are scaled by independent factors in
+// [0.95, 1.05] (seeded by the candidate), which moves the Fiedler cuts
+// where they are close; the rest run Algorithm 1 with seeded k-means and
+// random splits.  The kept candidate has
 // the smallest noise-free bond dimension (a cost evaluated without
 // simulating the noisy circuit); ties keep the earlier candidate.
 std::vector<int> searched_layout(const Code& code, const std::vector<Op>& ops, int N, int n_leaves,
@@ -390,14 +542,19 @@ std::vector<int> searched_layout(const Code& code, const std::vector<Op>& ops, i
   int best_bits = noise_free_bond_bits(ops, N, n_leaves, best);
   std::vector<double> Sc(S.size());
   for (int c = 1; c < candidates; ++c) {
-    for (int i = 0; i < N; ++i)
-      for (int j = i + 1; j < N; ++j) {
-        const uint64_t h = splitmix64(((uint64_t)c << 40) ^ ((uint64_t)i << 20) ^ (uint64_t)j);
-        const double f = 1.0 + 0.1 * ((double)(h >> 11) * (1.0 / 9007199254740992.0) - 0.5);
-        Sc[(size_t)i * N + j] = Sc[(size_t)j * N + i] = S[(size_t)i * N + j] * f;
-      }
-    for (int i = 0; i < N; ++i) Sc[(size_t)i * N + i] = 0.0;
-    std::vector<int> lay = layout_from_similarity(Sc, N, n_leaves);
+    std::vector<int> lay;
+    if (c < candidates / 2) {
+      for (int i = 0; i < N; ++i)
+        for (int j = i + 1; j < N; ++j) {
+          const uint64_t h = splitmix64(((uint64_t)c << 40) ^ ((uint64_t)i << 20) ^ (uint64_t)j);
+          const double f = 1.0 + 0.1 * ((double)(h >> 11) * (1.0 / 9007199254740992.0) - 0.5);
+          Sc[(size_t)i * N + j] = Sc[(size_t)j * N + i] = S[(size_t)i * N + j] * f;
+        }
+      for (int i = 0; i < N; ++i) Sc[(size_t)i * N + i] = 0.0;
+      lay = layout_from_similarity(Sc, N, n_leaves);
+    } else {
+      lay = alg1_layout(S, N, n_leaves, 0x5EED0000ull + (uint64_t)c);
+    }
     const int bits = noise_free_bond_bits(ops, N, n_leaves, lay);
     if (bits < best_bits) {
       best_bits = bits;
