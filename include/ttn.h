@@ -57,13 +57,15 @@ typedef enum { TTN_PREC_FP64 = 0, TTN_PREC_FP32 = 1 } ttn_precision;
 
 /* Qubit -> TTN leaf assignment (App. B).  DEFAULT: qubit i on leaf i.
  * OPTIMIZED: recursive spectral bisection of the gate-similarity graph
- * (Eq. 9).  EXPLICIT: the caller's leaf_of_qubit array.  SEARCH: OPTIMIZED
- * and TTN_LAYOUT_SEARCH_CANDIDATES - 1 clusterings of perturbed
- * similarities (off-diagonal entries scaled by seeded factors in
- * [0.95, 1.05]); the one with the smallest noise-free bond dimension
- * (ttn_layout_noise_free_chi) is kept, the earlier on ties (App. B samples
- * candidates and keeps the smallest chi_exact; this cost needs no
- * simulation of the noisy circuit).  Costs under a second of host time at
+ * (Eq. 9).  EXPLICIT: the caller's leaf_of_qubit array.  SEARCH: among
+ * TTN_LAYOUT_SEARCH_CANDIDATES candidates -- OPTIMIZED, bisections of
+ * similarities with off-diagonal entries scaled by seeded factors in
+ * [0.95, 1.05], and seeded runs of Algorithm 1 (k-way spectral clustering
+ * merged into two groups, random even split as fallback) -- the one with the
+ * smallest noise-free bond dimension (ttn_layout_noise_free_chi) is kept,
+ * the earlier on ties (App. B samples candidates and keeps the smallest
+ * chi_exact; this cost needs no simulation of the noisy circuit, and under
+ * strong noise it ranks layouts less well).  Costs under a second of host time at
  * d = 7, C = 7. */
 typedef enum {
   TTN_LAYOUT_DEFAULT = 0,
