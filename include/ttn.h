@@ -292,8 +292,9 @@ ttn_status ttn_grad_sums(const ttn_circuit* circuit, const ttn_run_params* param
  * where rounding exceeds the exact rank; cap = the bond's structural cap
  * when the move truncates, twice that while a gate's operator index rides
  * on the bond) and every threading step doubling bonds as the kernels do,
- * and reports the largest node size / slot ratio seen (worst_fill; <= 1
- * means no trajectory, whatever its rounding, can overflow a slot), where
+ * and reports the largest ratio of need to capacity seen over the node
+ * slots and the per-trajectory workspaces each step uses (worst_fill; <= 1
+ * means no trajectory, whatever its rounding, can overflow either), where
  * (worst_node, worst_step; -1 = the initial state) and how many truncating
  * moves have a structural cap below both chi and n (binding_moves: moves
  * where a cap at chi alone would keep more).  Outputs other than worst_fill

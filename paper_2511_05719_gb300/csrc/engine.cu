@@ -2803,8 +2803,9 @@ size_t run_bytes_per_traj(const ttn_circuit& c, const RunRequest& rq) {
 // an FP32 Gram matrix turns the n - m zero eigenvalues of a wide M into
 // values near the kept-rank floor), threading doubles bonds as its kernels
 // do, and every node's element count is compared with its slot after each
-// step.  fill <= 1 means no trajectory can overflow a slot, whatever its
-// rounding.  binding counts truncating moves whose structural cap is below
+// step, as are the workspaces each step uses (W, the n x n blocks, the
+// n-entry arrays).  fill <= 1 means no trajectory can overflow a slot or a
+// workspace, whatever its rounding.  binding counts truncating moves whose structural cap is below
 // chi and below n: there a cap at chi alone would keep more.
 void slot_check(const ttn_circuit& c, int noise, int chi, double* worst_fill, int* worst_node,
                 int* worst_step, int64_t* binding) {
@@ -2821,6 +2822,12 @@ void slot_check(const ttn_circuit& c, int noise, int chi, double* worst_fill, in
     const double f = (double)size(v) / (double)eng.ncap[v];
     if (f > wf) wf = f, wn = v, ws = si;
   };
+  // the per-trajectory workspaces a move or a threading step uses: W holds
+  // the node or the m x n bond matrix, V / Rm / G an n x n block, sv and perm
+  // n entries
+  auto check_ws = [&](double f, int v, int si) {
+    if (f > wf) wf = f, wn = v, ws = si;
+  };
   for (int v = 1; v < L; ++v) check(v, -1);
   for (int si = 0; si < (int)prog.steps.size(); ++si) {
     const Step& s = prog.steps[si];
@@ -2829,16 +2836,20 @@ void slot_check(const ttn_circuit& c, int noise, int chi, double* worst_fill, in
       case S_THREAD_NODE:
         D[s.a] *= 2;
         check(s.a, si);
+        check_ws((double)size(s.a) / (double)eng.wstride, s.a, si);
         break;
       case S_THREAD_LCA:
         check(s.a, si);
+        check_ws((double)size(s.a) / (double)eng.wstride, s.a, si);
         break;
       case S_MOVE: {
         const int v = s.a, w = s.b;
         const int bond = (w == v / 2) ? v : w;
         const int64_t n = D[bond], m = size(v) / n;  // M is m x n
         const int64_t cap = s.c ? eng.bcap[bond] : 2 * (int64_t)eng.bcap[bond];
-        (void)m;
+        check_ws((double)(m * n) / (double)eng.wstride, v, si);
+        check_ws((double)n / (double)eng.nmax, v, si);
+        check_ws((double)(n * n) / (double)eng.vstride, v, si);
         if (s.c && eng.bcap[bond] < chi && n > eng.bcap[bond]) ++nb;
         D[bond] = std::min(n, cap);
         check(v, si);
