@@ -87,7 +87,14 @@ typedef struct {
   int32_t noise;                 /* ttn_noise                            */
   double theta;                  /* SRX angle of Eq. 1 (rad)             */
   double gamma;                  /* AD probability of Eq. 2              */
-  int32_t chi;                   /* bond-dimension cap, >= 1             */
+  int32_t chi;                   /* bond-dimension cap, 1..4096.  Inside a
+                                    gate a bond reaches 2 chi; in FP32 the
+                                    Gram-path eigensolver takes bonds up to
+                                    512, so a larger bond on that path (chi
+                                    above 256 on a circuit whose bonds grow
+                                    that far) stops the run with a capacity
+                                    error (ECUDA); svd_mode 1 has no such
+                                    limit                                 */
   int32_t precision;             /* ttn_precision                        */
   uint64_t seed;                 /* Philox key                           */
   uint64_t first_traj;           /* index of the first trajectory        */
