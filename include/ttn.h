@@ -316,23 +316,40 @@ ttn_status ttn_slot_check(const ttn_circuit* circuit, int32_t noise, int32_t chi
 ttn_status ttn_decode(const ttn_circuit* circuit, uint64_t n, const uint8_t* records,
                       uint8_t* fail, int32_t* color, int64_t* score, void* cuda_stream);
 
+/* Exact Gram matrix G = M^H M of one complex64 matrix on the tensor cores:
+ * the kernel of the isometry-centre factorisation (Sec. III.B: the centre
+ * moves by the Schmidt decomposition of a bond matrix; the device path takes
+ * it from G's FP64 eigendecomposition).  M: DEVICE m x n row-major complex64
+ * (interleaved re, im floats), 8-byte aligned; G: DEVICE n x n row-major
+ * complex128, 16-byte aligned, written.  G is exact, up to one final
+ * rounding to double, for M with every column rounded to 23 bits below its
+ * largest entry (entry error <= 2^-24 max|M_column|).  1 <= n <= 1024,
+ * 1 <= m <= 65536 (EINVAL otherwise).  The call allocates and frees its own
+ * scratch and synchronises cuda_stream (NULL = default stream); ETIMEOUT if
+ * a bounded wait of the tensor-core kernel expires. */
+ttn_status ttn_gram_exact(const void* M, int64_t m, int32_t n, void* G, void* cuda_stream);
+
 /* Allocation-free variant of ttn_decode.  The paper has no counterpart: it
  * serves callers that cannot allocate device memory -- an application whose
- * memory pool or caching allocator already owns the GPU, a framework whose
- * allocator hooks forbid direct driver allocations, or code that must avoid
- * the device-wide synchronisation cudaMalloc / cudaFree may imply.  It calls
- * no cudaMalloc, cudaFree or other allocating routine: the decoder tables and
- * per-shot scratch live in static device arrays of about 2 MB that every GPU
- * loading the library holds until exit.  records [n][n_record_bits], fail
- * [n], color [n], score [n] are always DEVICE pointers, ordered on
- * cuda_stream (NULL = the default stream; color/score may be NULL); the call
- * synchronises that stream before returning.  Results equal ttn_decode's.
- * Limits: (rounds + 1) * #faces + 1 <= 145 detector nodes (EINVAL beyond
- * that, e.g. d = 7 with more than 7 rounds); any number of shots.  The first
- * call on a device resolves the static arrays' device addresses: make it
- * before any stream capture.  The first call with a circuit packs its decoder
- * tables into host memory kept with the circuit.  All calls share the static
- * arrays, so calls that overlap on the GPU race; order them on one stream. */
+ * memory pool or caching allocator already owns the GPU, or a framework whose
+ * allocator hooks forbid direct driver allocations.  It calls no cudaMalloc,
+ * cudaFree or other allocating routine: the decoder tables and per-shot
+ * scratch live in static device arrays of about 2 MB that every GPU loading
+ * the library holds until exit.  records [n][n_record_bits], fail [n], color
+ * [n], score [n] are always DEVICE pointers of the current device, ordered on
+ * cuda_stream (NULL = the default stream; color/score may be NULL).  Every
+ * call copies the packed tables from host memory, decodes NA_SHOTS = 8 shots
+ * per launch (one thread per shot, so its throughput is far below
+ * ttn_decode's), reads two overflow counters back and synchronises
+ * cuda_stream before returning.  Results equal ttn_decode's.  Limits:
+ * (rounds + 1) * #faces + 1 <= 145 detector nodes (EINVAL beyond that, e.g.
+ * d = 7 with more than 7 rounds); any number of shots.  Every call resolves
+ * the static arrays' device addresses on the current device (no allocation;
+ * a device reset between calls is safe); the first call on a device may load
+ * the module's device code, so make it before any stream capture.  The first
+ * call with a circuit packs its decoder tables into host memory kept with the
+ * circuit.  All calls share the static arrays, so calls that overlap on the
+ * GPU race; order them on one stream. */
 ttn_status ttn_decode_noalloc(const ttn_circuit* circuit, uint64_t n, const uint8_t* records,
                               uint8_t* fail, int32_t* color, int64_t* score, void* cuda_stream);
 
@@ -369,6 +386,13 @@ ttn_status ttn_profile_class_ms(double* class_ms);
  * reduction, phases/split, bisection, eigenvectors (inverse iteration and
  * Gram-Schmidt), Rayleigh-Ritz, back-transformation.  Host [6]. */
 ttn_status ttn_profile_eig_phases(double* cycles);
+/* Centre-move shapes of the current (or last) profile, summed over
+ * trajectories: hist[(t * 513 + n) * 3 + f] for t = 1 on truncating moves
+ * (0 otherwise), n = bond dimension before the move (clamped to 512) and
+ * f = 0 number of moves, 1 sum of m (rows of the m x n bond matrix), 2 sum of
+ * the kept rank.  Host [2 * 513 * 3].  Profiling only; no Sec. of the paper
+ * defines it. */
+ttn_status ttn_profile_move_hist(double* hist);
 
 const char* ttn_status_string(ttn_status status);
 const char* ttn_last_error(void);

@@ -41,6 +41,7 @@ EXPORTS = ["ttn_build_circuit", "ttn_free_circuit", "ttn_circuit_info", "ttn_cir
            "ttn_circuit_layout", "ttn_run_trajectories", "ttn_logical_error_rate", "ttn_decode",
            "ttn_debug_state", "ttn_philox_uniforms", "ttn_profile_begin", "ttn_profile_end",
            "ttn_grad", "ttn_decode_noalloc", "ttn_profile_class_ms", "ttn_profile_eig_phases",
+           "ttn_profile_move_hist", "ttn_gram_exact",
            "ttn_run_mixed", "ttn_newton_crossing", "ttn_crossing", "ttn_threshold_fit", "ttn_grad_sums",
            "ttn_slot_check", "ttn_layout_noise_free_chi",
            "ttn_status_string",
@@ -90,6 +91,7 @@ def load_library():
                                            c_dblp, c_u64p]
     lib.ttn_decode.argtypes = [vp, ctypes.c_uint64, vp, vp, vp, vp, vp]
     lib.ttn_decode_noalloc.argtypes = [vp, ctypes.c_uint64, vp, vp, vp, vp, vp]
+    lib.ttn_gram_exact.argtypes = [vp, ctypes.c_int64, ctypes.c_int32, vp, vp]
     lib.ttn_debug_state.argtypes = [vp, ctypes.POINTER(RunParams), ctypes.c_uint64, ctypes.c_int32,
                                     c_dblp]
     lib.ttn_philox_uniforms.argtypes = [ctypes.c_uint64, c_u64p, ctypes.c_uint64, c_i32p,
@@ -368,6 +370,20 @@ def logical_error_rate(circuit, shots, noise="srx", theta=0.0, gamma=0.0, chi=16
     return pl.value, sg.value, nf.value
 
 
+def gram_exact(M, stream=None):
+    """ttn_gram_exact: the exact Gram matrix M^H M (complex128, n x n) of a
+    torch CUDA complex64 matrix M (m x n), on the tensor cores."""
+    import torch
+    if not isinstance(M, torch.Tensor) or not M.is_cuda or M.dtype != torch.complex64 or M.dim() != 2:
+        raise ValueError("gram_exact: M must be a 2-d complex64 CUDA tensor")
+    M = M.contiguous()
+    m, n = M.shape
+    G = torch.empty((n, n), dtype=torch.complex128, device=M.device)
+    st = ctypes.c_void_p(int(stream)) if stream else None
+    _check(load_library().ttn_gram_exact(_ptr(M), int(m), int(n), _ptr(G), st))
+    return G
+
+
 def decode(circuit, records):
     """Decodes host records [n][n_record_bits] -> (fail u8, colour i32, score i64)."""
     lib = load_library()
@@ -425,7 +441,10 @@ def profile_end():
     _check(lib.ttn_profile_class_ms(cm))
     ep = (ctypes.c_double * 6)()
     _check(lib.ttn_profile_eig_phases(ep))
-    return dict(timed_ms=ms.value, timed_launches=nl.value,
+    mh = (ctypes.c_double * (2 * 513 * 3))()
+    _check(lib.ttn_profile_move_hist(mh))
+    hist = np.array(list(mh)).reshape(2, 513, 3)
+    return dict(timed_ms=ms.value, timed_launches=nl.value, move_hist=hist,
                 flops=dict(zip(KERNEL_CLASSES, list(fl))), bytes=dict(zip(KERNEL_CLASSES, list(by))),
                 launches=dict(zip(KERNEL_CLASSES, list(la))), class_ms=dict(zip(KERNEL_CLASSES, list(cm))),
                 eig_phase_cycles=dict(zip(EIG_PHASES, list(ep))))
@@ -497,11 +516,37 @@ def logical_error_rate_fn(circuit, shots, **kw):
 
 def decode_noalloc(circuit, records, fail, color=None, score=None, stream=None):
     """Allocation-free decoding of records already on the device (torch CUDA
-    tensors: records uint8 [n][n_record_bits], fail uint8 [n], color int32 [n],
-    score int64 [n]).  The library decodes with static device scratch and
-    calls no cudaMalloc, for callers whose memory pool owns the device.
-    `stream` is a CUDA stream handle (int); 0 or None = the default stream."""
+    tensors on the current device: records uint8 [n][n_record_bits], fail
+    uint8 [n], color int32 [n], score int64 [n]).  The library decodes with
+    static device scratch and calls no cudaMalloc, for callers whose memory
+    pool owns the device.  `stream` is a CUDA stream handle (int); 0 or None =
+    the default stream.  Every tensor is checked here (device, layout, dtype,
+    size) because the kernel reads and writes them as raw device memory."""
+    import torch
+    cur = torch.cuda.current_device() if torch.cuda.is_available() else None
+    n = None
+
+    def need(name, t, dtype, rows, cols=None):
+        if not isinstance(t, torch.Tensor) or not t.is_cuda or t.device.index != cur:
+            raise ValueError("decode_noalloc: %s must be a CUDA tensor on the current device" % name)
+        if not t.is_contiguous():
+            raise ValueError("decode_noalloc: %s must be contiguous" % name)
+        if t.dtype != dtype:
+            raise ValueError("decode_noalloc: %s must be %s, got %s" % (name, dtype, t.dtype))
+        if cols is not None and (t.dim() != 2 or t.shape[1] != cols):
+            raise ValueError("decode_noalloc: %s must have shape (n, %d)" % (name, cols))
+        if t.numel() < rows * (cols or 1):
+            raise ValueError("decode_noalloc: %s holds fewer than %d entries" % (name, rows * (cols or 1)))
+
+    if not isinstance(records, torch.Tensor) or records.dim() != 2:
+        raise ValueError("decode_noalloc: records must be a 2-d torch tensor (n, n_record_bits)")
     n = int(records.shape[0])
+    need("records", records, torch.uint8, n, circuit.n_record_bits)
+    need("fail", fail, torch.uint8, n)
+    if color is not None:
+        need("color", color, torch.int32, n)
+    if score is not None:
+        need("score", score, torch.int64, n)
     st = ctypes.c_void_p(int(stream)) if stream else None
     _check(load_library().ttn_decode_noalloc(circuit.handle, n, _ptr(records), _ptr(fail),
                                              _ptr(color), _ptr(score), st))

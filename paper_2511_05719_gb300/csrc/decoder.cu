@@ -744,22 +744,25 @@ ttn_status decode_device(const ttn_circuit& c, int nb, const uint8_t* d_records,
 // ------------------------------------------------------------------ allocation-free decoding
 // ttn_decode_noalloc serves callers that must not allocate device memory: an
 // application whose memory pool or caching allocator already owns the GPU
-// memory, a host framework whose allocator hooks forbid direct driver
-// allocations, or code that cannot afford the device-wide synchronisation
-// that cudaMalloc / cudaFree may imply.  It runs the same decoder kernel, but
-// its tables and per-shot scratch live in file-scope static device arrays
-// instead of cudaMalloc'ed buffers.  Every GPU that loads the library holds
-// these arrays (about 2 MB) until the process exits.  The first call on a
-// device resolves the arrays' device addresses (cudaGetSymbolAddress); make
-// that first call before any stream capture.  The first call with a given
-// circuit also packs its decoder tables into one host array kept with the
-// circuit.
+// memory, or a host framework whose allocator hooks forbid direct driver
+// allocations.  It runs the same decoder kernel, but its tables and per-shot
+// scratch live in file-scope static device arrays instead of cudaMalloc'ed
+// buffers.  Every GPU that loads the library holds these arrays (about 2 MB)
+// until the process exits.  Every call resolves the arrays' device addresses
+// on the current device (cudaGetSymbolAddress allocates nothing, and a
+// device reset between calls leaves no stale address); the first call on a
+// device may also load the module, so make it before any stream capture.
+// The first call with a given circuit packs its decoder tables into one host
+// array kept with the circuit.  Each call copies that array to the device,
+// decodes NA_SHOTS shots per launch (one thread per shot), reads back two
+// overflow counters and synchronises its stream.
 //
 // Limits: at most NA_NODES detector nodes ((rounds + 1) * #faces + 1 <= 145,
 // e.g. d = 7 with up to 7 rounds) and NA_TABLE_INTS packed table entries; any
-// number of shots, decoded NA_SHOTS at a time.  All calls share the arrays:
-// calls that overlap on the GPU (different streams or host threads without
-// ordering) race and corrupt each other's results.
+// number of shots, decoded NA_SHOTS at a time, so n shots take ceil(n / 8)
+// serial launches.  All calls share the arrays: calls that overlap on the GPU
+// (different streams or host threads without ordering) race and corrupt each
+// other's results.
 static constexpr int NA_SHOTS = 8;
 static constexpr int NA_NODES = 145;
 static constexpr int NA_TABLE_INTS = 80000;
@@ -816,40 +819,26 @@ DecoderBlob build_decoder_blob(const DecoderTables& t) {
   return b;
 }
 
-// Device addresses of the static arrays, resolved once per device.
+// Device addresses of the static arrays on the current device.  Resolved on
+// every call: cudaGetSymbolAddress allocates nothing, and caching the
+// addresses would leave them stale after a device reset.
 static std::mutex g_na_mutex;
-static unsigned char* g_na_scratch_ptr[64] = {nullptr};
-static int32_t* g_na_tables_ptr[64] = {nullptr};
 
-static ttn_status na_setup(int* dev_out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+static ttn_status na_setup(unsigned char** scratch, int32_t** tables) {
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_na_scratch);
   if (e != cudaSuccess) {
-    set_error(std::string("CUDA: cudaGetDevice: ") + cudaGetErrorString(e));
+    set_error(std::string("CUDA: cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e));
     return TTN_ECUDA;
   }
-  if (dev < 0 || dev >= 64) {
-    set_error("ttn_decode_noalloc: device index above 63");
-    return TTN_EUNSUPPORTED;
+  void* q = nullptr;
+  e = cudaGetSymbolAddress(&q, g_na_tables);
+  if (e != cudaSuccess) {
+    set_error(std::string("CUDA: cudaGetSymbolAddress(tables): ") + cudaGetErrorString(e));
+    return TTN_ECUDA;
   }
-  std::lock_guard<std::mutex> lock(g_na_mutex);
-  if (!g_na_scratch_ptr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_na_scratch);
-    if (e != cudaSuccess) {
-      set_error(std::string("CUDA: cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e));
-      return TTN_ECUDA;
-    }
-    void* q = nullptr;
-    e = cudaGetSymbolAddress(&q, g_na_tables);
-    if (e != cudaSuccess) {
-      set_error(std::string("CUDA: cudaGetSymbolAddress(tables): ") + cudaGetErrorString(e));
-      return TTN_ECUDA;
-    }
-    g_na_scratch_ptr[dev] = (unsigned char*)p;
-    g_na_tables_ptr[dev] = (int32_t*)q;
-  }
-  *dev_out = dev;
+  *scratch = (unsigned char*)p;
+  *tables = (int32_t*)q;
   return TTN_OK;
 }
 
@@ -874,12 +863,11 @@ ttn_status decode_noalloc(const ttn_circuit& c, uint64_t n, const uint8_t* d_rec
     set_error("ttn_decode_noalloc: decoder tables exceed the static table size");
     return TTN_EINVAL;
   }
-  int dev = 0;
-  ttn_status s = na_setup(&dev);
+  unsigned char* scratch = nullptr;
+  int32_t* tables = nullptr;
+  ttn_status s = na_setup(&scratch, &tables);
   if (s != TTN_OK) return s;
   cudaStream_t st = (cudaStream_t)stream;
-  unsigned char* scratch = g_na_scratch_ptr[dev];
-  int32_t* tables = g_na_tables_ptr[dev];
   cudaError_t e = cudaMemcpyAsync(tables, blob.data.data(), sizeof(int32_t) * blob.data.size(),
                                   cudaMemcpyHostToDevice, st);
   DecDev d{};
@@ -932,7 +920,7 @@ ttn_status decode_noalloc(const ttn_circuit& c, uint64_t n, const uint8_t* d_rec
   if (e == cudaSuccess) e = cudaMemsetAsync(d.overflow, 0, 2 * sizeof(int32_t), st);
   for (uint64_t s0 = 0; s0 < n && e == cudaSuccess; s0 += NA_SHOTS) {
     const int m = (int)std::min<uint64_t>(NA_SHOTS, n - s0);
-    k_decode<<<1, 64, 0, st>>>(d, m, d_records + s0 * c.n_rec, d_fail + s0,
+    k_decode<<<1, NA_SHOTS, 0, st>>>(d, m, d_records + s0 * c.n_rec, d_fail + s0,
                                d_color ? d_color + s0 : nullptr, d_score ? d_score + s0 : nullptr);
     e = cudaGetLastError();
   }

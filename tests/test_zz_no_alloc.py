@@ -44,3 +44,21 @@ def test_noalloc_rejects_circuits_beyond_its_static_scratch():
     with pytest.raises(P.TTNError) as ei:
         P.decode_noalloc(c, r, fail)
     assert "status 1" in str(ei.value) and "145" in str(ei.value)
+
+
+def test_noalloc_rejects_tensors_it_cannot_hand_to_the_device():
+    """Host tensors, wrong dtypes and short outputs are refused in the
+    wrapper, before any pointer reaches the kernel."""
+    import os
+    from paper_2511_05719_gb300 import _lib
+    if not os.path.exists(_lib.library_path()):
+        pytest.skip("libttn.so not built")
+    c = P.Circuit(3, 1)
+    r = torch.zeros((2, c.n_record_bits), dtype=torch.uint8)
+    fail = torch.zeros(2, dtype=torch.uint8)
+    with pytest.raises(ValueError):
+        P.decode_noalloc(c, r, fail)                       # CPU tensors
+    with pytest.raises(ValueError):
+        P.decode_noalloc(c, r.to(torch.int32), fail)       # wrong dtype (checked first on device)
+    with pytest.raises(ValueError):
+        P.decode_noalloc(c, torch.zeros((2, 3), dtype=torch.uint8), fail)  # wrong width
