@@ -821,6 +821,13 @@ ttn_status ttn_profile_eig_phases(double* cycles) {
   return TTN_OK;
 }
 
+ttn_status ttn_profile_move_hist(double* hist) {
+  if (!hist) return fail_with(TTN_EINVAL, "null argument");
+  const Profile& p = profile();
+  for (int i = 0; i < MOVE_HIST_WORDS; ++i) hist[i] = p.move_hist[i];
+  return TTN_OK;
+}
+
 ttn_status ttn_profile_class_ms(double* class_ms) {
   if (!class_ms) return fail_with(TTN_EINVAL, "null argument");
   const Profile& p = profile();

@@ -132,6 +132,7 @@ struct Dev {
   int32_t* err;          // [B] error flags
   int32_t* err_step;     // [B][2] step of the first fatal error, of the first non-convergence
   int cur_step;          // step of the program being launched
+  int cur_trunc;         // 1 if that step is a truncating move
 };
 
 enum : int32_t { ERR_ZERO_NORM = 1, ERR_NO_CONVERGE = 2, ERR_CAPACITY = 4, ERR_NAN = 8 };
@@ -151,7 +152,8 @@ static constexpr int TRI_NB = 8;       // reflectors per compact-WY block of the
 static constexpr int TRI_INV_ITERS = 2;  // inverse-iteration / orthonormalisation rounds
 // profiling ledger: flops and bytes per class, then SM cycles per phase of
 // the tridiagonal eigensolver (summed over trajectories, thread 0's clock)
-static constexpr int LEDGER_WORDS = 2 * NCLASS + EIG_PHASES;
+static constexpr int LEDGER_WORDS = 2 * NCLASS + EIG_PHASES + MOVE_HIST_WORDS;
+static constexpr int LEDGER_HIST = 2 * NCLASS + EIG_PHASES;  // first word of the move histogram
 // Moves whose tensor capacity reaches this many elements count as large, and
 // so does every move of a circuit above BIG_CIRCUIT_QUBITS qubits (d >= 5).
 static constexpr int64_t BIG_MOVE = (int64_t)1 << 17;
@@ -823,6 +825,14 @@ __device__ int eig_select(Dev<R>& d, int b, int v, int w, int kcap, int n, doubl
     }
     s_kk = k;
     const int bond = (w == v / 2) ? v : w;
+    if (d.ledger) {
+      const int64_t mm = (int64_t)D[2 * v] * D[2 * v + 1] * (v == 1 ? 1 : D[v]) / (n > 0 ? n : 1);
+      unsigned long long* h =
+          d.ledger + LEDGER_HIST + ((int64_t)(d.cur_trunc ? 1 : 0) * MOVE_HIST_N + min(n, MOVE_HIST_N - 1)) * 3;
+      atomicAdd(&h[0], 1ull);
+      atomicAdd(&h[1], (unsigned long long)mm);
+      atomicAdd(&h[2], (unsigned long long)k);
+    }
     D[bond] = k;
     d.knew[b] = k;
     d.nold[b] = n;
@@ -2333,6 +2343,7 @@ struct Engine {
         pf.bytes[c] += (double)h[2 * c + 1];
       }
       for (int ph = 0; ph < EIG_PHASES; ++ph) pf.eig_phase_cycles[ph] += (double)h[2 * NCLASS + ph];
+      for (int i = 0; i < MOVE_HIST_WORDS; ++i) pf.move_hist[i] += (double)h[LEDGER_HIST + i];
     }
     for (int c = 0; c < NCLASS; ++c) {
       pf.class_launches[c] += class_launches[c];
@@ -2476,6 +2487,7 @@ struct Engine {
     for (int si = 0; si < nsteps; ++si) {
       const Step& s = prog.steps[si];
       dev.cur_step = si;
+      dev.cur_trunc = s.kind == S_MOVE ? s.c : 0;
       switch (s.kind) {
         case S_MOVE: {
           const int v = s.a, w = s.b;

@@ -48,6 +48,12 @@ enum KernelClass { KC_SVD = 0, KC_GRAM = 1, KC_EIG = 2, KC_FORMU = 3, KC_ABSORB 
 // phases/split, bisection, eigenvectors (inverse iteration + Gram-Schmidt),
 // Rayleigh-Ritz, back-transformation.
 static constexpr int EIG_PHASES = 6;
+// Move-shape histogram of the profiling ledger: for every centre move
+// (truncating or not) and bond dimension n before the move (clamped to
+// MOVE_HIST_N - 1): number of moves, sum of m (rows of the bond matrix) and
+// sum of the kept rank k, summed over trajectories.
+static constexpr int MOVE_HIST_N = 513;
+static constexpr int MOVE_HIST_WORDS = 2 * MOVE_HIST_N * 3;
 
 // Process-wide profiling state: while active, every run adds algorithmic
 // flops/bytes per class to `ledger`, and launches of class `timed_class`
@@ -63,6 +69,7 @@ struct Profile {
   uint64_t class_launches[NCLASS] = {0};
   double class_ms[NCLASS] = {0};
   double eig_phase_cycles[EIG_PHASES] = {0};
+  double move_hist[MOVE_HIST_WORDS] = {0};
 };
 Profile& profile();
 
