@@ -1,19 +1,30 @@
 """Benchmark of the TTN trajectory simulator (one JSON line on rank 0).
 
-A step is one batch of trajectories of the whole hot path -- circuit on the
-tree tensor network, Born / Kraus sampling, decoding -- through the C ABI.
-Default workload: d = 7 color code, 7 rounds, SRX with theta swept over 8
-values in [0.01, 0.15] rad (trajectory i of a batch at theta_(i mod 8)),
-chi = 128, complex64 tensors.  Inputs are synthetic and seeded (the paper's
-workloads are themselves synthetic circuits).
+Workload: d = 7 color code, 7 rounds, SRX with theta swept over 8 values in
+[0.01, 0.15] rad (trajectory t at theta_(t mod 8)), chi = 128, MIXED
+precision (complex64 tensors, 3xTF32 contractions, FP64 isometry-centre
+factorisations, FP64 probabilities).  Inputs are synthetic and seeded (the
+paper's workloads are themselves synthetic circuits).
 
-value: trajectories/s with device-side outputs (CUDA events on the launch
-stream, max over ranks).  e2e: the same metric through the same call with
-host buffers (device -> host copies of records / fail bits / log-probs
-inside the timed region).  Trajectories are sharded across ranks by index
-(no collective on the data path: weak scaling).  Every launch works on the
-full per-trajectory arena (hundreds of MB per trajectory, far above L2), so
-no L2 flush is needed between steps.
+A step is one step of the pipelined resident batch (ttn_pipeline_*):
+`--resident` trajectories stay on the device in `--segments` groups; every
+step runs one program segment of every group (each group on its own stream)
+and completes exactly `resident / segments` whole trajectories -- circuit on
+the tree tensor network, Born / Kraus sampling, decoding.  All steps do the
+same work (one full trajectory per group), so every timed step is a
+steady-state step.  Creating the pipeline (filling it) is untimed.
+
+value: completed trajectories/s with device-side outputs (CUDA events on the
+caller's stream, max over ranks).  e2e: the same metric through the same
+call with host output buffers (fail byte, log-probability, discarded weight
+copied back every step).  Trajectories are sharded across ranks by index (no
+collective on the data path: weak scaling).  Every step streams hundreds of
+MB per trajectory, far above L2, so no L2 flush is needed between steps.
+
+--impl reference: the CPU oracle (plain numpy TTN, float64) on the host
+cores, on the same workload: a complete d = 7, one-round trajectory cut into
+`--steps` equal op-count steps, scaled to 7-round trajectories by the number
+of rounds.
 """
 import argparse
 import json
@@ -30,62 +41,47 @@ sys.path.insert(0, ROOT)
 
 import workloads as WL  # noqa: E402
 
-FP32_ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max clock
 METRIC = "d=7 trajectories/s (chi=128), batched vs plain at matched p_L; grad/fwd cost"
-TENSOR_CLASSES = ("gram", "form_u", "absorb")   # on the tensor cores in FP32 Gram-path moves
+FP64_PEAK_TFLOPS = 1.25   # nominal GB300 FP64 (152 SMs x 2 FP64 FMA/clk x 2 flops x ~2.06 GHz)
 
 
-def tensor_peak():
-    """Effective 3xTF32 complex-FP32 peak: the measured bf16 dense peak x the
-    nominal TF32/bf16 ratio (1.1 / 2.25 PFLOP/s), / 3 for the three TF32
-    passes each FP32 product takes.  Returns (TFLOP/s, source)."""
+def peaks():
+    """(bf16 sustained TFLOP/s, source) from MEASURED_PEAKS.json, else the fallback."""
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
         with open(path) as f:
             pk = json.load(f)
-        bf16, src = float(pk["bf16_tflops_sustained"]), "of measured (bf16 sustained)"
+        return float(pk["bf16_tflops_sustained"]), "of measured (bf16 sustained)"
     except (OSError, KeyError, ValueError):
-        bf16, src = 1700.0, "of fallback (bf16 sustained 1.7 PFLOP/s)"
-    return bf16 * (1.1 / 2.25) / 3.0, src + " x 1.1/2.25 (TF32) / 3 (3xTF32 passes)"
+        return 1700.0, "of fallback (bf16 sustained 1.7 PFLOP/s)"
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ttn", choices=["ttn", "reference"])
-    ap.add_argument("--batch", type=int, default=0,
-                    help="trajectories per step and rank (0: 64 for d >= 7, else 512)")
+    ap.add_argument("--resident", type=int, default=152, help="trajectories on the device per rank")
+    ap.add_argument("--segments", type=int, default=19, help="pipeline segments (resident must be a multiple)")
     ap.add_argument("--distance", type=int, default=7)
     ap.add_argument("--rounds", type=int, default=7)
     ap.add_argument("--chi", type=int, default=128)
-    ap.add_argument("--precision", default="fp32")
-    ap.add_argument("--roofline-class", default="auto")
-    ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--precision", default="mixed")
+    ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
 
 def workload_name(a):
-    return "d%d_C%d_srx_theta_sweep8_chi%d_%s" % (a.distance, a.rounds, a.chi, a.precision)
+    centre = "fp64centre" if a.precision in ("mixed", "fp64") else "fp32centre"
+    return "d%d_C%d_srx_theta_sweep8_chi%d_%s_%s" % (a.distance, a.rounds, a.chi, a.precision, centre)
 
 
-def default_batch(a):
-    # d >= 7: 64 trajectories per step.  The eigensolver runs one CTA per
-    # trajectory and is latency-bound, so a step's time grows slowly with the
-    # batch until every SM holds one (d=7, C=1: 12.0 s at 16, 24.1 s at 152,
-    # 47.3 s at 304 trajectories on 152 SMs).  64 keeps most of that gain
-    # while five default steps (3 warm-up, 1 timed, 1 end-to-end) of the
-    # 7-round circuit stay near a quarter of an hour; --batch 152 gives the
-    # highest throughput.
-    return a.batch if a.batch > 0 else (64 if a.distance >= 7 else 512)
-
-
-def run_config(a, B):
-    """The workload both arms report (the same keys and values)."""
-    return {"workload": workload_name(a), "trajectories_per_step": B, "rounds": a.rounds,
-            "distance": a.distance, "chi": a.chi,
+def run_config(a):
+    return {"workload": workload_name(a), "distance": a.distance, "rounds": a.rounds, "chi": a.chi,
+            "resident_trajectories": a.resident, "segments": a.segments,
+            "trajectories_per_step": a.resident // a.segments,
             "l2": "working set per step far above L2 (no flush)"}
 
 
@@ -141,53 +137,91 @@ class ClockSampler:
                 "samples": len(self.rows)}
 
 
-def cpu_baseline(a, seconds):
-    """The plain CPU TTN oracle (numpy, float64) on a bounded sample of the
-    same workload: one trajectory's ops in program order for about `seconds`,
-    extrapolated by op count to trajectories/s."""
+def oracle_c1_trajectory(a, n_chunks=1, warm_chunks=0):
+    """The CPU oracle (plain numpy TTN, float64, threaded BLAS) on one complete
+    one-round trajectory of the workload's code (the oracle's own layout,
+    App. B), timed in n_chunks equal op-count chunks after warm_chunks chunks
+    of an untimed trajectory.  Returns (chunk seconds, total ops, theta)."""
     from oracle.circuit import build_circuit
+    from oracle.layout import optimized_layout
     from oracle import ttn as TT
     from oracle.channels import SRX
-    import paper_2511_05719_gb300 as P  # only for the circuit's leaf layout
-    circ = build_circuit(a.distance, a.rounds)
-    layout = P.Circuit(a.distance, a.rounds, layout="optimized").layout()
-    thetas = WL.M3["thetas"]
-    total = len(circ.ops)
-    done = 0
-    # one trajectory in program order, stopped after about `seconds`
-    t1 = time.time()
-    r = TT.run_trajectory(circ, SRX, thetas[3], 0.0, WL.M3["seed"], 0, chi=a.chi,
-                          leaf_of_qubit=list(layout), deadline=t1 + seconds)
-    elapsed = time.time() - t1
-    done = r["ops_done"]
-    traj_s = (done / total) / elapsed if elapsed > 0 else 0.0
-    cores = os.cpu_count()
-    return {"value": traj_s, "unit": "trajectories/s", "cores": cores, "kind": "oracle",
-            "sample": "plain numpy TTN (float64, threaded BLAS) on the first %d of %d ops of one "
-                      "trajectory (theta=%.3f), %.1f s, extrapolated by op count"
-                      % (done, total, thetas[3], elapsed)}
+    circ = build_circuit(a.distance, 1)
+    lay = optimized_layout(circ)
+    theta = WL.M3["thetas"][3]
+    n_ops = len(circ.ops)
+    bounds = [round(n_ops * k / n_chunks) for k in range(n_chunks + 1)]
+    if warm_chunks > 0:
+        TT.run_trajectory(circ, SRX, theta, 0.0, WL.M3["seed"], 1, chi=a.chi, leaf_of_qubit=lay,
+                          max_ops=bounds[min(warm_chunks, n_chunks)])
+    stamps = {}
+    marks = set(bounds[1:])
+
+    def on_op(i):
+        if i + 1 in marks:
+            stamps[i + 1] = time.perf_counter()
+
+    t0 = time.perf_counter()
+    TT.run_trajectory(circ, SRX, theta, 0.0, WL.M3["seed"], 0, chi=a.chi, leaf_of_qubit=lay, on_op=on_op)
+    prev, chunks = t0, []
+    for b in bounds[1:]:
+        chunks.append(stamps[b] - prev)
+        prev = stamps[b]
+    return chunks, n_ops, theta
+
+
+def cpu_sample_text(a, n_ops, theta, secs):
+    return ("plain numpy TTN oracle (float64, threaded BLAS, oracle-side layout): one complete d=%d "
+            "one-round trajectory (%d ops, theta=%.3f, chi=%d) in %.1f s; a %d-round trajectory counted "
+            "as %d one-round ones (later rounds cost more, so this overstates the CPU rate)"
+            % (a.distance, n_ops, theta, a.chi, secs, a.rounds, a.rounds))
+
+
+def cpu_baseline(a):
+    chunks, n_ops, theta = oracle_c1_trajectory(a)
+    secs = sum(chunks)
+    return {"value": 1.0 / (a.rounds * secs), "unit": "trajectories/s", "cores": os.cpu_count(),
+            "kind": "oracle", "sample": cpu_sample_text(a, n_ops, theta, secs)}
 
 
 def run_reference(a):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    seconds = max(5.0, min(60.0, a.cpu_seconds))
-    vals = []
-    cb = None
-    for _ in range(max(1, a.steps)):
-        cb = cpu_baseline(a, seconds / max(1, a.steps))
-        vals.append(cb["value"])
-    v = float(np.mean(vals))
-    cb["value"] = v
-    line = {"impl": "reference", "metric": METRIC, "value": v,
-            "unit": "trajectories/s", "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
+    K = max(1, a.steps)
+    chunks, n_ops, theta = oracle_c1_trajectory(a, n_chunks=K, warm_chunks=a.warmup)
+    secs = sum(chunks)
+    v = 1.0 / (a.rounds * secs)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "trajectories/s",
+            "n_gpus": a.gpus, "steps": K, "warmup": a.warmup, "ms_per_step": 1e3 * secs / K,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
-            "data": "synthetic", "config": run_config(a, default_batch(a)),
-            "cpu_baseline": cb,
-            "e2e": {"value": v, "unit": "trajectories/s", "h2d_bytes_per_step": 0,
-                    "d2h_bytes_per_step": 0}}
+            "data": "synthetic", "config": run_config(a),
+            "cpu_baseline": {"value": v, "unit": "trajectories/s", "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": cpu_sample_text(a, n_ops, theta, secs) +
+                             "; %d steps of equal op count" % K},
+            "e2e": {"value": v, "unit": "trajectories/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
+
+
+def roofline(a, prof, cls):
+    fl = prof["flops"][cls]
+    ms = prof["class_ms"][cls]
+    achieved = fl / (ms / 1e3) / 1e12 if ms > 0 else 0.0
+    bf16, src = peaks()
+    if cls == "eig":
+        bound, peak, psrc = "alu", FP64_PEAK_TFLOPS, "FP64 nominal (MEASURED_PEAKS has no FP64 entry)"
+    elif cls == "gram":
+        bound, peak, psrc = "tensor", bf16, src + "; algorithmic complex Gram flops 8mn^2 (the kernel " \
+                                                  "executes 9 bf16 digit products of the real Gram)"
+    elif cls in ("form_u", "absorb"):
+        bound, peak = "tensor", bf16 * (1.1 / 2.25) / 3.0
+        psrc = src + " x 1.1/2.25 (TF32) / 3 (3xTF32 passes)"
+    else:
+        bound, peak, psrc = "alu", 152 * 128 * 2 * 2.070e9 / 1e12, "FP32 FMA: 152 SMs x 128 lanes x 2 x 2070 MHz"
+    return {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak if peak else 0.0, "traffic": None, "kernel_class": cls,
+            "launches": prof["launches"][cls], "kernel_ms": ms,
+            "per_launch_ms": ms / max(1, prof["launches"][cls]), "peak_source": psrc}
 
 
 def main():
@@ -205,47 +239,47 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    B = default_batch(a)
-    circ = P.Circuit(a.distance, a.rounds, layout="optimized")
-    thetas = WL.theta_sweep_per_traj(B, WL.M3["thetas"])
-    stream = torch.cuda.Stream()
+    if a.resident % a.segments:
+        raise SystemExit("--resident must be a multiple of --segments")
     dev = torch.device("cuda", local)
-    out = dict(records=torch.empty((B, circ.n_record_bits), dtype=torch.uint8, device=dev),
-               fail=torch.empty(B, dtype=torch.uint8, device=dev),
-               log_prob=torch.empty(B, dtype=torch.float64, device=dev),
-               discarded=torch.empty(B, dtype=torch.float64, device=dev))
+    stream = torch.cuda.Stream()
+    circ = P.Circuit(a.distance, a.rounds, layout="optimized")
     seed = WL.M3["seed"]
-    step_id = [0]
-
-    def step(device_out=True):
-        first = (rank * 1_000_000 + step_id[0]) * B
-        step_id[0] += 1
-        kw = dict(noise="srx", theta=0.0, chi=a.chi, precision=a.precision, seed=seed,
-                  first_traj=first, theta_per_traj=thetas)
-        try:
-            if device_out:
-                P.run_trajectories(circ, B, out=out, stream=stream.cuda_stream, **kw)
-                return None
-            return P.run_trajectories(circ, B, **kw)
-        except P.TTNError as e:
-            if e.status == 6:      # decoder bound exceeded on some shots: counted, not fatal
-                return None
-            raise
-
-    for _ in range(a.warmup):
-        step()
+    t_fill = time.perf_counter()
+    pipe = P.Pipeline(circ, a.resident, a.segments, noise="srx", theta=0.0, chi=a.chi, precision=a.precision,
+                      seed=seed, first_traj=rank << 40, theta_cycle=WL.M3["thetas"], stream=stream.cuda_stream)
     torch.cuda.synchronize()
+    fill_s = time.perf_counter() - t_fill
+    G = pipe.group_size
+    K, W = a.steps, a.warmup
+    fails = torch.zeros(K * G, dtype=torch.uint8, device=dev)
+    logp = torch.zeros(K * G, dtype=torch.float64, device=dev)
+    disc = torch.zeros(K * G, dtype=torch.float64, device=dev)
+    trajs = []
+    # warm-up steps, profiled per kernel class: the dominant class
+    P.profile_begin("all")
+    wout = dict(fail=torch.zeros(G, dtype=torch.uint8, device=dev),
+                log_prob=torch.zeros(G, dtype=torch.float64, device=dev))
+    for _ in range(W):
+        pipe.step(wout, stream=stream.cuda_stream)
+    torch.cuda.synchronize()
+    wprof = P.profile_end()
+    cms = wprof["class_ms"]
+    dom = max(cms, key=lambda c: cms[c]) if W > 0 else "eig"
+    # timed steps: device outputs; only the dominant class's launches carry events
     clocks = ClockSampler(local)
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     clocks.start()
-    P.profile_begin("all")   # device time of every launch, per kernel class (CUDA events)
+    P.profile_begin(dom)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for _ in range(a.steps):
-        step()
+    for k in range(K):
+        sl = slice(k * G, (k + 1) * G)
+        r = pipe.step(dict(fail=fails[sl], log_prob=logp[sl], discarded=disc[sl]), stream=stream.cuda_stream)
+        trajs.append(r["traj"])
     e1.record(stream)
     torch.cuda.synchronize()
     prof = P.profile_end()
@@ -256,52 +290,49 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         dist.barrier()
         ms = float(t.item())
-    traj = world * a.steps * B
-    value = traj / (ms / 1e3)
-    lost = int((out["fail"] == 3).sum().item())   # of the last timed step (fail byte 3)
-    # end to end: host buffers through the same call (one step)
+    value = world * K * G / (ms / 1e3)
+    # end to end: host output buffers through the same call
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    step(device_out=False)
+    for _ in range(max(1, a.e2e_steps)):
+        pipe.step()
     e2e_s = time.perf_counter() - t0
-    # bytes the call copies per step: theta, gamma and trajectory index in
-    # (8 B each per trajectory); records, fail byte, log-probability,
-    # discarded weight, near-tie count, error word and two error-step words out
-    e2e = {"value": world * B / e2e_s, "unit": "trajectories/s",
-           "h2d_bytes_per_step": 24 * B,
-           "d2h_bytes_per_step": B * (circ.n_record_bits + 1 + 8 + 8 + 4 + 4 + 8)}
-    # roofline of the dominant kernel class (most device time in the timed region)
-    cms = prof["class_ms"]
-    rclass = a.roofline_class if a.roofline_class != "auto" else max(cms, key=lambda c: cms[c])
-    fl = prof["flops"][rclass]
-    by = prof["bytes"][rclass]
-    tms = cms[rclass]
-    achieved = fl / (tms / 1e3) / 1e12 if tms > 0 else 0.0
-    roof = {"bound": "alu", "achieved": achieved, "peak": FP32_ALU_PEAK_TFLOPS,
-            "unit": "TFLOP/s", "frac": achieved / FP32_ALU_PEAK_TFLOPS if achieved else 0.0,
-            "traffic": None, "kernel_class": rclass, "launches": prof["launches"][rclass],
-            "kernel_ms": tms, "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 x 2070 MHz"}
-    if a.precision == "fp32" and rclass in TENSOR_CLASSES:
-        pk, src = tensor_peak()
-        roof.update(bound="tensor", peak=pk, frac=achieved / pk if achieved else 0.0, peak_source=src)
-    if a.precision == "fp64":
-        roof["peak"] = 1.25
-        roof["frac"] = achieved / 1.25 if achieved else 0.0
-        roof["peak_source"] = "FP64 nominal 1.25 TFLOP/s"
+    pipe.close()
+    ne = max(1, a.e2e_steps)
+    e2e = {"value": world * ne * G / e2e_s, "unit": "trajectories/s",
+           # theta, gamma and trajectory index of the restarting group in; fail
+           # byte, log-probability, discarded weight of the completing group
+           # and every resident trajectory's error word out
+           "h2d_bytes_per_step": 24 * G,
+           "d2h_bytes_per_step": 17 * G + 4 * a.resident}
     if rank != 0:
+        if dist:
+            dist.destroy_process_group()
         return
+    # p_L per theta over the timed trajectories
+    f = fails.cpu().numpy()
+    tr = np.concatenate(trajs)
+    th = np.asarray(WL.M3["thetas"])[(tr % len(WL.M3["thetas"])).astype(np.int64)]
+    pl = {}
+    for x in WL.M3["thetas"]:
+        m = np.isclose(th, x)
+        n = int(m.sum())
+        nf = int(f[m].sum()) if n else 0
+        pl["%.3f" % x] = {"n": n, "fail": nf, "p_L": nf / n if n else None}
     line = {"metric": METRIC,
-            "value": value, "unit": "trajectories/s", "n_gpus": world, "steps": a.steps,
-            "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "c64" if a.precision == "fp32" else "c128",
-            "data": "synthetic",
-            "config": dict(run_config(a, B), lost_trajectories_last_step=lost),
-            "clocks": ck, "e2e": e2e, "gpu_launches": int(sum(prof["launches"].values())),
-            "roofline": roof,
-            "ledger_tflop": {k: v / 1e12 for k, v in prof["flops"].items()},
-            "device_ms_by_class": {k: round(v, 1) for k, v in cms.items()}}
+            "value": value, "unit": "trajectories/s", "n_gpus": world, "steps": K,
+            "warmup": W, "ms_per_step": ms / K, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "c64+f64", "data": "synthetic",
+            "config": run_config(a),
+            "clocks": ck, "e2e": e2e, "gpu_launches": int(prof["kernels"]),
+            "roofline": roofline(a, prof, dom),
+            "fill_s": fill_s,
+            "device_ms_by_class_warmup": {k: round(v, 1) for k, v in cms.items()},
+            "ledger_tflop_per_traj": {k: v / 1e12 / max(1, K * G) for k, v in prof["flops"].items()},
+            "pL_by_theta": pl,
+            "mean_log_prob": float(logp.cpu().numpy().mean()), "mean_discarded": float(disc.cpu().numpy().mean())}
     if not a.no_cpu_baseline and world == 1:
-        line["cpu_baseline"] = cpu_baseline(a, a.cpu_seconds)
+        line["cpu_baseline"] = cpu_baseline(a)
     print(json.dumps(line))
     if dist:
         dist.destroy_process_group()

@@ -33,7 +33,10 @@ typedef enum {
   TTN_ECUDA = 3,        /* a CUDA call failed                                */
   TTN_ETIMEOUT = 4,     /* a device-side bounded wait expired                */
   TTN_EUNSUPPORTED = 5, /* valid request this build does not implement       */
-  TTN_EOVERFLOW = 6     /* a per-shot bound was exceeded (message says which)*/
+  TTN_EOVERFLOW = 6,    /* a per-shot bound was exceeded (message says which)*/
+  TTN_ENUMERIC = 7      /* a trajectory's state lost its norm or became
+                           non-finite (message names the trajectory and the
+                           step); no result of the call is valid            */
 } ttn_status;
 
 /* Error channel after every layer on every qubit the layer does not measure
@@ -52,8 +55,15 @@ typedef enum {
 
 /* Arithmetic of the tree tensors.  FP64: complex128 throughout.  FP32:
  * complex64 tensors and singular value decompositions, with probabilities,
- * log-probabilities and discarded weights accumulated in double. */
-typedef enum { TTN_PREC_FP64 = 0, TTN_PREC_FP32 = 1 } ttn_precision;
+ * log-probabilities and discarded weights accumulated in double.  MIXED:
+ * complex64 tensors and contractions, with every isometry-centre
+ * factorisation in FP64 -- the Gram matrix of the bond matrix formed exactly
+ * on the tensor cores (see ttn_gram_exact), its Hermitian eigendecomposition
+ * (cyclic Jacobi for bonds up to 64, tridiagonal above), the kept rank and
+ * the singular values in double -- and probabilities, log-probabilities and
+ * discarded weights in double.  svd_mode is ignored in MIXED runs; their
+ * contractions use the FP32 FMA units unless gemm_mode = 2. */
+typedef enum { TTN_PREC_FP64 = 0, TTN_PREC_FP32 = 1, TTN_PREC_MIXED = 2 } ttn_precision;
 
 /* Qubit -> TTN leaf assignment (App. B).  DEFAULT: qubit i on leaf i.
  * OPTIMIZED: recursive spectral bisection of the gate-similarity graph
@@ -99,8 +109,8 @@ typedef struct {
   uint64_t seed;                 /* Philox key                           */
   uint64_t first_traj;           /* index of the first trajectory        */
   double svd_eps;                /* singular values <= svd_eps * s_max are
-                                    dropped; <= 0 selects 1e-13 (FP64) or
-                                    5e-7 (FP32)                           */
+                                    dropped; <= 0 selects 1e-13 (FP64),
+                                    5e-7 (FP32) or 1e-6 (MIXED)           */
   const double* theta_per_traj;  /* optional [n_traj], overrides theta    */
   const double* gamma_per_traj;  /* optional [n_traj], overrides gamma    */
   int32_t svd_mode;              /* factorisation of a centre move:
@@ -163,14 +173,14 @@ ttn_status ttn_circuit_layout(const ttn_circuit* circuit, int32_t* leaf_of_qubit
  * draws from Philox4x32-10 keyed by (seed, trajectory, event), then decodes
  * (App. A.2).  Outputs (any may be NULL): records [n_traj][n_record_bits]
  * (u8 0/1), logical_fail [n_traj] (u8: 0/1 decoded logical outcome, 2 the
- * decoder's bound was exceeded, 3 the trajectory's state lost its norm or
- * became non-finite in the FP32 arithmetic -- such trajectories are kept out
- * of p_L), log_prob [n_traj] (log p of the
+ * decoder's bound was exceeded), log_prob [n_traj] (log p of the
  * sampled record and branches), discarded [n_traj] (sum of discarded
  * squared singular values), near_ties [n_traj] (draws with |u - p| < 1e-9
  * (FP64) or 1e-5 (FP32)).  Results depend only on (seed, trajectory index),
  * not on batching.  EOVERFLOW if a decoding instance exceeds the decoder's
- * bound; ENOMEM if one trajectory does not fit on the device. */
+ * bound; ENOMEM if one trajectory does not fit on the device; ENUMERIC if a
+ * trajectory's state lost its norm or became non-finite (the whole call
+ * fails: leaving such a trajectory out would bias p_L). */
 ttn_status ttn_run_trajectories(const ttn_circuit* circuit, const ttn_run_params* params,
                                 uint64_t n_traj, uint8_t* records, uint8_t* logical_fail,
                                 double* log_prob, double* discarded, int32_t* near_ties,
@@ -316,6 +326,40 @@ ttn_status ttn_slot_check(const ttn_circuit* circuit, int32_t noise, int32_t chi
 ttn_status ttn_decode(const ttn_circuit* circuit, uint64_t n, const uint8_t* records,
                       uint8_t* fail, int32_t* color, int64_t* score, void* cuda_stream);
 
+/* Pipelined resident batch of trajectories (Sec. III.C trajectories, the
+ * same semantics and random draws as ttn_run_trajectories).  n_resident
+ * trajectories stay on the device in n_segments groups of
+ * G = n_resident / n_segments; the circuit's step program is cut into
+ * n_segments segments of about equal worst-case cost.  Creating the pipeline
+ * runs group g through its first g segments (synchronously on cuda_stream);
+ * afterwards every ttn_pipeline_step runs one segment of every group, each
+ * group on its own library-created stream ordered after cuda_stream, and the
+ * group that finished its last segment is decoded (App. A.2) and restarts
+ * with the next G trajectory indices.  So every step completes exactly G
+ * trajectories, first_traj, first_traj + 1, ... in order of completion.
+ * Trajectory t uses theta_cycle[t % n_theta] as its SRX angle when
+ * n_theta > 0 (host array, copied), else params->theta; per-trajectory
+ * arrays in params are rejected (EINVAL).  max_device_bytes bounds the
+ * resident batch (0: 85 % of free memory; ENOMEM if it does not fit).
+ * *out: library-owned handle, released by ttn_pipeline_free. */
+typedef struct ttn_pipeline ttn_pipeline;
+ttn_status ttn_pipeline_create(const ttn_circuit* circuit, const ttn_run_params* params, int32_t n_resident,
+                               int32_t n_segments, const double* theta_cycle, int32_t n_theta,
+                               uint64_t max_device_bytes, void* cuda_stream, ttn_pipeline** out);
+/* One pipeline step.  Outputs of the G trajectories it completed (any may
+ * be NULL): logical_fail [G] (u8 as in ttn_run_trajectories), log_prob [G],
+ * discarded [G] -- DEVICE pointers when outputs_on_device, else host -- and
+ * traj [G] (host: their trajectory indices), *n_done = G.  Synchronises
+ * cuda_stream.  ENUMERIC / ETIMEOUT / ECUDA as in ttn_run_trajectories;
+ * EOVERFLOW if a decoding instance exceeded the decoder's bound (fail byte
+ * 2, the other outputs valid). */
+ttn_status ttn_pipeline_step(ttn_pipeline* pipeline, uint8_t* logical_fail, double* log_prob,
+                             double* discarded, uint64_t* traj, int32_t* n_done, int32_t outputs_on_device,
+                             void* cuda_stream);
+/* G, the trajectories each step completes (0 for NULL). */
+int32_t ttn_pipeline_group_size(const ttn_pipeline* pipeline);
+void ttn_pipeline_free(ttn_pipeline* pipeline);
+
 /* Exact Gram matrix G = M^H M of one complex64 matrix on the tensor cores:
  * the kernel of the isometry-centre factorisation (Sec. III.B: the centre
  * moves by the Schmidt decomposition of a bond matrix; the device path takes
@@ -387,12 +431,16 @@ ttn_status ttn_profile_class_ms(double* class_ms);
  * Gram-Schmidt), Rayleigh-Ritz, back-transformation.  Host [6]. */
 ttn_status ttn_profile_eig_phases(double* cycles);
 /* Centre-move shapes of the current (or last) profile, summed over
- * trajectories: hist[(t * 513 + n) * 3 + f] for t = 1 on truncating moves
+ * trajectories: hist[(t * 513 + n) * 4 + f] for t = 1 on truncating moves
  * (0 otherwise), n = bond dimension before the move (clamped to 512) and
  * f = 0 number of moves, 1 sum of m (rows of the m x n bond matrix), 2 sum of
- * the kept rank.  Host [2 * 513 * 3].  Profiling only; no Sec. of the paper
+ * the kept rank, 3 SM cycles of the Gram eigensolver (kernel entry to rank
+ * selection).  Host [2 * 513 * 4].  Profiling only; no Sec. of the paper
  * defines it. */
 ttn_status ttn_profile_move_hist(double* hist);
+/* Kernel launches of the library in the current (or last) profile: every
+ * engine kernel, the tensor-core Gram kernels and the decoder's. */
+ttn_status ttn_profile_kernels(uint64_t* kernels);
 
 const char* ttn_status_string(ttn_status status);
 const char* ttn_last_error(void);

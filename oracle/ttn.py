@@ -311,10 +311,11 @@ def apply_noise_ttn(tt, q, model, theta, gamma, u):
 
 
 def run_trajectory(circ, model, theta, gamma, seed, traj, chi, leaf_of_qubit=None,
-                   snapshot_layers=(), eps=1e-13, max_ops=None, deadline=None):
+                   snapshot_layers=(), eps=1e-13, max_ops=None, deadline=None, on_op=None):
     """One trajectory on the numpy TTN.  max_ops / deadline (a time.time()
     value) stop the run early, for bounded timing samples; `ops_done` in the
-    result counts the ops run."""
+    result counts the ops run.  on_op(i), if given, is called after op i
+    (a timing hook; it does not touch the state)."""
     N = circ.n_qubits
     if leaf_of_qubit is None:
         leaf_of_qubit = default_layout(N)
@@ -364,6 +365,8 @@ def run_trajectory(circ, model, theta, gamma, seed, traj, chi, leaf_of_qubit=Non
             logp += lp
             if dist is not None:
                 margin = min(margin, dist)
+        if on_op is not None:
+            on_op(i)
     if cur_layer in snap:
         states[cur_layer] = tt.amplitudes()
     return dict(rec=rec, logp=logp, margin=margin, states=states, ttn=tt,

@@ -8,7 +8,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB = None
 
 NOISE = {"none": 0, "srx": 1, "ad": 2, "srx_pta": 3, "ad_pta": 4, "srx_ad": 5}
-PRECISION = {"fp64": 0, "fp32": 1}
+PRECISION = {"fp64": 0, "fp32": 1, "mixed": 2}
 LAYOUT = {"default": 0, "optimized": 1, "explicit": 2, "search": 3}
 
 c_i32p = ctypes.POINTER(ctypes.c_int32)
@@ -41,7 +41,8 @@ EXPORTS = ["ttn_build_circuit", "ttn_free_circuit", "ttn_circuit_info", "ttn_cir
            "ttn_circuit_layout", "ttn_run_trajectories", "ttn_logical_error_rate", "ttn_decode",
            "ttn_debug_state", "ttn_philox_uniforms", "ttn_profile_begin", "ttn_profile_end",
            "ttn_grad", "ttn_decode_noalloc", "ttn_profile_class_ms", "ttn_profile_eig_phases",
-           "ttn_profile_move_hist", "ttn_gram_exact",
+           "ttn_profile_move_hist", "ttn_gram_exact", "ttn_pipeline_create", "ttn_pipeline_step",
+           "ttn_pipeline_group_size", "ttn_pipeline_free", "ttn_profile_kernels",
            "ttn_run_mixed", "ttn_newton_crossing", "ttn_crossing", "ttn_threshold_fit", "ttn_grad_sums",
            "ttn_slot_check", "ttn_layout_noise_free_chi",
            "ttn_status_string",
@@ -92,6 +93,14 @@ def load_library():
     lib.ttn_decode.argtypes = [vp, ctypes.c_uint64, vp, vp, vp, vp, vp]
     lib.ttn_decode_noalloc.argtypes = [vp, ctypes.c_uint64, vp, vp, vp, vp, vp]
     lib.ttn_gram_exact.argtypes = [vp, ctypes.c_int64, ctypes.c_int32, vp, vp]
+    lib.ttn_pipeline_create.argtypes = [vp, ctypes.POINTER(RunParams), ctypes.c_int32, ctypes.c_int32, vp,
+                                        ctypes.c_int32, ctypes.c_uint64, vp, ctypes.POINTER(vp)]
+    lib.ttn_pipeline_step.argtypes = [vp, vp, vp, vp, vp, ctypes.POINTER(ctypes.c_int32), ctypes.c_int32, vp]
+    lib.ttn_pipeline_group_size.argtypes = [vp]
+    lib.ttn_pipeline_group_size.restype = ctypes.c_int32
+    lib.ttn_pipeline_free.argtypes = [vp]
+    lib.ttn_profile_kernels.argtypes = [ctypes.POINTER(ctypes.c_uint64)]
+    lib.ttn_pipeline_free.restype = None
     lib.ttn_debug_state.argtypes = [vp, ctypes.POINTER(RunParams), ctypes.c_uint64, ctypes.c_int32,
                                     c_dblp]
     lib.ttn_philox_uniforms.argtypes = [ctypes.c_uint64, c_u64p, ctypes.c_uint64, c_i32p,
@@ -237,6 +246,65 @@ def run_trajectories(circuit, n_traj, noise="srx", theta=0.0, gamma=0.0, chi=16,
                                     _ptr(out.get("near_ties")), st))
     del keep
     return out
+
+
+class Pipeline:
+    """Pipelined resident batch (ttn_pipeline_*): n_resident trajectories on
+    the device in n_segments groups; every step() runs one program segment of
+    every group and completes group_size trajectories.  theta_cycle: optional
+    SRX angles, trajectory t at theta_cycle[t % len]."""
+
+    def __init__(self, circuit, n_resident, n_segments, noise="srx", theta=0.0, gamma=0.0, chi=16,
+                 precision="mixed", seed=0, first_traj=0, theta_cycle=None, svd_eps=0.0, gemm_mode="auto",
+                 max_device_bytes=0, stream=None):
+        lib = load_library()
+        p, keep = _run_params(noise, theta, gamma, chi, precision, seed, first_traj, svd_eps,
+                              gemm_mode=gemm_mode)
+        cyc = None if theta_cycle is None else np.ascontiguousarray(theta_cycle, dtype=np.float64)
+        h = ctypes.c_void_p()
+        st = ctypes.c_void_p(int(stream)) if stream else None
+        self.circuit = circuit
+        self._lib = lib
+        _check(lib.ttn_pipeline_create(circuit.handle, ctypes.byref(p), int(n_resident), int(n_segments),
+                                       _ptr(cyc), 0 if cyc is None else cyc.size, int(max_device_bytes),
+                                       st, ctypes.byref(h)))
+        del keep
+        self.handle = h
+        self.group_size = int(lib.ttn_pipeline_group_size(h))
+
+    def step(self, out=None, stream=None):
+        """One step.  out=None: returns host {fail, log_prob, discarded,
+        traj}; else `out` holds torch CUDA tensors (fail uint8 [G], log_prob
+        and discarded float64 [G]) written on the device, and `stream` is a
+        CUDA stream handle (int).  The trajectory indices are returned in
+        host memory either way."""
+        G = self.group_size
+        traj = np.zeros(G, dtype=np.uint64)
+        nd = ctypes.c_int32()
+        st = ctypes.c_void_p(int(stream)) if stream else None
+        if out is None:
+            res = dict(fail=np.zeros(G, dtype=np.uint8), log_prob=np.zeros(G), discarded=np.zeros(G))
+            on_dev = 0
+        else:
+            res = out
+            on_dev = 1
+        _check(self._lib.ttn_pipeline_step(self.handle, _ptr(res.get("fail")), _ptr(res.get("log_prob")),
+                                           _ptr(res.get("discarded")), _ptr(traj), ctypes.byref(nd),
+                                           on_dev, st))
+        res = dict(res)
+        res["traj"] = traj[:nd.value]
+        return res
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self._lib.ttn_pipeline_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def run_mixed(items, out=None, stream=None):
@@ -441,10 +509,12 @@ def profile_end():
     _check(lib.ttn_profile_class_ms(cm))
     ep = (ctypes.c_double * 6)()
     _check(lib.ttn_profile_eig_phases(ep))
-    mh = (ctypes.c_double * (2 * 513 * 3))()
+    mh = (ctypes.c_double * (2 * 513 * 4))()
     _check(lib.ttn_profile_move_hist(mh))
-    hist = np.array(list(mh)).reshape(2, 513, 3)
-    return dict(timed_ms=ms.value, timed_launches=nl.value, move_hist=hist,
+    hist = np.array(list(mh)).reshape(2, 513, 4)
+    nk = ctypes.c_uint64()
+    _check(lib.ttn_profile_kernels(ctypes.byref(nk)))
+    return dict(timed_ms=ms.value, timed_launches=nl.value, move_hist=hist, kernels=nk.value,
                 flops=dict(zip(KERNEL_CLASSES, list(fl))), bytes=dict(zip(KERNEL_CLASSES, list(by))),
                 launches=dict(zip(KERNEL_CLASSES, list(la))), class_ms=dict(zip(KERNEL_CLASSES, list(cm))),
                 eig_phase_cycles=dict(zip(EIG_PHASES, list(ep))))

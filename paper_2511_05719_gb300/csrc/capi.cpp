@@ -38,6 +38,7 @@ const char* ttn_status_string(ttn_status s) {
     case TTN_ETIMEOUT: return "device wait timed out";
     case TTN_EUNSUPPORTED: return "unsupported";
     case TTN_EOVERFLOW: return "per-shot bound exceeded";
+    case TTN_ENUMERIC: return "trajectory lost its norm";
   }
   return "unknown status";
 }
@@ -150,7 +151,7 @@ ttn_status ttn_circuit_layout(const ttn_circuit* c, int32_t* leaf_of_qubit) {
 static ttn_status check_params(const ttn_circuit* c, const ttn_run_params* p) {
   if (!c || !p) return fail_with(TTN_EINVAL, "null argument");
   if (p->noise < TTN_NOISE_NONE || p->noise > TTN_NOISE_SRX_AD) return fail_with(TTN_EINVAL, "unknown noise model");
-  if (p->precision != TTN_PREC_FP64 && p->precision != TTN_PREC_FP32)
+  if (p->precision != TTN_PREC_FP64 && p->precision != TTN_PREC_FP32 && p->precision != TTN_PREC_MIXED)
     return fail_with(TTN_EINVAL, "unknown precision");
   if (p->chi < 1 || p->chi > 4096) return fail_with(TTN_EINVAL, "chi must be in [1, 4096]");
   if (!std::isfinite(p->theta)) return fail_with(TTN_EINVAL, "theta must be finite");
@@ -167,7 +168,8 @@ static RunRequest make_request(const ttn_run_params* p, uint64_t n_traj, void* s
   rq.precision = p->precision;
   rq.theta = p->theta;
   rq.gamma = p->gamma;
-  rq.svd_eps = p->svd_eps > 0 ? p->svd_eps : (p->precision == TTN_PREC_FP64 ? 1e-13 : 5e-7);
+  rq.svd_eps = p->svd_eps > 0 ? p->svd_eps
+                              : (p->precision == TTN_PREC_FP64 ? 1e-13 : (p->precision == TTN_PREC_MIXED ? 1e-6 : 5e-7));
   rq.seed = p->seed;
   rq.first_traj = p->first_traj;
   rq.n_traj = n_traj;
@@ -325,7 +327,7 @@ ttn_status ttn_logical_error_rate(const ttn_circuit* c, const ttn_run_params* p,
   uint64_t nf = 0, nv = 0;
   for (uint8_t f : fail) {
     nf += f == 1;
-    nv += f <= 1;  // 2: decoder bound exceeded, 3: trajectory lost its norm
+    nv += f <= 1;  // 2: decoder bound exceeded
   }
   if (nv == 0) return fail_with(TTN_EOVERFLOW, "no valid shots");
   double pl = (double)nf / (double)nv;
@@ -375,7 +377,7 @@ ttn_status grad_run(const ttn_circuit* c, const ttn_run_params* p, uint64_t shot
   // score-function estimator: dp_L/dx = E[fail * d/dx log p(trajectory)]
   double n = 0, nf = 0, m1 = 0, m2 = 0;
   for (uint64_t i = 0; i < shots; ++i) {
-    if (fail[i] > 1) continue;  // decoder bound exceeded or state lost: not counted
+    if (fail[i] > 1) continue;  // decoder bound exceeded: not counted
     const double f = fail[i];
     const double x = f * sc[i];
     n += 1;
@@ -821,10 +823,54 @@ ttn_status ttn_profile_eig_phases(double* cycles) {
   return TTN_OK;
 }
 
+ttn_status ttn_pipeline_create(const ttn_circuit* c, const ttn_run_params* p, int32_t n_resident,
+                               int32_t n_segments, const double* theta_cycle, int32_t n_theta,
+                               uint64_t max_device_bytes, void* cuda_stream, ttn_pipeline** out) {
+  ttn_status s = check_params(c, p);
+  if (s != TTN_OK) return s;
+  if (!out) return fail_with(TTN_EINVAL, "null argument");
+  *out = nullptr;
+  if (n_segments < 1 || n_resident < n_segments || n_resident % n_segments != 0)
+    return fail_with(TTN_EINVAL, "n_resident must be a positive multiple of n_segments >= 1");
+  if (n_theta < 0 || (n_theta > 0 && !theta_cycle)) return fail_with(TTN_EINVAL, "theta_cycle / n_theta");
+  for (int i = 0; i < n_theta; ++i)
+    if (!std::isfinite(theta_cycle[i])) return fail_with(TTN_EINVAL, "theta_cycle must be finite");
+  if (p->theta_per_traj || p->gamma_per_traj)
+    return fail_with(TTN_EINVAL, "per-trajectory strengths: pass theta_cycle to the pipeline");
+  RunRequest rq = make_request(p, 0, cuda_stream);
+  rq.max_device_bytes = (size_t)max_device_bytes;
+  ttn::PipelineImpl* impl = nullptr;
+  s = ttn::pipeline_create(*c, rq, n_resident, n_segments, theta_cycle, n_theta, cuda_stream, &impl);
+  if (s != TTN_OK) return s;
+  *out = reinterpret_cast<ttn_pipeline*>(impl);
+  return TTN_OK;
+}
+
+ttn_status ttn_pipeline_step(ttn_pipeline* p, uint8_t* logical_fail, double* log_prob, double* discarded,
+                             uint64_t* traj, int32_t* n_done, int32_t outputs_on_device, void* cuda_stream) {
+  if (!p) return fail_with(TTN_EINVAL, "null pipeline");
+  return ttn::pipeline_step(reinterpret_cast<ttn::PipelineImpl*>(p), logical_fail, log_prob, discarded, traj,
+                            n_done, outputs_on_device != 0, cuda_stream);
+}
+
+int32_t ttn_pipeline_group_size(const ttn_pipeline* p) {
+  return p ? ttn::pipeline_group_size(reinterpret_cast<const ttn::PipelineImpl*>(p)) : 0;
+}
+
+void ttn_pipeline_free(ttn_pipeline* p) {
+  if (p) ttn::pipeline_free(reinterpret_cast<ttn::PipelineImpl*>(p));
+}
+
 ttn_status ttn_profile_move_hist(double* hist) {
   if (!hist) return fail_with(TTN_EINVAL, "null argument");
   const Profile& p = profile();
   for (int i = 0; i < MOVE_HIST_WORDS; ++i) hist[i] = p.move_hist[i];
+  return TTN_OK;
+}
+
+ttn_status ttn_profile_kernels(uint64_t* kernels) {
+  if (!kernels) return fail_with(TTN_EINVAL, "null argument");
+  *kernels = profile().kernels;
   return TTN_OK;
 }
 

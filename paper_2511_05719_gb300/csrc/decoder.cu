@@ -709,6 +709,7 @@ ttn_status decode_device(const ttn_circuit& c, int nb, const uint8_t* d_records,
     int m = std::min(chunk, nb - s0);
     k_decode<<<(m + 63) / 64, 64, 0, st>>>(d, m, d_records + (size_t)s0 * c.n_rec, dfail + s0,
                                            dcol ? dcol + s0 : nullptr, dscore ? dscore + s0 : nullptr);
+    if (profile().active) profile().kernels += 1;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
       cleanup();

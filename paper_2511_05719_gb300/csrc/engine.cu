@@ -23,6 +23,7 @@
 #include <vector>
 
 #include "engine.h"
+#include "gram.h"
 
 namespace ttn {
 
@@ -133,6 +134,8 @@ struct Dev {
   int32_t* err_step;     // [B][2] step of the first fatal error, of the first non-convergence
   int cur_step;          // step of the program being launched
   int cur_trunc;         // 1 if that step is a truncating move
+  int eig_nsplit;        // > 0: k_eig takes bonds n <= eig_nsplit, k_eig_tri the larger ones
+  int2* shape;           // [B] (m, n) of the current move's bond matrix (MIXED runs)
 };
 
 enum : int32_t { ERR_ZERO_NORM = 1, ERR_NO_CONVERGE = 2, ERR_CAPACITY = 4, ERR_NAN = 8 };
@@ -147,6 +150,10 @@ __device__ __forceinline__ void flag_err(const Dev<R>& d, int b, int32_t code) {
 // Gram matrices up to this size are diagonalised in shared memory (k_eig);
 // larger ones by the tridiagonal solver (k_eig_tri).
 static constexpr int EIG_SMEM_MAX = 131072;
+// MIXED runs: FP64 bond Gram matrices up to this dimension go to the
+// shared-memory Jacobi solver (36 n^3 flops, short serial chains), larger
+// ones to the tridiagonal solver (~12 n^3 flops, longer serial chains).
+static constexpr int EIG_JACOBI_N = 64;
 static constexpr int TRI_UNROLL = 16;  // loads in flight per thread in L2-resident sweeps
 static constexpr int TRI_NB = 8;       // reflectors per compact-WY block of the back-transformation
 static constexpr int TRI_INV_ITERS = 2;  // inverse-iteration / orthonormalisation rounds
@@ -743,6 +750,8 @@ __global__ void k_gather_rows(Dev<R> d, int v, int w) {
   const int leg = (w == 2 * v) ? 0 : ((w == 2 * v + 1) ? 1 : 2);
   const int n = leg == 0 ? dl : (leg == 1 ? dr : du);
   const int m = dl * dr * du / n;
+  if (d.shape && blockIdx.x == 0 && threadIdx.x == 0)
+    d.shape[b] = (int64_t)m * n > d.wstride ? make_int2(0, 0) : make_int2(m, n);
   if ((int64_t)m * n > d.wstride) return;
   const cx<R>* T = node_ptr(d, b, v);
   cx<R>* W = d.W + (int64_t)b * d.wstride;
@@ -785,7 +794,7 @@ __global__ void __launch_bounds__(256) k_gram(Dev<R> d, int v, int w) {
 // thread.
 template <typename R>
 __device__ int eig_select(Dev<R>& d, int b, int v, int w, int kcap, int n, double trace,
-                          double eps_keep) {
+                          double eps_keep, long long clk_start = 0) {
   const int tid = threadIdx.x, nth = blockDim.x;
   int* D = d.dims + b * d.ds;
   double* sv = d.sv + (int64_t)b * d.nmax;
@@ -827,11 +836,12 @@ __device__ int eig_select(Dev<R>& d, int b, int v, int w, int kcap, int n, doubl
     const int bond = (w == v / 2) ? v : w;
     if (d.ledger) {
       const int64_t mm = (int64_t)D[2 * v] * D[2 * v + 1] * (v == 1 ? 1 : D[v]) / (n > 0 ? n : 1);
-      unsigned long long* h =
-          d.ledger + LEDGER_HIST + ((int64_t)(d.cur_trunc ? 1 : 0) * MOVE_HIST_N + min(n, MOVE_HIST_N - 1)) * 3;
+      unsigned long long* h = d.ledger + LEDGER_HIST +
+                              ((int64_t)(d.cur_trunc ? 1 : 0) * MOVE_HIST_N + min(n, MOVE_HIST_N - 1)) * MOVE_HIST_F;
       atomicAdd(&h[0], 1ull);
       atomicAdd(&h[1], (unsigned long long)mm);
       atomicAdd(&h[2], (unsigned long long)k);
+      if (clk_start > 0) atomicAdd(&h[3], (unsigned long long)(clock64() - clk_start));
     }
     D[bond] = k;
     d.knew[b] = k;
@@ -846,8 +856,8 @@ __device__ int eig_select(Dev<R>& d, int b, int v, int w, int kcap, int n, doubl
 // Jacobi tail: V (row-major n x n eigenvectors) -> V_k into G.
 template <typename R>
 __device__ void eig_select_tail(Dev<R>& d, int b, int v, int w, int kcap, int n, const cx<R>* V,
-                                cx<R>* Gglob, double trace) {
-  const int k = eig_select(d, b, v, w, kcap, n, trace, d.eps_gram);
+                                cx<R>* Gglob, double trace, long long clk_entry) {
+  const int k = eig_select(d, b, v, w, kcap, n, trace, d.eps_gram, clk_entry);
   const int32_t* perm = d.perm + (int64_t)b * d.nmax;
   // V_k (n x k, row-major, columns in descending eigenvalue order) into G
   for (int idx = threadIdx.x; idx < n * k; idx += blockDim.x) {
@@ -860,6 +870,7 @@ __device__ void eig_select_tail(Dev<R>& d, int b, int v, int w, int kcap, int n,
 // V_k S_k^-1 (into G) and R = S_k V_k^H (into Rm).
 template <typename R>
 __global__ void __launch_bounds__(512) k_eig(Dev<R> d, int v, int w, int kcap) {
+  const long long clk_entry = clock64();
   const int b = blockIdx.x;
   const int tid = threadIdx.x, nth = blockDim.x;
   int* D = d.dims + b * d.ds;
@@ -877,6 +888,7 @@ __global__ void __launch_bounds__(512) k_eig(Dev<R> d, int v, int w, int kcap) {
   __shared__ cx<R> pe[256];
   __shared__ int pp[256], pq[256];
   __shared__ double s_tr;
+  if (d.eig_nsplit > 0 && n > d.eig_nsplit) return;  // the tridiagonal solver's share
   if ((int64_t)n * n > d.vstride || n > d.nmax || n > 512) {
     if (tid == 0) {
       flag_err(d, b, ERR_CAPACITY);
@@ -976,7 +988,7 @@ __global__ void __launch_bounds__(512) k_eig(Dev<R> d, int v, int w, int kcap) {
   }
   for (int j = tid; j < n; j += nth) sv[j] = (double)G[(int64_t)j * n + j].x;  // eigenvalues
   __syncthreads();
-  eig_select_tail(d, b, v, w, kcap, n, V, Gglob, s_tr);
+  eig_select_tail(d, b, v, w, kcap, n, V, Gglob, s_tr, clk_entry);
 }
 
 // Block-wide sums (blockDim.x a multiple of 32); red holds 64 doubles.
@@ -1073,11 +1085,13 @@ __device__ void tri_reflector(cx<R>* A, int n, int c, cx<R>* vout, R* tau, cx<R>
 // k_eig: V_k (n x k, row-major) into G.
 template <typename R>
 __global__ void __launch_bounds__(512) k_eig_tri(Dev<R> d, int v, int w, int kcap) {
+  const long long clk_entry = clock64();
   const int b = blockIdx.x;
   const int tid = threadIdx.x, nth = blockDim.x;
   const int* D = d.dims + b * d.ds;
   const int leg = (w == 2 * v) ? 0 : ((w == 2 * v + 1) ? 1 : 2);
   const int n = leg == 0 ? D[2 * v] : (leg == 1 ? D[2 * v + 1] : D[v]);
+  if (d.eig_nsplit > 0 && n <= d.eig_nsplit) return;  // the Jacobi solver's share
   if ((int64_t)n * n > d.vstride || n > d.nmax || n > nth || nth > 512) {
     if (tid == 0) {
       flag_err(d, b, ERR_CAPACITY);
@@ -1353,7 +1367,7 @@ __global__ void __launch_bounds__(512) k_eig_tri(Dev<R> d, int v, int w, int kca
   // singular values below sqrt(eps) s_max are not resolved by a Gram matrix
   // in this precision
   const double eps_keep = fmax(d.eps_gram, sqrt((double)epsR));
-  const int k = eig_select(d, b, v, w, kcap, n, trace, eps_keep);
+  const int k = eig_select(d, b, v, w, kcap, n, trace, eps_keep, clk_entry);
   if (tid == 0)
     ledger_add(d.ledger, KC_EIG, 16.0 / 3.0 * (double)n * n * n + 8.0 * (double)n * n * k,
                (double)sizeof(cx<R>) * ((double)n * n + (double)n * k));
@@ -1795,6 +1809,18 @@ __global__ void __launch_bounds__(256) k_unorm_apply(Dev<R> d, int v, int w) {
     const R sc = (R)sv[c] * scale;
     Rm[idx] = {sc * vv.x, -sc * vv.y};
   }
+}
+
+// MIXED runs: the FP64 eigensolver leaves V_k (n x k, row-major, complex128)
+// in its Gram buffer; the tensor-core contraction Y = M V_k takes it in
+// complex64.
+__global__ void k_vk_to_float(Dev<float> d, const cx<double>* G64) {
+  const int b = blockIdx.x;
+  const int n = d.nold[b], k = d.knew[b];
+  if (k <= 0 || (int64_t)n * k > d.vstride) return;
+  const cx<double>* src = G64 + (int64_t)b * d.vstride;
+  cx<float>* dst = d.G + (int64_t)b * d.vstride;
+  for (int i = threadIdx.x; i < n * k; i += blockDim.x) dst[i] = {(float)src[i].x, (float)src[i].y};
 }
 
 // Y = M V_k: m x k, written into T_v with bond dimension k.
@@ -2259,6 +2285,7 @@ struct Engine {
   const Program& prog;
   int chi, noise, B;
   int gemm_mode = 0;               // 0 auto, 1 FMA units, 2 tensor cores (FP32)
+  bool mixed = false;              // MIXED: exact Gram matrix + FP64 eigensolver on every move
   cudaStream_t st;
   std::vector<int> bcap;           // bond caps (outside gates)
   std::vector<int64_t> ncap;       // node slot capacity (elements)
@@ -2295,6 +2322,20 @@ struct Engine {
   Op1* dOp1 = nullptr;
   Group1* dGroups = nullptr;
   unsigned long long* dLedger = nullptr;
+  // MIXED runs: exact Gram matrix workspaces and the FP64 eigensolver's buffers
+  int2* dShape = nullptr;
+  unsigned int* dAmax = nullptr;
+  int* dExpo = nullptr;
+  uint16_t* dSlices = nullptr;
+  unsigned long long* dGfix = nullptr;
+  cx<double>* dG64 = nullptr;
+  cx<double>* dV64 = nullptr;
+  cx<double>* dTs64 = nullptr;
+  int64_t sstride = 0;             // bf16 digit tiles per trajectory (largest move)
+  GramArgs gargs, gbase;
+  Dev<R> base{};                   // the whole batch (dev = a group of it, see select_group)
+  int64_t b0 = 0;                  // first trajectory of the selected group
+  double eps_mixed = 1e-6;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> events;
   std::vector<int> event_class;
   uint64_t class_launches[NCLASS] = {0};
@@ -2302,10 +2343,18 @@ struct Engine {
 
   // Launch wrapper: counts launches per class and, when profiling that
   // class, brackets the launch with events on the launch stream.
+  uint64_t kernel_launches = 0;    // kernels launched since the last collect_profile
+
   template <typename F>
   void timed(int cls, F&& fn) {
+    timed(cls, 1, fn);
+  }
+  // nk: kernels fn launches
+  template <typename F>
+  void timed(int cls, int nk, F&& fn) {
     Profile& pf = profile();
     class_launches[cls]++;
+    kernel_launches += (uint64_t)nk;
     if (pf.active && (pf.timed_class == cls || pf.timed_class == NCLASS)) {
       cudaEvent_t a, b;
       cudaEventCreate(&a);
@@ -2349,6 +2398,8 @@ struct Engine {
       pf.class_launches[c] += class_launches[c];
       class_launches[c] = 0;
     }
+    pf.kernels += kernel_launches;
+    kernel_launches = 0;
     if (dLedger) cudaMemset(dLedger, 0, sizeof(h));
   }
 
@@ -2373,12 +2424,31 @@ struct Engine {
     wstride = (wmax + 31) / 32 * 32;
     nmax = 2 * maxb;
     vstride = (int64_t)nmax * nmax;
+    // digit tiles of the exact Gram matrix: the largest bond matrix any move
+    // of the program can form (capacities, legs doubled inside a gate)
+    for (const Step& st : prog.steps) {
+      if (st.kind != S_MOVE) continue;
+      const int v = st.a, w = st.b;
+      const int bond = (w == v / 2) ? v : w;
+      const int lv = (w == 2 * v) ? 0 : ((w == 2 * v + 1) ? 1 : 2);
+      const int64_t c3[3] = {2 * (int64_t)bcap[2 * v], 2 * (int64_t)bcap[2 * v + 1],
+                             v == 1 ? 1 : 2 * (int64_t)bcap[v]};
+      int64_t mm = 1;
+      for (int t = 0; t < 3; ++t)
+        if (t != lv) mm *= c3[t];
+      mm = std::min<int64_t>(mm, ncap[v]);
+      sstride = std::max<int64_t>(sstride, gram_slice_elems(mm, (int)(2 * bcap[bond])));
+    }
   }
 
   size_t bytes_per_traj() const {
-    return sizeof(cx<R>) * (size_t)(tstride + wstride + 5 * vstride) +  // V, Rm, G, Ts (2)
-           sizeof(int32_t) * (2 * c.L + 2 * nmax + 4) + sizeof(double) * (nmax + 5) + c.n_rec + c.N +
-           c.n_events + 64;
+    size_t b = sizeof(cx<R>) * (size_t)(tstride + wstride + 5 * vstride) +  // V, Rm, G, Ts (2)
+               sizeof(int32_t) * (2 * c.L + 2 * nmax + 4) + sizeof(double) * (nmax + 5) + c.n_rec + c.N +
+               c.n_events + 64;
+    if (mixed)
+      b += sizeof(uint16_t) * (size_t)sstride + sizeof(unsigned long long) * (size_t)(2 * nmax) * (2 * nmax) +
+           sizeof(cx<double>) * (size_t)(4 * vstride) + (sizeof(unsigned) + sizeof(int)) * 2 * nmax + 64;
+    return b;
   }
 
   ttn_status alloc(int Bmax) {
@@ -2464,27 +2534,157 @@ struct Engine {
     dev.choice = dChoice;
     dev.n_events = std::max(1, c.n_events);
     dev.forced = 0;
+    dev.shape = nullptr;
+    dev.eig_nsplit = 0;
+    if (mixed) {
+      const size_t cs = 2 * (size_t)nmax;
+      CK(cudaMalloc(&dShape, sizeof(int2) * B));
+      CK(cudaMalloc(&dAmax, sizeof(unsigned) * cs * B));
+      CK(cudaMalloc(&dExpo, sizeof(int) * cs * B));
+      CK(cudaMalloc(&dSlices, sizeof(uint16_t) * (size_t)sstride * B));
+      CK(cudaMalloc(&dGfix, sizeof(unsigned long long) * cs * cs * B));
+      CK(cudaMalloc(&dG64, sizeof(cx<double>) * (size_t)vstride * B));
+      CK(cudaMalloc(&dV64, sizeof(cx<double>) * (size_t)vstride * B));
+      CK(cudaMalloc(&dTs64, sizeof(cx<double>) * (size_t)vstride * 2 * B));
+      // the Gram kernels leave these zero after every matrix
+      CK(cudaMemset(dAmax, 0, sizeof(unsigned) * cs * B));
+      CK(cudaMemset(dGfix, 0, sizeof(unsigned long long) * cs * cs * B));
+      dev.shape = dShape;
+      gargs.M = reinterpret_cast<const float2*>(dW);
+      gargs.mstride = wstride;
+      gargs.shape = dShape;
+      gargs.amax = dAmax;
+      gargs.expo = dExpo;
+      gargs.cstride = (int)cs;
+      gargs.slices = dSlices;
+      gargs.sstride = sstride;
+      gargs.gfix = dGfix;
+      gargs.gld = (int)cs;
+      gargs.G = reinterpret_cast<double2*>(dG64);
+      gargs.g64stride = vstride;
+      gargs.err = dErr;
+      gargs.ledger = dLedger;
+      gargs.ledger_class = KC_GRAM;
+    }
+    base = dev;
+    gbase = gargs;
+    b0 = 0;
     return TTN_OK;
+  }
+
+  // The FP64 eigensolvers' view of the batch (MIXED runs): the exact Gram
+  // matrices and FP64 scratch in place of the FP32 ones; bond dimensions,
+  // singular values, kept ranks and flags shared with the FP32 state.
+  Dev<double> view64() const {
+    Dev<double> v{};
+    v.off = dev.off;
+    v.ncap = dev.ncap;
+    v.tstride = dev.tstride;
+    v.dims = dev.dims;
+    v.ds = dev.ds;
+    v.wstride = dev.wstride;
+    v.G = dG64 + b0 * vstride;
+    v.V = dV64 + b0 * vstride;
+    v.Ts = dTs64 + b0 * 2 * vstride;
+    v.vstride = dev.vstride;
+    v.sv = dev.sv;
+    v.perm = dev.perm;
+    v.nmax = dev.nmax;
+    v.knew = dev.knew;
+    v.nold = dev.nold;
+    v.logp = dev.logp;
+    v.disc = dev.disc;
+    v.ties = dev.ties;
+    v.n_rec = dev.n_rec;
+    v.N = dev.N;
+    v.L = dev.L;
+    v.chi = dev.chi;
+    v.noise = dev.noise;
+    v.eps_gram = eps_mixed;
+    v.tol_gram = 1e-13;
+    v.tol_abs_gram = 1e-15;
+    v.max_sweeps = 40;
+    v.ledger = dev.ledger;
+    v.frob = dev.frob;
+    v.trunc = dev.trunc;
+    v.err = dev.err;
+    v.err_step = dev.err_step;
+    v.cur_step = dev.cur_step;
+    v.cur_trunc = dev.cur_trunc;
+    v.svd_mode = 2;
+    return v;
   }
 
   void release() {
     void* ptrs[] = {dT, dW, dV, dR, dG, dTs, dOff, dDims, dSv, dPerm, dK, dN, dLogp, dDisc, dTies, dRec,
                     dLast, dTheta, dGamma, dTraj, dErr, dErrStep, dFrob, dTrunc, dLeafdim, dOp1, dGroups,
-                    dLedger, dChoice};
+                    dLedger, dChoice, dShape, dAmax, dExpo, dSlices, dGfix, dG64, dV64, dTs64};
     for (void* p : ptrs)
       if (p) cudaFree(p);
   }
 
   // Launch the step program for trajectories [0, nb) of the batch.
   ttn_status launch(int nb, int stop_step) {
+    return launch_range(nb, 0, stop_step < 0 ? (int)prog.steps.size() : stop_step);
+  }
+
+  // Trajectories [b0, b0 + nb) of the batch on stream s: every later launch
+  // sees only that group (per-trajectory pointers shifted by b0).
+  void select_group(int64_t b0_, cudaStream_t s) {
+    b0 = b0_;
+    st = s;
+    dev = base;
+    Dev<R>& x = dev;
+    x.T += b0 * tstride;
+    x.dims += b0 * x.ds;
+    x.W += b0 * wstride;
+    x.V += b0 * vstride;
+    x.Rm += b0 * vstride;
+    x.G += b0 * vstride;
+    x.Ts += b0 * 2 * vstride;
+    x.sv += b0 * nmax;
+    x.perm += b0 * nmax;
+    x.knew += b0;
+    x.nold += b0;
+    x.logp += b0;
+    x.disc += b0;
+    x.ties += b0;
+    x.rec += b0 * c.n_rec;
+    x.last += b0 * c.N;
+    x.theta += b0;
+    x.gamma += b0;
+    x.traj += b0;
+    x.choice += b0 * x.n_events;
+    x.frob += b0;
+    x.trunc += b0;
+    x.err += b0;
+    x.err_step += 2 * b0;
+    if (x.shape) x.shape += b0;
+    if (mixed) {
+      gargs = gbase;
+      gargs.M += b0 * gbase.mstride;
+      gargs.shape += b0;
+      gargs.amax += b0 * gbase.cstride;
+      gargs.expo += b0 * gbase.cstride;
+      gargs.slices += b0 * gbase.sstride;
+      gargs.gfix += b0 * (int64_t)gbase.gld * gbase.gld;
+      gargs.G += b0 * gbase.g64stride;
+      gargs.err += b0;
+    }
+  }
+
+  // Steps [s0, s1) of the program for the selected group's first nb
+  // trajectories; s0 == 0 starts them from |0...0>.
+  ttn_status launch_range(int nb, int s0, int s1) {
     const int L = c.L;
-    dim3 gi(1, nb);
-    dev.cur_step = -1;
-    k_init<R><<<dim3(std::max(1, ceil_div(2 * L, 256)), nb), 256, 0, st>>>(dev, dLeafdim, nb);
-    CK(cudaGetLastError());
-    (void)gi;
-    const int nsteps = stop_step < 0 ? (int)prog.steps.size() : stop_step;
-    for (int si = 0; si < nsteps; ++si) {
+    if (s0 == 0) {
+      dev.cur_step = -1;
+      k_init<R><<<dim3(std::max(1, ceil_div(2 * L, 256)), nb), 256, 0, st>>>(dev, dLeafdim, nb);
+      CK(cudaGetLastError());
+      kernel_launches += 1;
+    }
+    const int nsteps = std::min<int>(s1, (int)prog.steps.size());
+    for (int si = s0; si < nsteps; ++si) {
       const Step& s = prog.steps[si];
       dev.cur_step = si;
       dev.cur_trunc = s.kind == S_MOVE ? s.c : 0;
@@ -2511,9 +2711,12 @@ struct Engine {
           for (int t = 0; t < 3; ++t)
             if (t != lv0) mcap *= cc3[t];
           const bool big = c.N > BIG_CIRCUIT_QUBITS || mcap * nmv >= BIG_MOVE;
-          const bool gram = dev.svd_mode >= 2 || (dev.svd_mode == 0 && sizeof(R) == 4 && (nmv > 64 || big));
+          const bool gram = mixed || dev.svd_mode >= 2 || (dev.svd_mode == 0 && sizeof(R) == 4 && (nmv > 64 || big));
           // contractions of this move on the tensor cores (FP32 only)
-          const bool tc = sizeof(R) == 4 && (gemm_mode == 2 || (gemm_mode == 0 && gram));
+          // MIXED: the FMA units unless tensor cores are asked for (the
+          // mma.sync 3xTF32 tile's truncating FP32 accumulation costs ~1e-5
+          // of amplitude accuracy over a syndrome round)
+          const bool tc = sizeof(R) == 4 && (gemm_mode == 2 || (gemm_mode == 0 && gram && !mixed));
           if (gram) {
             const int lv = (w == 2 * v) ? 0 : ((w == 2 * v + 1) ? 1 : 2);
             int64_t c3[3] = {2 * (int64_t)bcap[2 * v], 2 * (int64_t)bcap[2 * v + 1],
@@ -2523,11 +2726,30 @@ struct Engine {
               if (t != lv) mmax *= c3[t];
             timed(KC_COPY, [&] { k_gather_rows<R><<<dim3(std::max(1, ceil_div(ncap[v], 1024)), nb), 256, 0, st>>>(dev, v, w); });
             const int tn = std::max(1, ceil_div(nmv, 64));
+            if (mixed) {
+              // exact Gram matrix on the tensor cores, FP64 eigensolver
+              timed(KC_GRAM, 5, [&] { (void)gram_exact_launch(gargs, nb, (int)nmv, std::min<int64_t>(mmax, ncap[v]), st); });
+              // the solver is chosen per trajectory by its bond's actual
+              // dimension: cyclic Jacobi in shared memory up to EIG_JACOBI_N,
+              // the tridiagonal solver above (each kernel skips the others)
+              const bool both = nmv > EIG_JACOBI_N;
+              timed(KC_EIG, (sizeof(R) == 4 ? 2 : 1) + (both ? 1 : 0), [&] {
+                Dev<double> dv = view64();
+                dv.eig_nsplit = EIG_JACOBI_N;
+                dv.eig_smem_bytes = EIG_JACOBI_N * EIG_JACOBI_N * (int)sizeof(cx<double>);
+                k_eig<double><<<nb, 512, dv.eig_smem_bytes, st>>>(dv, v, w, kcap);
+                if (both) k_eig_tri<double><<<nb, 512, tri_smem_bytes<double>(), st>>>(dv, v, w, kcap);
+                if constexpr (sizeof(R) == 4) k_vk_to_float<<<nb, 256, 0, st>>>(dev, dG64 + b0 * vstride);
+              });
+            } else {
             timed(KC_GRAM, [&] {
               if (tc) k_gram<R, true><<<dim3(tn, tn, nb), 256, 0, st>>>(dev, v, w);
               else k_gram<R, false><<<dim3(tn, tn, nb), 256, 0, st>>>(dev, v, w);
             });
-            if (dev.svd_mode != 3 && !(dev.svd_mode == 0 && big) &&
+            }
+            if (mixed) {
+              // eigendecomposition done above
+            } else if (dev.svd_mode != 3 && !(dev.svd_mode == 0 && big) &&
                 nmv * nmv * (int64_t)sizeof(cx<R>) <= EIG_SMEM_MAX) {
               dev.eig_smem_bytes = (int)(nmv * nmv * (int64_t)sizeof(cx<R>));
               timed(KC_EIG, [&] { k_eig<R><<<nb, 512, dev.eig_smem_bytes, st>>>(dev, v, w, kcap); });
@@ -2539,7 +2761,7 @@ struct Engine {
               if (tc) k_form_u<R, true><<<gf, 256, 0, st>>>(dev, v, w);
               else k_form_u<R, false><<<gf, 256, 0, st>>>(dev, v, w);
             });
-            timed(KC_OTHER, [&] {
+            timed(KC_OTHER, 4, [&] {
               const int gx = (int)std::min<int64_t>(std::max<int64_t>(1, mmax * nmv / 4096), 512);
               k_unorm_zero<R><<<nb, 256, 0, st>>>(dev, nb);
               k_unorm_sums<R><<<dim3(gx, nb), 256, 0, st>>>(dev, v, w);
@@ -2565,7 +2787,7 @@ struct Engine {
           break;
         }
         case S_THREAD_LEAF: {
-          timed(KC_LOCAL, [&] {
+          timed(KC_LOCAL, 2, [&] {
             k_thread_leaf<R><<<dim3(std::max(1, ceil_div(ncap[s.a], 256)), nb), 256, 0, st>>>(
                 dev, s.a, s.b, s.c);
             k_thread_dims_leaf<R><<<ceil_div(nb, 128), 128, 0, st>>>(dev, s.a, nb);
@@ -2576,7 +2798,7 @@ struct Engine {
           break;
         }
         case S_THREAD_NODE: {
-          timed(KC_LOCAL, [&] {
+          timed(KC_LOCAL, 2, [&] {
             k_thread_node<R><<<dim3(std::max(1, ceil_div(ncap[s.a], 256)), nb), 256, 0, st>>>(
                 dev, s.a, s.b);
             // same dims update as the leaf step: only the node's up bond
@@ -2627,11 +2849,10 @@ struct Engine {
   }
 };
 
+// Numerical settings of an engine from a request (precision-dependent
+// tolerances, eigensolver shared-memory limits).
 template <typename R>
-static ttn_status run_impl(const ttn_circuit& c, const RunRequest& rq, RunOutputs& out) {
-  Program prog = compile_program(c, rq.noise, -1);
-  cudaStream_t st = (cudaStream_t)rq.stream;
-  Engine<R> eng(c, prog, rq.chi, rq.noise, st);
+static ttn_status configure(Engine<R>& eng, const RunRequest& rq) {
   eng.dev.seed = rq.seed;
   eng.dev.eps = rq.svd_eps;
   eng.dev.tie_eps = sizeof(R) == 8 ? 1e-9 : 1e-5;
@@ -2640,11 +2861,28 @@ static ttn_status run_impl(const ttn_circuit& c, const RunRequest& rq, RunOutput
   eng.dev.svd_mode = rq.svd_mode;
   eng.gemm_mode = rq.gemm_mode;
   eng.dev.eig_smem_bytes = 0;
+  eng.mixed = rq.precision == TTN_PREC_MIXED;
+  eng.eps_mixed = rq.svd_eps > 0 ? rq.svd_eps : 1e-6;
   CK(cudaFuncSetAttribute(k_eig<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, EIG_SMEM_MAX));
   CK(cudaFuncSetAttribute(k_eig_tri<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, tri_smem_bytes<R>()));
+  if (eng.mixed) {
+    CK(cudaFuncSetAttribute(k_eig<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, EIG_SMEM_MAX));
+    CK(cudaFuncSetAttribute(k_eig_tri<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            tri_smem_bytes<double>()));
+  }
   eng.dev.eps_gram = sizeof(R) == 8 ? 1e-7 : 1e-4;
   eng.dev.tol_gram = sizeof(R) == 8 ? 1e-13 : 3e-6;
   eng.dev.tol_abs_gram = sizeof(R) == 8 ? 1e-15 : 2e-7;
+  return TTN_OK;
+}
+
+template <typename R>
+static ttn_status run_impl(const ttn_circuit& c, const RunRequest& rq, RunOutputs& out) {
+  Program prog = compile_program(c, rq.noise, -1);
+  cudaStream_t st = (cudaStream_t)rq.stream;
+  Engine<R> eng(c, prog, rq.chi, rq.noise, st);
+  ttn_status cs = configure(eng, rq);
+  if (cs != TTN_OK) return cs;
   size_t freeb = 0, totb = 0;
   CK(cudaMemGetInfo(&freeb, &totb));
   const size_t per = eng.bytes_per_traj();
@@ -2755,28 +2993,15 @@ static ttn_status run_impl(const ttn_circuit& c, const RunRequest& rq, RunOutput
     CK(cudaStreamSynchronize(st));
     eng.collect_profile();
     for (int i = 0; i < nb; ++i) out.err_flags |= err[i];
-    // A trajectory whose state lost its norm (or became non-finite) is kept
-    // out of the statistics: its fail byte becomes 3 and the run goes on.
-    // Capacity overflows and failures in single-trajectory debug runs stay
-    // fatal.
-    bool fatal = (out.err_flags & ERR_CAPACITY) != 0 || (rq.debug_amps && (out.err_flags & (ERR_ZERO_NORM | ERR_NAN)));
-    if (!fatal && (out.err_flags & (ERR_ZERO_NORM | ERR_NAN))) {
-      static const uint8_t lost_byte = 3;
-      for (int i = 0; i < nb; ++i)
-        if (err[i] & (ERR_ZERO_NORM | ERR_NAN)) {
-          out.lost += 1;
-          if (out.fail)
-            CK(cudaMemcpyAsync(out.fail + t0 + i, &lost_byte, 1,
-                               out.on_device ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost, st));
-        }
-      CK(cudaStreamSynchronize(st));
-      out.err_flags &= ~(ERR_ZERO_NORM | ERR_NAN);
-    }
+    // Every error is fatal: a trajectory whose state lost its norm or became
+    // non-finite cannot be left out of p_L without biasing it (the loss
+    // depends on the state), so the run stops and names it.
+    const bool fatal = (out.err_flags & (ERR_CAPACITY | ERR_ZERO_NORM | ERR_NAN | GRAM_ERR_TIMEOUT)) != 0;
     if (fatal) {
       // first failing trajectory: which step of the program raised it
       std::string where;
       for (int i = 0; i < nb; ++i)
-        if (err[i] & (ERR_CAPACITY | ERR_ZERO_NORM | ERR_NAN)) {
+        if (err[i] & (ERR_CAPACITY | ERR_ZERO_NORM | ERR_NAN | GRAM_ERR_TIMEOUT)) {
           static const char* kinds[] = {"move", "thread-leaf", "thread-node", "thread-lca",
                                         "gate-node", "single-qubit layer", "measure", "damping"};
           where = " (trajectory " + std::to_string(rq.first_traj + t0 + i) + ", flags " + std::to_string(err[i]);
@@ -2792,10 +3017,14 @@ static ttn_status run_impl(const ttn_circuit& c, const RunRequest& rq, RunOutput
           break;
         }
       eng.release();
+      const int f = out.err_flags;
       set_error(std::string("engine: ") +
-                ((out.err_flags & ERR_CAPACITY) ? "tensor exceeded its slot capacity"
-                 : (out.err_flags & ERR_NAN) ? "non-finite singular value" : "zero-norm state") + where);
-      return TTN_ECUDA;
+                ((f & GRAM_ERR_TIMEOUT) ? "a bounded wait of the tensor-core Gram kernel expired"
+                 : (f & ERR_CAPACITY) ? "tensor exceeded its slot capacity"
+                 : (f & ERR_NAN) ? "non-finite value in a centre move" : "zero-norm state") + where);
+      if (f & GRAM_ERR_TIMEOUT) return TTN_ETIMEOUT;
+      if (f & ERR_CAPACITY) return TTN_ECUDA;
+      return TTN_ENUMERIC;
     }
   }
   eng.release();
@@ -2805,7 +3034,9 @@ static ttn_status run_impl(const ttn_circuit& c, const RunRequest& rq, RunOutput
 size_t run_bytes_per_traj(const ttn_circuit& c, const RunRequest& rq) {
   Program prog = compile_program(c, rq.noise, -1);
   if (rq.precision == TTN_PREC_FP64) return Engine<double>(c, prog, rq.chi, rq.noise, nullptr).bytes_per_traj();
-  return Engine<float>(c, prog, rq.chi, rq.noise, nullptr).bytes_per_traj();
+  Engine<float> e(c, prog, rq.chi, rq.noise, nullptr);
+  e.mixed = rq.precision == TTN_PREC_MIXED;
+  return e.bytes_per_traj();
 }
 
 // Worst case of the node-slot fill over the step program: every move keeps
@@ -2880,7 +3111,254 @@ void slot_check(const ttn_circuit& c, int noise, int chi, double* worst_fill, in
 
 ttn_status run_trajectories_device(const ttn_circuit& c, const RunRequest& rq, RunOutputs& out) {
   if (rq.precision == TTN_PREC_FP64) return run_impl<double>(c, rq, out);
+  // FP32 and MIXED: complex64 tensors (MIXED adds the FP64 centre)
   return run_impl<float>(c, rq, out);
 }
+
+}  // namespace ttn
+
+namespace ttn {
+
+// ------------------------------------------------------------------ pipelined resident batch
+// n_resident trajectories live on the device at once, in S groups of
+// G = n_resident / S.  The step program is cut into S segments of about
+// equal worst-case cost; group g holds trajectories that have run g segments
+// when the pipeline starts, and every pipeline step runs one segment of
+// every group, each group on its own stream.  The group that runs the last
+// segment is decoded and restarts with the next G trajectory indices, so
+// every step completes exactly G trajectories and all steps cost the same.
+struct PipelineImpl {
+  virtual ~PipelineImpl() {}
+  virtual ttn_status step(uint8_t* fail, double* log_prob, double* discarded, uint64_t* traj,
+                          int32_t* n_done, bool on_device, cudaStream_t caller) = 0;
+  virtual int group_size() const = 0;
+};
+
+template <typename R>
+struct PipelineT : PipelineImpl {
+  const ttn_circuit& c;
+  Program prog;
+  RunRequest rq;
+  Engine<R> eng;
+  int B = 0, S = 0, G = 0;
+  std::vector<int> seg;             // S + 1 step boundaries
+  std::vector<int> phase;           // next segment of each group
+  std::vector<uint64_t> first;      // first trajectory index of each group's trajectories
+  std::vector<cudaStream_t> streams;
+  std::vector<cudaEvent_t> ev;
+  cudaEvent_t ev_start = nullptr;
+  uint64_t next_traj = 0;
+  std::vector<double> theta_cycle;
+  double* h_theta = nullptr;        // pinned [B]
+  double* h_gamma = nullptr;
+  uint64_t* h_traj = nullptr;
+
+  PipelineT(const ttn_circuit& cc, const RunRequest& r)
+      : c(cc), prog(compile_program(cc, r.noise, -1)), rq(r), eng(cc, prog, r.chi, r.noise, nullptr) {}
+
+  ~PipelineT() override {
+    for (cudaStream_t x : streams) cudaStreamDestroy(x);
+    for (cudaEvent_t e : ev) cudaEventDestroy(e);
+    if (ev_start) cudaEventDestroy(ev_start);
+    if (h_theta) cudaFreeHost(h_theta);
+    if (h_gamma) cudaFreeHost(h_gamma);
+    if (h_traj) cudaFreeHost(h_traj);
+    eng.release();
+  }
+
+  int group_size() const override { return G; }
+
+  ttn_status create(int n_resident, int n_segments, const double* cycle, int n_cycle, cudaStream_t caller) {
+    S = n_segments;
+    B = n_resident;
+    G = B / S;
+    next_traj = rq.first_traj;
+    if (cycle && n_cycle > 0) theta_cycle.assign(cycle, cycle + n_cycle);
+    ttn_status s = configure(eng, rq);
+    if (s != TTN_OK) return s;
+    size_t freeb = 0, totb = 0;
+    CK(cudaMemGetInfo(&freeb, &totb));
+    size_t budget = (size_t)((double)freeb * 0.85);
+    if (rq.max_device_bytes > 0) budget = std::min(budget, rq.max_device_bytes);
+    if (eng.bytes_per_traj() * (size_t)B > budget) {
+      set_error("pipeline: " + std::to_string(B) + " resident trajectories need " +
+                std::to_string(eng.bytes_per_traj() * (size_t)B) + " device bytes; " + std::to_string(budget) +
+                " available");
+      return TTN_ENOMEM;
+    }
+    s = eng.alloc(B);
+    if (s != TTN_OK) return s;
+    // segments of about equal worst-case cost (moves: Gram + eigensolver
+    // of the capacity-sized bond matrix; other steps: one pass over a node)
+    std::vector<double> cost(prog.steps.size(), 1.0);
+    for (size_t i = 0; i < prog.steps.size(); ++i) {
+      const Step& st = prog.steps[i];
+      if (st.kind == S_MOVE) {
+        const int v = st.a, w = st.b;
+        const int bond = (w == v / 2) ? v : w;
+        const double nmv = 2.0 * eng.bcap[bond];
+        const double mm = (double)eng.ncap[v] / std::max(1.0, nmv);
+        cost[i] = mm * nmv * nmv + 12.0 * nmv * nmv * nmv;
+      } else if (st.kind == S_THREAD_LEAF || st.kind == S_THREAD_NODE || st.kind == S_THREAD_LCA) {
+        cost[i] = (double)eng.ncap[st.a];
+      }
+    }
+    double tot = 0.0;
+    for (double x : cost) tot += x;
+    seg.assign(S + 1, 0);
+    double acc = 0.0;
+    int k = 1;
+    for (size_t i = 0; i < prog.steps.size() && k < S; ++i) {
+      acc += cost[i];
+      if (acc >= tot * k / S) seg[k++] = (int)i + 1;
+    }
+    for (; k < S; ++k) seg[k] = (int)prog.steps.size();
+    seg[S] = (int)prog.steps.size();
+    for (int i = 1; i <= S; ++i) seg[i] = std::max(seg[i], seg[i - 1]);
+    streams.resize(S);
+    ev.resize(S);
+    for (int g = 0; g < S; ++g) {
+      CK(cudaStreamCreateWithFlags(&streams[g], cudaStreamNonBlocking));
+      CK(cudaEventCreateWithFlags(&ev[g], cudaEventDisableTiming));
+    }
+    CK(cudaEventCreateWithFlags(&ev_start, cudaEventDisableTiming));
+    CK(cudaMallocHost(&h_theta, sizeof(double) * B));
+    CK(cudaMallocHost(&h_gamma, sizeof(double) * B));
+    CK(cudaMallocHost(&h_traj, sizeof(uint64_t) * B));
+    phase.assign(S, 0);
+    first.assign(S, 0);
+    // ramp-up: group g runs segments 0 .. g-1
+    CK(cudaEventRecord(ev_start, caller));
+    for (int g = 0; g < S; ++g) CK(cudaStreamWaitEvent(streams[g], ev_start, 0));
+    for (int r = 0; r + 1 < S; ++r)
+      for (int g = r + 1; g < S; ++g) {
+        s = run_segment(g);
+        if (s != TTN_OK) return s;
+      }
+    for (int g = 0; g < S; ++g) CK(cudaStreamSynchronize(streams[g]));
+    s = check_errors();
+    eng.collect_profile();
+    return s;
+  }
+
+  ttn_status start_group(int g) {
+    first[g] = next_traj;
+    next_traj += (uint64_t)G;
+    for (int i = 0; i < G; ++i) {
+      const uint64_t t = first[g] + (uint64_t)i;
+      h_traj[g * G + i] = t;
+      h_theta[g * G + i] = theta_cycle.empty() ? rq.theta : theta_cycle[(size_t)(t % theta_cycle.size())];
+      h_gamma[g * G + i] = rq.gamma;
+    }
+    cudaStream_t st = streams[g];
+    CK(cudaMemcpyAsync(eng.dTraj + g * G, h_traj + g * G, sizeof(uint64_t) * G, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(eng.dTheta + g * G, h_theta + g * G, sizeof(double) * G, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(eng.dGamma + g * G, h_gamma + g * G, sizeof(double) * G, cudaMemcpyHostToDevice, st));
+    return TTN_OK;
+  }
+
+  // Next segment of group g on its stream.
+  ttn_status run_segment(int g) {
+    if (phase[g] == 0) {
+      ttn_status s = start_group(g);
+      if (s != TTN_OK) return s;
+    }
+    eng.select_group((int64_t)g * G, streams[g]);
+    ttn_status s = eng.launch_range(G, seg[phase[g]], seg[phase[g] + 1]);
+    phase[g] = (phase[g] + 1) % S;
+    return s;
+  }
+
+  ttn_status check_errors() {
+    std::vector<int32_t> err(B);
+    CK(cudaMemcpy(err.data(), eng.dErr, sizeof(int32_t) * B, cudaMemcpyDeviceToHost));
+    for (int i = 0; i < B; ++i) {
+      const int f = err[i];
+      if (!(f & (ERR_CAPACITY | ERR_ZERO_NORM | ERR_NAN | GRAM_ERR_TIMEOUT))) continue;
+      const int g = i / G;
+      set_error("pipeline: trajectory " + std::to_string(first[g] + (uint64_t)(i - g * G)) + ": " +
+                ((f & GRAM_ERR_TIMEOUT) ? "a bounded wait of the tensor-core Gram kernel expired"
+                 : (f & ERR_CAPACITY) ? "tensor exceeded its slot capacity"
+                 : (f & ERR_NAN) ? "non-finite value in a centre move" : "zero-norm state"));
+      if (f & GRAM_ERR_TIMEOUT) return TTN_ETIMEOUT;
+      if (f & ERR_CAPACITY) return TTN_ECUDA;
+      return TTN_ENUMERIC;
+    }
+    return TTN_OK;
+  }
+
+  ttn_status step(uint8_t* fail, double* log_prob, double* discarded, uint64_t* traj, int32_t* n_done,
+                  bool on_device, cudaStream_t caller) override {
+    CK(cudaEventRecord(ev_start, caller));
+    int done = -1;
+    for (int g = 0; g < S; ++g) {
+      CK(cudaStreamWaitEvent(streams[g], ev_start, 0));
+      if (phase[g] == S - 1) {
+        done = g;
+        continue;
+      }
+      ttn_status s = run_segment(g);
+      if (s != TTN_OK) return s;
+    }
+    ttn_status s = run_segment(done);  // the completing group last: its decode waits on it
+    if (s != TTN_OK) return s;
+    cudaStream_t st = streams[done];
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (log_prob) CK(cudaMemcpyAsync(log_prob, eng.dLogp + done * G, sizeof(double) * G, kind, st));
+    if (discarded) CK(cudaMemcpyAsync(discarded, eng.dDisc + done * G, sizeof(double) * G, kind, st));
+    int overflow = 0;
+    if (fail) {
+      s = decode_device(c, G, eng.dRec + (size_t)done * G * c.n_rec, fail, nullptr, nullptr, st, on_device);
+      if (s == TTN_EOVERFLOW) overflow = 1;
+      else if (s != TTN_OK) return s;
+    }
+    for (int g = 0; g < S; ++g) {
+      CK(cudaEventRecord(ev[g], streams[g]));
+      CK(cudaStreamWaitEvent(caller, ev[g], 0));
+    }
+    CK(cudaStreamSynchronize(caller));
+    if (traj)
+      for (int i = 0; i < G; ++i) traj[i] = first[done] + (uint64_t)i;
+    if (n_done) *n_done = G;
+    s = check_errors();
+    eng.collect_profile();
+    if (s != TTN_OK) return s;
+    if (overflow) {
+      set_error("decoder: shot(s) exceeded the matching bound (fail byte 2)");
+      return TTN_EOVERFLOW;
+    }
+    return TTN_OK;
+  }
+};
+
+ttn_status pipeline_create(const ttn_circuit& c, const RunRequest& rq, int n_resident, int n_segments,
+                           const double* theta_cycle, int n_theta, void* stream, PipelineImpl** out) {
+  PipelineImpl* p = nullptr;
+  ttn_status s;
+  if (rq.precision == TTN_PREC_FP64) {
+    auto* q = new PipelineT<double>(c, rq);
+    p = q;
+    s = q->create(n_resident, n_segments, theta_cycle, n_theta, (cudaStream_t)stream);
+  } else {
+    auto* q = new PipelineT<float>(c, rq);
+    p = q;
+    s = q->create(n_resident, n_segments, theta_cycle, n_theta, (cudaStream_t)stream);
+  }
+  if (s != TTN_OK) {
+    delete p;
+    return s;
+  }
+  *out = p;
+  return TTN_OK;
+}
+
+ttn_status pipeline_step(PipelineImpl* p, uint8_t* fail, double* log_prob, double* discarded, uint64_t* traj,
+                         int32_t* n_done, bool on_device, void* stream) {
+  return p->step(fail, log_prob, discarded, traj, n_done, on_device, (cudaStream_t)stream);
+}
+
+int pipeline_group_size(const PipelineImpl* p) { return p->group_size(); }
+
+void pipeline_free(PipelineImpl* p) { delete p; }
 
 }  // namespace ttn

@@ -50,10 +50,13 @@ enum KernelClass { KC_SVD = 0, KC_GRAM = 1, KC_EIG = 2, KC_FORMU = 3, KC_ABSORB 
 static constexpr int EIG_PHASES = 6;
 // Move-shape histogram of the profiling ledger: for every centre move
 // (truncating or not) and bond dimension n before the move (clamped to
-// MOVE_HIST_N - 1): number of moves, sum of m (rows of the bond matrix) and
-// sum of the kept rank k, summed over trajectories.
+// MOVE_HIST_N - 1): number of moves, sum of m (rows of the bond matrix), sum
+// of the kept rank k and SM cycles the Gram eigensolver spent on them (thread
+// 0's clock from kernel entry to the rank selection), summed over
+// trajectories.
 static constexpr int MOVE_HIST_N = 513;
-static constexpr int MOVE_HIST_WORDS = 2 * MOVE_HIST_N * 3;
+static constexpr int MOVE_HIST_F = 4;
+static constexpr int MOVE_HIST_WORDS = 2 * MOVE_HIST_N * MOVE_HIST_F;
 
 // Process-wide profiling state: while active, every run adds algorithmic
 // flops/bytes per class to `ledger`, and launches of class `timed_class`
@@ -70,6 +73,7 @@ struct Profile {
   double class_ms[NCLASS] = {0};
   double eig_phase_cycles[EIG_PHASES] = {0};
   double move_hist[MOVE_HIST_WORDS] = {0};
+  uint64_t kernels = 0;          // kernel launches of the library (every class, decoder included)
 };
 Profile& profile();
 
@@ -91,6 +95,15 @@ ttn_status decode_device(const ttn_circuit& c, int nb, const uint8_t* d_records,
 // Allocation-free decoding with static device scratch (device pointers).
 ttn_status decode_noalloc(const ttn_circuit& c, uint64_t n, const uint8_t* d_records, uint8_t* d_fail,
                           int32_t* d_color, int64_t* d_score, void* stream);
+
+// Pipelined resident batch (see engine.cu).
+struct PipelineImpl;
+ttn_status pipeline_create(const ttn_circuit& c, const RunRequest& rq, int n_resident, int n_segments,
+                           const double* theta_cycle, int n_theta, void* stream, PipelineImpl** out);
+ttn_status pipeline_step(PipelineImpl* p, uint8_t* fail, double* log_prob, double* discarded, uint64_t* traj,
+                         int32_t* n_done, bool on_device, void* stream);
+int pipeline_group_size(const PipelineImpl* p);
+void pipeline_free(PipelineImpl* p);
 
 ttn_status philox_uniforms_device(uint64_t seed, const uint64_t* trajs, uint64_t n_traj,
                                   const int32_t* events, int32_t n_events, double* out);
