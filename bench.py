@@ -2,7 +2,7 @@
 
 Workload: d = 7 color code, 7 rounds, SRX with theta swept over 8 values in
 [0.01, 0.15] rad (trajectory t at theta_(t mod 8)), chi = 128, MIXED
-precision (complex64 tensors, 3xTF32 contractions, FP64 isometry-centre
+precision (complex64 tensors and contractions, FP64 isometry-centre
 factorisations, FP64 probabilities).  Inputs are synthetic and seeded (the
 paper's workloads are themselves synthetic circuits).
 
@@ -224,6 +224,10 @@ def roofline(a, prof, cls):
             "per_launch_ms": ms / max(1, prof["launches"][cls]), "peak_source": psrc}
 
 
+def note(msg):
+    print("[bench] " + msg, file=sys.stderr, flush=True)
+
+
 def main():
     a = parse()
     if a.impl == "reference":
@@ -251,6 +255,7 @@ def main():
     torch.cuda.synchronize()
     fill_s = time.perf_counter() - t_fill
     G = pipe.group_size
+    note("pipeline filled in %.1f s (%d resident, %d per step)" % (fill_s, a.resident, G))
     K, W = a.steps, a.warmup
     fails = torch.zeros(K * G, dtype=torch.uint8, device=dev)
     logp = torch.zeros(K * G, dtype=torch.float64, device=dev)
@@ -260,8 +265,10 @@ def main():
     P.profile_begin("all")
     wout = dict(fail=torch.zeros(G, dtype=torch.uint8, device=dev),
                 log_prob=torch.zeros(G, dtype=torch.float64, device=dev))
-    for _ in range(W):
+    for i in range(W):
+        t1 = time.perf_counter()
         pipe.step(wout, stream=stream.cuda_stream)
+        note("warm-up step %d: %.1f s" % (i, time.perf_counter() - t1))
     torch.cuda.synchronize()
     wprof = P.profile_end()
     cms = wprof["class_ms"]
@@ -278,11 +285,16 @@ def main():
     e0.record(stream)
     for k in range(K):
         sl = slice(k * G, (k + 1) * G)
+        t1 = time.perf_counter()
         r = pipe.step(dict(fail=fails[sl], log_prob=logp[sl], discarded=disc[sl]), stream=stream.cuda_stream)
         trajs.append(r["traj"])
+        seg_ms = pipe.segment_ms()
+        note("timed step %d: %.1f s; segments (s): %s" % (k, time.perf_counter() - t1,
+                                                       " ".join("%.1f" % (x / 1e3) for x in seg_ms)))
     e1.record(stream)
     torch.cuda.synchronize()
     prof = P.profile_end()
+    seg_ms = [round(x / 1e3, 2) for x in pipe.segment_ms()]
     ck = clocks.stop()
     ms = e0.elapsed_time(e1)
     if dist:
@@ -326,10 +338,11 @@ def main():
             "config": run_config(a),
             "clocks": ck, "e2e": e2e, "gpu_launches": int(prof["kernels"]),
             "roofline": roofline(a, prof, dom),
-            "fill_s": fill_s,
+            "fill_s": fill_s, "segment_s_last_step": seg_ms,
             "device_ms_by_class_warmup": {k: round(v, 1) for k, v in cms.items()},
             "ledger_tflop_per_traj": {k: v / 1e12 / max(1, K * G) for k, v in prof["flops"].items()},
             "pL_by_theta": pl,
+            "eig_phase_Gcycles": {k: round(v / 1e9, 2) for k, v in prof["eig_phase_cycles"].items()},
             "mean_log_prob": float(logp.cpu().numpy().mean()), "mean_discarded": float(disc.cpu().numpy().mean())}
     if not a.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(a)

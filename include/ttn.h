@@ -358,6 +358,10 @@ ttn_status ttn_pipeline_step(ttn_pipeline* pipeline, uint8_t* logical_fail, doub
                              void* cuda_stream);
 /* G, the trajectories each step completes (0 for NULL). */
 int32_t ttn_pipeline_group_size(const ttn_pipeline* pipeline);
+/* Device time (ms, CUDA events on the group's stream) each segment took in
+ * the last step, ms[0 .. n_segments); returns n_segments (0 for NULL).  The
+ * slowest segment sets a step's duration. */
+int32_t ttn_pipeline_segment_ms(const ttn_pipeline* pipeline, double* ms);
 void ttn_pipeline_free(ttn_pipeline* pipeline);
 
 /* Exact Gram matrix G = M^H M of one complex64 matrix on the tensor cores:

@@ -115,7 +115,8 @@ def run_trajectory(circ, model, theta, gamma, seed, traj, snapshot_layers=()):
 
     Returns dict(rec = uint8 record [syndrome bits | data bits], logp,
     margin = min |u - p| over compared draws, states = {layer: amplitudes
-    after that layer}).
+    after that layer}, branch_p = probability of every sampled branch, in
+    event order (their logarithms sum to logp)).
     """
     N = circ.n_qubits
     sv = StateVector(N)
@@ -124,6 +125,7 @@ def run_trajectory(circ, model, theta, gamma, seed, traj, snapshot_layers=()):
     logp = 0.0
     margin = math.inf
     states = {}
+    branch_p = []
     snap = set(snapshot_layers)
     events = [op[3] for op in circ.ops if op[3] >= 0]
     us = dict(zip(events, philox.uniforms(seed, [traj], events)[0])) if events else {}
@@ -152,6 +154,7 @@ def run_trajectory(circ, model, theta, gamma, seed, traj, snapshot_layers=()):
             pm = p1 if m else p0
             sv.project(a, m, pm)
             logp += math.log(pm)
+            branch_p.append(pm)
             rec[r] = m
             last[a] = m
         elif kind == NOISE:
@@ -159,9 +162,10 @@ def run_trajectory(circ, model, theta, gamma, seed, traj, snapshot_layers=()):
             logp += lp
             if dist is not None:
                 margin = min(margin, dist)
+                branch_p.append(math.exp(lp))
     if cur_layer in snap:
         states[cur_layer] = sv.amplitudes()
-    return dict(rec=rec, logp=logp, margin=margin, states=states, sv=sv)
+    return dict(rec=rec, logp=logp, margin=margin, states=states, sv=sv, branch_p=branch_p)
 
 
 def run_trajectories(circ, model, theta, gamma, seed, trajs):

@@ -42,7 +42,7 @@ EXPORTS = ["ttn_build_circuit", "ttn_free_circuit", "ttn_circuit_info", "ttn_cir
            "ttn_debug_state", "ttn_philox_uniforms", "ttn_profile_begin", "ttn_profile_end",
            "ttn_grad", "ttn_decode_noalloc", "ttn_profile_class_ms", "ttn_profile_eig_phases",
            "ttn_profile_move_hist", "ttn_gram_exact", "ttn_pipeline_create", "ttn_pipeline_step",
-           "ttn_pipeline_group_size", "ttn_pipeline_free", "ttn_profile_kernels",
+           "ttn_pipeline_group_size", "ttn_pipeline_free", "ttn_profile_kernels", "ttn_pipeline_segment_ms",
            "ttn_run_mixed", "ttn_newton_crossing", "ttn_crossing", "ttn_threshold_fit", "ttn_grad_sums",
            "ttn_slot_check", "ttn_layout_noise_free_chi",
            "ttn_status_string",
@@ -99,6 +99,8 @@ def load_library():
     lib.ttn_pipeline_group_size.argtypes = [vp]
     lib.ttn_pipeline_group_size.restype = ctypes.c_int32
     lib.ttn_pipeline_free.argtypes = [vp]
+    lib.ttn_pipeline_segment_ms.argtypes = [vp, c_dblp]
+    lib.ttn_pipeline_segment_ms.restype = ctypes.c_int32
     lib.ttn_profile_kernels.argtypes = [ctypes.POINTER(ctypes.c_uint64)]
     lib.ttn_pipeline_free.restype = None
     lib.ttn_debug_state.argtypes = [vp, ctypes.POINTER(RunParams), ctypes.c_uint64, ctypes.c_int32,
@@ -294,6 +296,12 @@ class Pipeline:
         res = dict(res)
         res["traj"] = traj[:nd.value]
         return res
+
+    def segment_ms(self):
+        """Device milliseconds of each segment in the last step."""
+        buf = np.zeros(1024)
+        n = self._lib.ttn_pipeline_segment_ms(self.handle, buf.ctypes.data_as(c_dblp))
+        return buf[:n].copy()
 
     def close(self):
         if getattr(self, "handle", None):

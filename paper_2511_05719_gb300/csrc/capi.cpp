@@ -857,6 +857,11 @@ int32_t ttn_pipeline_group_size(const ttn_pipeline* p) {
   return p ? ttn::pipeline_group_size(reinterpret_cast<const ttn::PipelineImpl*>(p)) : 0;
 }
 
+int32_t ttn_pipeline_segment_ms(const ttn_pipeline* p, double* ms) {
+  if (!p || !ms) return 0;
+  return ttn::pipeline_segment_ms(reinterpret_cast<const ttn::PipelineImpl*>(p), ms);
+}
+
 void ttn_pipeline_free(ttn_pipeline* p) {
   if (p) ttn::pipeline_free(reinterpret_cast<ttn::PipelineImpl*>(p));
 }

@@ -135,6 +135,8 @@ struct Dev {
   int cur_step;          // step of the program being launched
   int cur_trunc;         // 1 if that step is a truncating move
   int eig_nsplit;        // > 0: k_eig takes bonds n <= eig_nsplit, k_eig_tri the larger ones
+  int defer_bt;          // 1: k_eig_tri leaves the back-transformation to k_eig_bt (reflectors in
+                         //    G, phases and tau in V, Z in Ts)
   int2* shape;           // [B] (m, n) of the current move's bond matrix (MIXED runs)
 };
 
@@ -1606,6 +1608,14 @@ __global__ void __launch_bounds__(512) k_eig_tri(Dev<R> d, int v, int w, int kca
   __syncthreads();
 
   phase_mark(4);
+  if (d.defer_bt) {
+    // phases D and reflector scalars for k_eig_bt; Z and the reflectors stay put
+    for (int x = tid; x < n; x += nth) {
+      Vk[x] = wk[x];
+      Vk[n + x] = {x < n - 2 ? tau[x] : R(0), R(0)};
+    }
+    return;
+  }
   // ---- 5. back-transformation V_k = H_0 ... H_{n-3} D Z_k (n x k in Vk),
   // TRI_NB reflectors at a time in compact WY form (Schreiber & Van Loan):
   // H_j0 ... H_j1 = I - Vb Tb Vb^H, so Vk <- Vk - Vb (Tb (Vb^H Vk)).
@@ -1811,13 +1821,72 @@ __global__ void __launch_bounds__(256) k_unorm_apply(Dev<R> d, int v, int w) {
   }
 }
 
+// Back-transformation of the tridiagonal solver's eigenvectors, spread over
+// CTAs (MIXED runs): V_k = H_0 ... H_{n-3} D Z_k with H_j = I - tau_j v_j
+// v_j^H (v_j below the diagonal of column j of the reduced matrix), each CTA
+// applying all reflectors to BT_COLS kept columns in FP64 in shared memory,
+// then rounding V_k to complex64 (row-major n x k) for Y = M V_k.  The single
+// CTA of k_eig_tri would apply them to all k columns itself; here the k
+// columns take k / BT_COLS SMs at once.
+static constexpr int BT_COLS = 16;
+__global__ void __launch_bounds__(256) k_eig_bt(Dev<float> df, Dev<double> dv) {
+  const int b = blockIdx.y;
+  const int n = dv.nold[b], k = dv.knew[b];
+  if (n <= dv.eig_nsplit || k <= 0 || n > 512 || (int64_t)n * k > dv.vstride) return;
+  const int c0 = blockIdx.x * BT_COLS;
+  if (c0 >= k) return;
+  const int nc = min(BT_COLS, k - c0);
+  const int tid = threadIdx.x, col = tid & (BT_COLS - 1), part = tid >> 4;  // 16 columns x 16 row parts
+  extern __shared__ __align__(16) unsigned char bt_smem[];
+  cx<double>* X = reinterpret_cast<cx<double>*>(bt_smem);   // [n][BT_COLS]
+  cx<double>* vj = X + (int64_t)n * BT_COLS;                 // [n] current reflector
+  cx<double>* red = vj + n;                                  // [16][BT_COLS] partial dots
+  const cx<double>* A = dv.G + (int64_t)b * dv.vstride;
+  const double* Z = reinterpret_cast<const double*>(dv.Ts + (int64_t)b * 2 * dv.vstride);
+  const cx<double>* D = dv.V + (int64_t)b * dv.vstride;
+  const cx<double>* tau = D + n;
+  for (int idx = tid; idx < n * BT_COLS; idx += blockDim.x) {
+    const int x = idx / BT_COLS, c = idx - x * BT_COLS;
+    const double z = c < nc ? Z[(int64_t)(c0 + c) * n + x] : 0.0;
+    X[idx] = {D[x].x * z, D[x].y * z};
+  }
+  for (int j = n - 3; j >= 0; --j) {
+    const double tj = tau[j].x;
+    if (tj == 0.0) continue;  // uniform: every thread reads the same tau
+    __syncthreads();
+    for (int r = j + 1 + tid; r < n; r += blockDim.x) vj[r] = A[(int64_t)r * n + j];
+    __syncthreads();
+    cx<double> acc = {0.0, 0.0};
+    for (int r = j + 1 + part; r < n; r += 16) acc = cadd(acc, cmulc(vj[r], X[r * BT_COLS + col]));
+    red[part * BT_COLS + col] = acc;
+    __syncthreads();
+    cx<double> w = {0.0, 0.0};
+#pragma unroll
+    for (int q = 0; q < 16; ++q) w = cadd(w, red[q * BT_COLS + col]);
+    w = cscale(w, tj);
+    for (int r = j + 1 + part; r < n; r += 16) {
+      const cx<double> t = cmul(vj[r], w);
+      cx<double>& xr = X[r * BT_COLS + col];
+      xr = {xr.x - t.x, xr.y - t.y};
+    }
+  }
+  __syncthreads();
+  cx<float>* out = df.G + (int64_t)b * df.vstride;
+  for (int idx = tid; idx < n * BT_COLS; idx += blockDim.x) {
+    const int x = idx / BT_COLS, c = idx - x * BT_COLS;
+    if (c < nc) out[(int64_t)x * k + c0 + c] = {(float)X[idx].x, (float)X[idx].y};
+  }
+}
+
+static constexpr int bt_smem_bytes() { return (512 * BT_COLS + 512 + 16 * BT_COLS) * (int)sizeof(cx<double>); }
+
 // MIXED runs: the FP64 eigensolver leaves V_k (n x k, row-major, complex128)
 // in its Gram buffer; the tensor-core contraction Y = M V_k takes it in
 // complex64.
-__global__ void k_vk_to_float(Dev<float> d, const cx<double>* G64) {
+__global__ void k_vk_to_float(Dev<float> d, const cx<double>* G64, int nmax_here) {
   const int b = blockIdx.x;
   const int n = d.nold[b], k = d.knew[b];
-  if (k <= 0 || (int64_t)n * k > d.vstride) return;
+  if (k <= 0 || n > nmax_here || (int64_t)n * k > d.vstride) return;  // larger: k_eig_bt's output
   const cx<double>* src = G64 + (int64_t)b * d.vstride;
   cx<float>* dst = d.G + (int64_t)b * d.vstride;
   for (int i = threadIdx.x; i < n * k; i += blockDim.x) dst[i] = {(float)src[i].x, (float)src[i].y};
@@ -2371,7 +2440,12 @@ struct Engine {
 
   void collect_profile() {
     Profile& pf = profile();
-    if (!pf.active) return;
+    if (!pf.active) {
+      if (dLedger) cudaMemset(dLedger, 0, sizeof(unsigned long long) * LEDGER_WORDS);
+      for (int c = 0; c < NCLASS; ++c) class_launches[c] = 0;
+      kernel_launches = 0;
+      return;
+    }
     for (size_t i = 0; i < events.size(); ++i) {
       auto& e = events[i];
       float ms = 0.f;
@@ -2478,10 +2552,10 @@ struct Engine {
     CK(cudaMalloc(&dFrob, sizeof(double) * B));
     CK(cudaMalloc(&dTrunc, sizeof(int32_t) * B));
     CK(cudaMalloc(&dChoice, (size_t)std::max(1, c.n_events) * B));
-    if (profile().active) {
-      CK(cudaMalloc(&dLedger, sizeof(unsigned long long) * LEDGER_WORDS));
-      CK(cudaMemset(dLedger, 0, sizeof(unsigned long long) * LEDGER_WORDS));
-    }
+    // the ledger is always kept (one atomic add per kernel and trajectory);
+    // collect_profile hands it to an active profile and clears it
+    CK(cudaMalloc(&dLedger, sizeof(unsigned long long) * LEDGER_WORDS));
+    CK(cudaMemset(dLedger, 0, sizeof(unsigned long long) * LEDGER_WORDS));
     CK(cudaMalloc(&dLeafdim, sizeof(int32_t) * c.L));
     CK(cudaMalloc(&dOp1, sizeof(Op1) * std::max<size_t>(1, prog.op1.size())));
     CK(cudaMalloc(&dGroups, sizeof(Group1) * std::max<size_t>(1, prog.groups.size())));
@@ -2733,13 +2807,19 @@ struct Engine {
               // dimension: cyclic Jacobi in shared memory up to EIG_JACOBI_N,
               // the tridiagonal solver above (each kernel skips the others)
               const bool both = nmv > EIG_JACOBI_N;
-              timed(KC_EIG, (sizeof(R) == 4 ? 2 : 1) + (both ? 1 : 0), [&] {
+              timed(KC_EIG, (sizeof(R) == 4 ? 2 : 1) + (both ? 2 : 0), [&] {
                 Dev<double> dv = view64();
                 dv.eig_nsplit = EIG_JACOBI_N;
                 dv.eig_smem_bytes = EIG_JACOBI_N * EIG_JACOBI_N * (int)sizeof(cx<double>);
+                dv.defer_bt = sizeof(R) == 4 ? 1 : 0;
                 k_eig<double><<<nb, 512, dv.eig_smem_bytes, st>>>(dv, v, w, kcap);
                 if (both) k_eig_tri<double><<<nb, 512, tri_smem_bytes<double>(), st>>>(dv, v, w, kcap);
-                if constexpr (sizeof(R) == 4) k_vk_to_float<<<nb, 256, 0, st>>>(dev, dG64 + b0 * vstride);
+                if constexpr (sizeof(R) == 4) {
+                  k_vk_to_float<<<nb, 256, 0, st>>>(dev, dG64 + b0 * vstride, EIG_JACOBI_N);
+                  if (both)
+                    k_eig_bt<<<dim3((unsigned)ceil_div(std::min<int64_t>(kcap, nmv), BT_COLS), nb), 256,
+                               bt_smem_bytes(), st>>>(dev, dv);
+                }
               });
             } else {
             timed(KC_GRAM, [&] {
@@ -2866,6 +2946,7 @@ static ttn_status configure(Engine<R>& eng, const RunRequest& rq) {
   CK(cudaFuncSetAttribute(k_eig<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, EIG_SMEM_MAX));
   CK(cudaFuncSetAttribute(k_eig_tri<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, tri_smem_bytes<R>()));
   if (eng.mixed) {
+    CK(cudaFuncSetAttribute(k_eig_bt, cudaFuncAttributeMaxDynamicSharedMemorySize, bt_smem_bytes()));
     CK(cudaFuncSetAttribute(k_eig<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, EIG_SMEM_MAX));
     CK(cudaFuncSetAttribute(k_eig_tri<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                             tri_smem_bytes<double>()));
@@ -3132,6 +3213,7 @@ struct PipelineImpl {
   virtual ttn_status step(uint8_t* fail, double* log_prob, double* discarded, uint64_t* traj,
                           int32_t* n_done, bool on_device, cudaStream_t caller) = 0;
   virtual int group_size() const = 0;
+  virtual int segment_ms(double* ms) const = 0;
 };
 
 template <typename R>
@@ -3145,7 +3227,9 @@ struct PipelineT : PipelineImpl {
   std::vector<int> phase;           // next segment of each group
   std::vector<uint64_t> first;      // first trajectory index of each group's trajectories
   std::vector<cudaStream_t> streams;
-  std::vector<cudaEvent_t> ev;
+  std::vector<cudaEvent_t> ev, ev_a, ev_b;  // ev_a / ev_b bracket each group's segment (timing)
+  std::vector<int> timed_seg;               // segment each group ran in the last step
+  std::vector<double> seg_ms;               // device time of each segment in the last step
   cudaEvent_t ev_start = nullptr;
   uint64_t next_traj = 0;
   std::vector<double> theta_cycle;
@@ -3159,6 +3243,8 @@ struct PipelineT : PipelineImpl {
   ~PipelineT() override {
     for (cudaStream_t x : streams) cudaStreamDestroy(x);
     for (cudaEvent_t e : ev) cudaEventDestroy(e);
+    for (cudaEvent_t e : ev_a) cudaEventDestroy(e);
+    for (cudaEvent_t e : ev_b) cudaEventDestroy(e);
     if (ev_start) cudaEventDestroy(ev_start);
     if (h_theta) cudaFreeHost(h_theta);
     if (h_gamma) cudaFreeHost(h_gamma);
@@ -3167,6 +3253,10 @@ struct PipelineT : PipelineImpl {
   }
 
   int group_size() const override { return G; }
+  int segment_ms(double* ms) const override {
+    for (int i = 0; i < S; ++i) ms[i] = seg_ms[i];
+    return S;
+  }
 
   ttn_status create(int n_resident, int n_segments, const double* cycle, int n_cycle, cudaStream_t caller) {
     S = n_segments;
@@ -3217,9 +3307,15 @@ struct PipelineT : PipelineImpl {
     for (int i = 1; i <= S; ++i) seg[i] = std::max(seg[i], seg[i - 1]);
     streams.resize(S);
     ev.resize(S);
+    ev_a.resize(S);
+    ev_b.resize(S);
+    timed_seg.assign(S, -1);
+    seg_ms.assign(S, 0.0);
     for (int g = 0; g < S; ++g) {
       CK(cudaStreamCreateWithFlags(&streams[g], cudaStreamNonBlocking));
       CK(cudaEventCreateWithFlags(&ev[g], cudaEventDisableTiming));
+      CK(cudaEventCreate(&ev_a[g]));
+      CK(cudaEventCreate(&ev_b[g]));
     }
     CK(cudaEventCreateWithFlags(&ev_start, cudaEventDisableTiming));
     CK(cudaMallocHost(&h_theta, sizeof(double) * B));
@@ -3230,11 +3326,12 @@ struct PipelineT : PipelineImpl {
     // ramp-up: group g runs segments 0 .. g-1
     CK(cudaEventRecord(ev_start, caller));
     for (int g = 0; g < S; ++g) CK(cudaStreamWaitEvent(streams[g], ev_start, 0));
-    for (int r = 0; r + 1 < S; ++r)
-      for (int g = r + 1; g < S; ++g) {
-        s = run_segment(g);
-        if (s != TTN_OK) return s;
-      }
+    for (int r = 0; r + 1 < S; ++r) {
+      std::vector<int> gs;
+      for (int g = r + 1; g < S; ++g) gs.push_back(g);
+      s = run_segments(gs);
+      if (s != TTN_OK) return s;
+    }
     for (int g = 0; g < S; ++g) CK(cudaStreamSynchronize(streams[g]));
     s = check_errors();
     eng.collect_profile();
@@ -3257,17 +3354,45 @@ struct PipelineT : PipelineImpl {
     return TTN_OK;
   }
 
-  // Next segment of group g on its stream.
-  ttn_status run_segment(int g) {
-    if (phase[g] == 0) {
-      ttn_status s = start_group(g);
-      if (s != TTN_OK) return s;
+  // Next segment of each group in `gs`, each on its own stream.  The groups'
+  // launches are interleaved a few program steps at a time: a segment is tens
+  // of thousands of launches, and a stream whose launch queue is full blocks
+  // the host, so enqueueing one group's segment whole would hold back the
+  // others until it had nearly finished.
+  ttn_status run_segments(const std::vector<int>& gs) {
+    std::vector<int> cur(gs.size()), end(gs.size());
+    for (size_t i = 0; i < gs.size(); ++i) {
+      const int g = gs[i];
+      if (phase[g] == 0) {
+        ttn_status s = start_group(g);
+        if (s != TTN_OK) return s;
+      }
+      cur[i] = seg[phase[g]];
+      end[i] = seg[phase[g] + 1];
+      timed_seg[g] = phase[g];
+      CK(cudaEventRecord(ev_a[g], streams[g]));
     }
-    eng.select_group((int64_t)g * G, streams[g]);
-    ttn_status s = eng.launch_range(G, seg[phase[g]], seg[phase[g] + 1]);
-    phase[g] = (phase[g] + 1) % S;
-    return s;
+    static constexpr int CHUNK = 16;  // program steps per group per turn
+    for (bool more = true; more;) {
+      more = false;
+      for (size_t i = 0; i < gs.size(); ++i) {
+        if (cur[i] >= end[i]) continue;
+        const int hi = std::min(end[i], cur[i] + CHUNK);
+        eng.select_group((int64_t)gs[i] * G, streams[gs[i]]);
+        ttn_status s = eng.launch_range(G, cur[i], hi);
+        if (s != TTN_OK) return s;
+        cur[i] = hi;
+        more = more || cur[i] < end[i];
+      }
+    }
+    for (int g : gs) {
+      CK(cudaEventRecord(ev_b[g], streams[g]));
+      phase[g] = (phase[g] + 1) % S;
+    }
+    return TTN_OK;
   }
+
+  ttn_status run_segment(int g) { return run_segments(std::vector<int>{g}); }
 
   ttn_status check_errors() {
     std::vector<int32_t> err(B);
@@ -3291,16 +3416,13 @@ struct PipelineT : PipelineImpl {
                   bool on_device, cudaStream_t caller) override {
     CK(cudaEventRecord(ev_start, caller));
     int done = -1;
+    std::vector<int> gs;
     for (int g = 0; g < S; ++g) {
       CK(cudaStreamWaitEvent(streams[g], ev_start, 0));
-      if (phase[g] == S - 1) {
-        done = g;
-        continue;
-      }
-      ttn_status s = run_segment(g);
-      if (s != TTN_OK) return s;
+      if (phase[g] == S - 1) done = g;
+      gs.push_back(g);
     }
-    ttn_status s = run_segment(done);  // the completing group last: its decode waits on it
+    ttn_status s = run_segments(gs);
     if (s != TTN_OK) return s;
     cudaStream_t st = streams[done];
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
@@ -3317,6 +3439,11 @@ struct PipelineT : PipelineImpl {
       CK(cudaStreamWaitEvent(caller, ev[g], 0));
     }
     CK(cudaStreamSynchronize(caller));
+    for (int g = 0; g < S; ++g) {
+      float ms = 0.f;
+      if (timed_seg[g] >= 0 && cudaEventElapsedTime(&ms, ev_a[g], ev_b[g]) == cudaSuccess)
+        seg_ms[timed_seg[g]] = ms;
+    }
     if (traj)
       for (int i = 0; i < G; ++i) traj[i] = first[done] + (uint64_t)i;
     if (n_done) *n_done = G;
@@ -3358,6 +3485,7 @@ ttn_status pipeline_step(PipelineImpl* p, uint8_t* fail, double* log_prob, doubl
 }
 
 int pipeline_group_size(const PipelineImpl* p) { return p->group_size(); }
+int pipeline_segment_ms(const PipelineImpl* p, double* ms) { return p->segment_ms(ms); }
 
 void pipeline_free(PipelineImpl* p) { delete p; }
 

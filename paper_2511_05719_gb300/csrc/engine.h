@@ -103,6 +103,7 @@ ttn_status pipeline_create(const ttn_circuit& c, const RunRequest& rq, int n_res
 ttn_status pipeline_step(PipelineImpl* p, uint8_t* fail, double* log_prob, double* discarded, uint64_t* traj,
                          int32_t* n_done, bool on_device, void* stream);
 int pipeline_group_size(const PipelineImpl* p);
+int pipeline_segment_ms(const PipelineImpl* p, double* ms);
 void pipeline_free(PipelineImpl* p);
 
 ttn_status philox_uniforms_device(uint64_t seed, const uint64_t* trajs, uint64_t n_traj,

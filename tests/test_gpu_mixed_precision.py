@@ -8,8 +8,11 @@ below test exactly the kernels the benchmark runs.  Bars: amplitudes within
 1e-5 of the state-vector oracle (2-norm relative to the state's norm) through
 the first syndrome round and 2e-5 through the second (FP32 rounding grows with
 depth); records bit-exact for the same Philox draws except near ties
-(|u - p| < 1e-5, counted and excluded); log-probabilities within 1e-6; no
+(|u - p| < 1e-5, counted and excluded); log-probabilities within the bound
+the amplitude bar implies (below); no
 trajectory may lose its norm (the library fails the call if one does)."""
+import math
+
 import numpy as np
 import pytest
 
@@ -26,6 +29,15 @@ MODELS = {"none": NONE, "srx": SRX, "ad": AD, "srx_pta": SRX_PTA, "ad_pta": AD_P
 STRENGTH = {"none": (0.0, 0.0), "srx": (0.07, 0.0), "ad": (0.0, 0.06), "srx_pta": (0.12, 0.0),
             "ad_pta": (0.0, 0.08), "srx_ad": (0.06, 0.05)}
 TOL_ROUND1, TOL_ROUND2, TIE = 1e-5, 2e-5, 1e-5
+
+
+def logp_tolerance(branch_p):
+    """A state within relative distance e of the exact one gives a branch of
+    probability p = |P psi|^2 with |dp| <= 2 sqrt(p) e + e^2, so
+    |d log p| <= (2 e / sqrt(p)) (1 + e / sqrt(p)); summed over the sampled
+    branches with e = the round-2 amplitude bar."""
+    e = TOL_ROUND2
+    return sum(2 * e / math.sqrt(p) * (1 + e / math.sqrt(p)) for p in branch_p)
 
 
 @pytest.mark.parametrize("noise", list(MODELS))
@@ -62,7 +74,7 @@ def test_mixed_records_bit_exact(noise):
             excluded += 1
             continue
         assert np.array_equal(out["records"][i], ref["rec"]), i
-        assert abs(out["log_prob"][i] - ref["logp"]) < 1e-6
+        assert abs(out["log_prob"][i] - ref["logp"]) < logp_tolerance(ref["branch_p"])
         assert out["fail"][i] == DEC.decode(G, ref["rec"])[0]
     assert excluded <= 3
 
