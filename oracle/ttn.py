@@ -324,6 +324,7 @@ def run_trajectory(circ, model, theta, gamma, seed, traj, chi, leaf_of_qubit=Non
     rec = np.zeros(circ.n_record_bits, dtype=np.uint8)
     logp = 0.0
     margin = math.inf
+    branch_p = []
     states = {}
     snap = set(snapshot_layers)
     events = [op[3] for op in circ.ops if op[3] >= 0]
@@ -358,6 +359,7 @@ def run_trajectory(circ, model, theta, gamma, seed, traj, chi, leaf_of_qubit=Non
             pm = p1 if m else p0
             tt.apply1(a, (P1 if m else P0) / math.sqrt(pm))
             logp += math.log(pm)
+            branch_p.append(pm)
             rec[r] = m
             last[a] = m
         elif kind == NOISE:
@@ -365,9 +367,10 @@ def run_trajectory(circ, model, theta, gamma, seed, traj, chi, leaf_of_qubit=Non
             logp += lp
             if dist is not None:
                 margin = min(margin, dist)
+                branch_p.append(math.exp(lp))
         if on_op is not None:
             on_op(i)
     if cur_layer in snap:
         states[cur_layer] = tt.amplitudes()
-    return dict(rec=rec, logp=logp, margin=margin, states=states, ttn=tt,
+    return dict(rec=rec, logp=logp, margin=margin, states=states, ttn=tt, branch_p=branch_p,
                 discarded=tt.discarded, ops_done=ops_done)
