@@ -38,6 +38,9 @@ import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
+# the pipeline runs one stream per group: give the GPU enough hardware work
+# queues that the streams do not share one (set before CUDA starts)
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 
 import workloads as WL  # noqa: E402
 
@@ -70,6 +73,7 @@ def parse():
     ap.add_argument("--precision", default="mixed")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 single-instance leg")
     return ap.parse_args()
 
 
@@ -201,6 +205,28 @@ def run_reference(a):
                              "; %d steps of equal op count" % K},
             "e2e": {"value": v, "unit": "trajectories/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
+
+
+def plain_fp64_single(a, P, torch):
+    """The plain FP64 single-instance GPU path: one trajectory per call,
+    complex128 tensors, FP64 Gram matrices on the FMA units and the FP64
+    tridiagonal eigensolver, no batching and no pipelining.  A complete d = 7
+    trajectory of it is a long run, so the sample is one complete one-round
+    trajectory, counted as 1 / rounds of a full one (later rounds cost more:
+    this overstates its rate, i.e. understates the batched path's gain)."""
+    circ1 = P.Circuit(a.distance, 1, layout="optimized")
+    theta = WL.M3["thetas"][3]
+    kw = dict(noise="srx", theta=theta, chi=a.chi, precision="fp64", seed=WL.M3["seed"],
+              svd_mode="gram_tri")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    P.run_trajectories(circ1, 1, first_traj=3, **kw)
+    torch.cuda.synchronize()
+    secs = time.perf_counter() - t0
+    return {"value": 1.0 / (a.rounds * secs), "unit": "trajectories/s",
+            "sample": "one complete d=%d one-round trajectory (theta=%.3f, chi=%d), FP64, one trajectory "
+                      "per call, %.1f s, counted as 1/%d of a %d-round trajectory"
+                      % (a.distance, theta, a.chi, secs, a.rounds, a.rounds)}
 
 
 def roofline(a, prof, cls):
@@ -344,7 +370,13 @@ def main():
             "pL_by_theta": pl,
             "eig_phase_Gcycles": {k: round(v / 1e9, 2) for k, v in prof["eig_phase_cycles"].items()},
             "mean_log_prob": float(logp.cpu().numpy().mean()), "mean_discarded": float(disc.cpu().numpy().mean())}
+    if not a.no_plain:
+        note("plain FP64 single-instance leg")
+        pl1 = plain_fp64_single(a, P, torch)
+        pl1["batched_over_plain"] = value / pl1["value"] if pl1["value"] > 0 else None
+        line["plain_fp64_single"] = pl1
     if not a.no_cpu_baseline and world == 1:
+        note("CPU oracle baseline")
         line["cpu_baseline"] = cpu_baseline(a)
     print(json.dumps(line))
     if dist:

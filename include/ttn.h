@@ -341,7 +341,10 @@ ttn_status ttn_decode(const ttn_circuit* circuit, uint64_t n, const uint8_t* rec
  * n_theta > 0 (host array, copied), else params->theta; per-trajectory
  * arrays in params are rejected (EINVAL).  max_device_bytes bounds the
  * resident batch (0: 85 % of free memory; ENOMEM if it does not fit).
- * *out: library-owned handle, released by ttn_pipeline_free. */
+ * The groups' streams overlap only if the GPU has as many hardware work
+ * queues: set CUDA_DEVICE_MAX_CONNECTIONS (up to 32) above n_segments before
+ * the process starts CUDA.  *out: library-owned handle, released by
+ * ttn_pipeline_free. */
 typedef struct ttn_pipeline ttn_pipeline;
 ttn_status ttn_pipeline_create(const ttn_circuit* circuit, const ttn_run_params* params, int32_t n_resident,
                                int32_t n_segments, const double* theta_cycle, int32_t n_theta,

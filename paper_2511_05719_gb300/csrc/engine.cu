@@ -171,6 +171,11 @@ template <typename R>
 constexpr int tri_smem_bytes() {
   return 512 * (5 * 2 * (int)sizeof(R) + 3 * (int)sizeof(R)) + 2 * TRI_NB * 512 * 2 * (int)sizeof(R);
 }
+// without the back-transformation's blocks (MIXED runs defer it to k_eig_bt)
+template <typename R>
+constexpr int tri_smem_bytes_nobt() {
+  return 512 * (5 * 2 * (int)sizeof(R) + 3 * (int)sizeof(R));
+}
 
 template <typename R>
 __device__ __forceinline__ cx<R>* node_ptr(const Dev<R>& d, int b, int v) {
@@ -1317,6 +1322,12 @@ __global__ void __launch_bounds__(512) k_eig_tri(Dev<R> d, int v, int w, int kca
   const double sc = s_sc;
   const R epsR = sizeof(R) == 8 ? R(2.220446049250313e-16) : R(1.1920929e-07);
   const R pivmin = sizeof(R) == 8 ? R(1e-280) : R(1e-30);
+  // rescaling window of the Sturm minors (exact powers of two)
+  const R sturm_hi = sizeof(R) == 8 ? R(0x1p400) : R(0x1p50);
+  const R sturm_lo = sizeof(R) == 8 ? R(0x1p-400) : R(0x1p-50);
+  const R sturm_down = sizeof(R) == 8 ? R(0x1p-400) : R(0x1p-50);
+  const R sturm_up = sizeof(R) == 8 ? R(0x1p400) : R(0x1p50);
+  const R sturm_tiny = sizeof(R) == 8 ? R(0x1p-1000) : R(0x1p-120);
   for (int j = tid; j < n; j += nth) {
     dg[j] = (R)(dg[j] / sc);
     if (j + 1 < n) {
@@ -1349,13 +1360,29 @@ __global__ void __launch_bounds__(512) k_eig_tri(Dev<R> d, int v, int w, int kca
       const R mid = R(0.5) * (lo + hi);
       if (!(hi - lo > fmax(2 * epsR * fmax(fabs(lo), fabs(hi)), R(0.125) * epsR)) || mid == lo || mid == hi)
         break;
-      R q = dg[s0] - mid;
-      if (fabs(q) < pivmin) q = -pivmin;
-      int cnt = q < R(0);
+      // Sturm count without divisions: the leading principal minors
+      // p_i = (d_i - mid) p_{i-1} - b_{i-1}^2 p_{i-2} (p_0 = 1) change sign
+      // once per eigenvalue below mid (q_i = p_{i+1} / p_i is the pivot of
+      // T - mid I); a zero minor counts as a tiny negative pivot, and the
+      // pair is rescaled by exact powers of two to stay in range
+      R pm2 = R(1), pm1 = dg[s0] - mid;
+      if (fabs(pm1) < pivmin) pm1 = -pivmin;
+      int cnt = pm1 < R(0);
       for (int i = s0 + 1; i < e0; ++i) {
-        q = (dg[i] - mid) - fast_div(b2[i - 1], q);
-        if (fabs(q) < pivmin) q = -pivmin;
-        cnt += q < R(0);
+        R pc = (dg[i] - mid) * pm1 - b2[i - 1] * pm2;
+        if (pc == R(0) || fabs(pc) < pivmin * fabs(pm1))
+          pc = -copysign(fmax(pivmin * fabs(pm1), sturm_tiny), pm1);
+        cnt += (pc < R(0)) != (pm1 < R(0));
+        pm2 = pm1;
+        pm1 = pc;
+        const R big = fmax(fabs(pm1), fabs(pm2));
+        if (big > sturm_hi) {
+          pm1 *= sturm_down;
+          pm2 *= sturm_down;
+        } else if (big < sturm_lo) {
+          pm1 *= sturm_up;
+          pm2 *= sturm_up;
+        }
       }
       if (cnt <= j - s0) lo = mid;
       else hi = mid;
@@ -2813,7 +2840,13 @@ struct Engine {
                 dv.eig_smem_bytes = EIG_JACOBI_N * EIG_JACOBI_N * (int)sizeof(cx<double>);
                 dv.defer_bt = sizeof(R) == 4 ? 1 : 0;
                 k_eig<double><<<nb, 512, dv.eig_smem_bytes, st>>>(dv, v, w, kcap);
-                if (both) k_eig_tri<double><<<nb, 512, tri_smem_bytes<double>(), st>>>(dv, v, w, kcap);
+                // a bond up to 256 fits 256 threads (one per eigenvalue); half
+                // the SM's registers and a quarter of its shared memory then
+                // leave room for other streams' kernels beside it
+                if (both)
+                  k_eig_tri<double><<<nb, nmv <= 256 ? 256 : 512,
+                                      dv.defer_bt ? tri_smem_bytes_nobt<double>() : tri_smem_bytes<double>(), st>>>(
+                      dv, v, w, kcap);
                 if constexpr (sizeof(R) == 4) {
                   k_vk_to_float<<<nb, 256, 0, st>>>(dev, dG64 + b0 * vstride, EIG_JACOBI_N);
                   if (both)
