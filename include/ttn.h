@@ -176,8 +176,10 @@ ttn_status ttn_circuit_layout(const ttn_circuit* circuit, int32_t* leaf_of_qubit
  * decoder's bound was exceeded), log_prob [n_traj] (log p of the
  * sampled record and branches), discarded [n_traj] (sum of discarded
  * squared singular values), near_ties [n_traj] (draws with |u - p| < 1e-9
- * (FP64) or 1e-5 (FP32)).  Results depend only on (seed, trajectory index),
- * not on batching.  EOVERFLOW if a decoding instance exceeds the decoder's
+ * (FP64) or 1e-5 (FP32)).  Records and fail bytes depend only on (seed,
+ * trajectory index), not on batching (except draws within rounding of a
+ * probability); log_prob and discarded agree across batchings to rounding,
+ * since a few of their FP64 reductions are atomic and order-dependent.  EOVERFLOW if a decoding instance exceeds the decoder's
  * bound; ENOMEM if one trajectory does not fit on the device; ENUMERIC if a
  * trajectory's state lost its norm or became non-finite (the whole call
  * fails: leaving such a trajectory out would bias p_L). */

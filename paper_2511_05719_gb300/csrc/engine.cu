@@ -159,6 +159,7 @@ static constexpr int EIG_JACOBI_N = 64;
 static constexpr int TRI_UNROLL = 16;  // loads in flight per thread in L2-resident sweeps
 static constexpr int TRI_NB = 8;       // reflectors per compact-WY block of the back-transformation
 static constexpr int TRI_INV_ITERS = 2;  // inverse-iteration / orthonormalisation rounds
+static constexpr double TRI_CLUSTER_TOL = 1e-3;  // eigenvalue cluster width (relative to |T|)
 // profiling ledger: flops and bytes per class, then SM cycles per phase of
 // the tridiagonal eigensolver (summed over trajectories, thread 0's clock)
 static constexpr int LEDGER_WORDS = 2 * NCLASS + EIG_PHASES + MOVE_HIST_WORDS;
@@ -1129,6 +1130,7 @@ __global__ void __launch_bounds__(512) k_eig_tri(Dev<R> d, int v, int w, int kca
   __shared__ double wx2[32], wt2[32], wvp[32];  // per-warp partial sums
   __shared__ double s_sc;
   __shared__ int bstart[512], bend[512];  // unreduced block [bstart, bend) of each row
+  __shared__ short cst[512], cen[512];     // cluster [cst, cen) of each kept column
 
   double trp = 0.0;
   for (int j = tid; j < n; j += nth) trp += (double)A[(int64_t)j * n + j].x;
@@ -1424,6 +1426,18 @@ __global__ void __launch_bounds__(512) k_eig_tri(Dev<R> d, int v, int w, int kca
     const int jj = perm[c];
     start_vec(c, 0, bstart[jj], bend[jj]);
   }
+  // clusters of kept eigenvalues (descending order): neighbours closer than
+  // TRI_CLUSTER_TOL |T| share one.  Inverse-iteration vectors of eigenvalues
+  // further apart are orthogonal to about eps |T| / gap already, so
+  // Gram-Schmidt and the Rayleigh-Ritz rotation act within clusters only (the
+  // cluster rule of LAPACK's stein).
+  if (tid == 0) {
+    const R tolc = TRI_CLUSTER_TOL * fmax(fabs(lam[perm[0]]), fabs(lam[perm[k - 1]]));
+    cst[0] = 0;
+    for (int a = 1; a < k; ++a) cst[a] = (lam[perm[a - 1]] - lam[perm[a]] <= tolc) ? cst[a - 1] : (short)a;
+    cen[k - 1] = (short)k;
+    for (int a = k - 2; a >= 0; --a) cen[a] = (cst[a + 1] == cst[a]) ? cen[a + 1] : (short)(a + 1);
+  }
   __syncthreads();
   R* cf = reinterpret_cast<R*>(pp);  // Gram-Schmidt coefficients (k <= 512)
   const int warp_id = tid >> 5, lane_id = tid & 31, nwarp = nth >> 5;
@@ -1502,7 +1516,7 @@ __global__ void __launch_bounds__(512) k_eig_tri(Dev<R> d, int v, int w, int kca
       for (int rep = 0; rep < 2; ++rep) {
         for (int attempt = 0; attempt < 2; ++attempt) {
           // coefficients <z_b, z_a>: one warp per b, lanes over rows
-          for (int bb = warp_id; bb < a; bb += nwarp) {
+          for (int bb = cst[a] + warp_id; bb < a; bb += nwarp) {
             R acc = R(0);
             const R* zb = Z + (int64_t)bb * n;
             const R* za = Z + (int64_t)a * n;
@@ -1515,7 +1529,7 @@ __global__ void __launch_bounds__(512) k_eig_tri(Dev<R> d, int v, int w, int kca
           for (int i = tid; i < n; i += nth) {
             R z = Z[(int64_t)a * n + i];
             n0 += (double)z * z;
-            for (int bb = 0; bb < a; ++bb) z -= cf[bb] * Z[(int64_t)bb * n + i];
+            for (int bb = cst[a]; bb < a; ++bb) z -= cf[bb] * Z[(int64_t)bb * n + i];
             Z[(int64_t)a * n + i] = z;
             n1 += (double)z * z;
           }
@@ -1547,11 +1561,14 @@ __global__ void __launch_bounds__(512) k_eig_tri(Dev<R> d, int v, int w, int kca
     if (i + 1 < n) t += bt[i] * zc[i + 1];
     TZ[idx] = t;
   }
-  for (int idx = tid; idx < k * k; idx += nth) Q[idx] = R((idx / k) == (idx % k));
+  for (int idx = tid; idx < k * k; idx += nth) {
+    Q[idx] = R((idx / k) == (idx % k));
+    H[idx] = R(0);
+  }
   __syncthreads();
   for (int e = warp_id; e < k * k; e += nwarp) {  // one warp per entry, lanes over rows
     const int a = e / k, c = e - a * k;
-    if (c < a) continue;
+    if (c < a || c >= cen[a]) continue;  // within a's cluster only
     R acc = R(0);
     const R* za = Z + (int64_t)a * n;
     const R* tc = TZ + (int64_t)c * n;
@@ -1627,7 +1644,7 @@ __global__ void __launch_bounds__(512) k_eig_tri(Dev<R> d, int v, int w, int kca
   for (int idx = tid; idx < n * k; idx += nth) {
     const int c = idx / n, i = idx - c * n;
     R acc = R(0);
-    for (int a = 0; a < k; ++a) acc += Z[(int64_t)a * n + i] * Q[a * k + c];
+    for (int a = cst[c]; a < cen[c]; ++a) acc += Z[(int64_t)a * n + i] * Q[a * k + c];
     TZ[idx] = acc;
   }
   __syncthreads();

@@ -1,8 +1,12 @@
 """The pipelined resident batch (ttn_pipeline_*) against ttn_run_trajectories:
 trajectories depend only on (seed, trajectory index), so every trajectory a
-pipeline step completes must carry exactly the decoded outcome,
-log-probability and discarded weight the plain call gives for that index
-(same kernels, same draws), whatever group and segment it ran in."""
+pipeline step completes must carry the decoded outcome the plain call gives
+for that index (same kernels, same draws), whatever group and segment it ran
+in.  Log-probabilities and discarded weights agree to 1e-6 relative: a few
+reductions (column norms of a centre move, log-probability terms of
+simultaneous Pauli draws) add in FP64 atomically, in an order that varies from
+run to run, and a last-bit difference can round the other way into the FP32
+tensors."""
 import numpy as np
 import pytest
 
@@ -46,8 +50,8 @@ def test_pipeline_equals_plain_runs(precision, noise, R, S):
     for i in range(n):
         f, lp, ds = got[first + i]
         assert f == ref["fail"][i]
-        assert lp == ref["log_prob"][i]
-        assert ds == ref["discarded"][i]
+        assert abs(lp - ref["log_prob"][i]) <= 1e-6 * (1.0 + abs(lp))
+        assert abs(ds - ref["discarded"][i]) <= 1e-6 * (1e-12 + abs(ds))
 
 
 def test_pipeline_argument_checks():
