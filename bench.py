@@ -65,13 +65,13 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ttn", choices=["ttn", "reference"])
-    ap.add_argument("--resident", type=int, default=152, help="trajectories on the device per rank")
-    ap.add_argument("--segments", type=int, default=19, help="pipeline segments (resident must be a multiple)")
+    ap.add_argument("--resident", type=int, default=160, help="trajectories on the device per rank")
+    ap.add_argument("--segments", type=int, default=32, help="pipeline segments (resident must be a multiple)")
     ap.add_argument("--distance", type=int, default=7)
     ap.add_argument("--rounds", type=int, default=7)
     ap.add_argument("--chi", type=int, default=128)
     ap.add_argument("--precision", default="mixed")
-    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 single-instance leg")
     return ap.parse_args()

@@ -1018,6 +1018,15 @@ __device__ __forceinline__ double2 block_sum2(double a, double c, double* red) {
   return t;
 }
 
+__device__ __forceinline__ bool is_zero_bits(double x) { return (__double_as_longlong(x) << 1) == 0; }
+__device__ __forceinline__ bool is_zero_bits(float x) { return (__float_as_int(x) << 1) == 0; }
+__device__ __forceinline__ int sign_differs(double a, double b) {
+  return (int)(((unsigned long long)(__double_as_longlong(a) ^ __double_as_longlong(b))) >> 63);
+}
+__device__ __forceinline__ int sign_differs(float a, float b) {
+  return (int)(((unsigned)(__float_as_int(a) ^ __float_as_int(b))) >> 31);
+}
+
 template <typename R>
 __device__ __forceinline__ R fast_div(R a, R b) {
   return a / b;
@@ -1325,7 +1334,7 @@ __global__ void __launch_bounds__(512) k_eig_tri(Dev<R> d, int v, int w, int kca
   const R epsR = sizeof(R) == 8 ? R(2.220446049250313e-16) : R(1.1920929e-07);
   const R pivmin = sizeof(R) == 8 ? R(1e-280) : R(1e-30);
   // rescaling window of the Sturm minors (exact powers of two)
-  const R sturm_hi = sizeof(R) == 8 ? R(0x1p400) : R(0x1p50);
+  const R sturm_hi = sizeof(R) == 8 ? R(0x1p400) : R(0x1p50);   // far from overflow after 8 rows
   const R sturm_lo = sizeof(R) == 8 ? R(0x1p-400) : R(0x1p-50);
   const R sturm_down = sizeof(R) == 8 ? R(0x1p-400) : R(0x1p-50);
   const R sturm_up = sizeof(R) == 8 ? R(0x1p400) : R(0x1p50);
@@ -1367,23 +1376,27 @@ __global__ void __launch_bounds__(512) k_eig_tri(Dev<R> d, int v, int w, int kca
       // once per eigenvalue below mid (q_i = p_{i+1} / p_i is the pivot of
       // T - mid I); a zero minor counts as a tiny negative pivot, and the
       // pair is rescaled by exact powers of two to stay in range
+      // (sign and zero tests on the bit patterns keep the FP64 pipe to the
+      // three operations of the recurrence; |T| <= 1 bounds the growth of a
+      // minor to 3x per row, so the range is checked every 8 rows)
       R pm2 = R(1), pm1 = dg[s0] - mid;
       if (fabs(pm1) < pivmin) pm1 = -pivmin;
       int cnt = pm1 < R(0);
       for (int i = s0 + 1; i < e0; ++i) {
         R pc = (dg[i] - mid) * pm1 - b2[i - 1] * pm2;
-        if (pc == R(0) || fabs(pc) < pivmin * fabs(pm1))
-          pc = -copysign(fmax(pivmin * fabs(pm1), sturm_tiny), pm1);
-        cnt += (pc < R(0)) != (pm1 < R(0));
+        if (is_zero_bits(pc)) pc = -copysign(sturm_tiny, pm1);
+        cnt += sign_differs(pc, pm1);
         pm2 = pm1;
         pm1 = pc;
-        const R big = fmax(fabs(pm1), fabs(pm2));
-        if (big > sturm_hi) {
-          pm1 *= sturm_down;
-          pm2 *= sturm_down;
-        } else if (big < sturm_lo) {
-          pm1 *= sturm_up;
-          pm2 *= sturm_up;
+        if (((i - s0) & 7) == 0) {
+          const R big = fmax(fabs(pm1), fabs(pm2));
+          if (big > sturm_hi) {
+            pm1 *= sturm_down;
+            pm2 *= sturm_down;
+          } else if (big < sturm_lo) {
+            pm1 *= sturm_up;
+            pm2 *= sturm_up;
+          }
         }
       }
       if (cnt <= j - s0) lo = mid;

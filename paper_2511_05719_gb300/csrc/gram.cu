@@ -44,17 +44,22 @@
 
 namespace ttn {
 
-static constexpr int G_KT = 64;                  // rows of M per K-tile
+static constexpr int G_KT = 32;                  // rows of M per K-tile
 static constexpr int G_TA = 128;                 // X-columns per A tile (MMA M)
 static constexpr int G_TB = 64;                  // X-columns per B tile (MMA N)
-static constexpr int G_TILE = G_TA * G_KT;       // bf16 elements of a packed 128 x 64 tile (16 KB)
-static constexpr int G_CHUNK = 4;                // K-tiles per exact FP32 accumulation (256 rows)
-static constexpr int G_SPLIT = 64;               // K-tiles per CTA (4096 rows)
-static constexpr int G_STAGE = 3 * 16384 + 3 * 8192;  // bytes of one pipeline stage
-static constexpr int G_ACC = 64 * 128 * 8;       // bytes of the per-row 64-bit sums (column-major)
-static constexpr int G_SMEM = 2 * G_STAGE + G_ACC;  // dynamic shared memory of k_gram_mma
+static constexpr int G_TILE = G_TA * G_KT;       // bf16 elements of a packed 128 x 32 tile (8 KB)
+static constexpr int G_TILE_B = G_TILE * 2;      // its bytes
+static constexpr int G_SBO = G_KT / 8 * 128;     // bytes between 8-column groups of a tile
+static constexpr int G_CHUNK = 256 / G_KT;       // K-tiles per exact FP32 accumulation (256 rows)
+static constexpr int G_SPLIT = 4096 / G_KT;      // K-tiles per CTA (4096 rows)
+static constexpr int G_NS = 3;                   // pipeline stages
+static constexpr int G_STAGE = 3 * G_TILE_B + 3 * (G_TILE_B / 2);  // A digits (128 rows) + B digits (64)
+static constexpr int G_SMEM = G_NS * G_STAGE;    // dynamic shared memory of k_gram_mma
 static constexpr uint32_t G_WAIT = 1u << 22;     // polls of a bounded mbarrier wait
-static constexpr int G_TMEM_COLS = 512;          // five 64-column accumulators, rounded up
+// tensor memory: five 64-column FP32 accumulators (columns 0..319), then the
+// row's 64-bit fixed-point sums as low (320..383) and high (384..447) words
+static constexpr int G_TMEM_COLS = 512;
+static constexpr int G_TM_LO = 5 * G_TB, G_TM_HI = 6 * G_TB;
 
 __host__ __device__ inline int g_nct(int n) { return (2 * n + G_TA - 1) / G_TA; }
 __host__ __device__ inline int g_nkt(int64_t m) { return (int)((m + G_KT - 1) / G_KT); }
@@ -99,11 +104,11 @@ __global__ void k_gram_exps(GramArgs a) {
 }
 
 // ---------------------------------------------------------------- 2. digit tiles
-// Tile (s, ct, kt) of trajectory b: X-columns ct*128.., rows kt*64.., digit
+// Tile (s, ct, kt) of trajectory b: X-columns ct*128.., rows kt*32.., digit
 // s, at ((s * NCT + ct) * NKT + kt) * G_TILE.  Inside a tile, element
-// (column cc, row rr) at (cc/8)*512 + (rr/8)*64 + (cc%8)*8 + rr%8: core
+// (column cc, row rr) at (cc/8)*256 + (rr/8)*64 + (cc%8)*8 + rr%8: core
 // matrices of 8 columns x 8 rows (16 bytes per column), K-groups adjacent
-// (LBO 128 bytes), 8-column groups 1024 bytes apart (SBO).
+// (LBO 128 bytes), 8-column groups G_SBO = 512 bytes apart (SBO).
 __global__ void __launch_bounds__(256) k_gram_pack(GramArgs a) {
   const int b = blockIdx.z;
   const int2 sh = a.shape[b];
@@ -142,7 +147,7 @@ __global__ void __launch_bounds__(256) k_gram_pack(GramArgs a) {
           n3 = r1 - n2 * 256;
         }
       }
-      const int off = (cc >> 3) * 512 + (rr >> 3) * 64 + (cc & 7) * 8 + (rr & 7);
+      const int off = (cc >> 3) * (G_SBO / 2) + (rr >> 3) * 64 + (cc & 7) * 8 + (rr & 7);
       t0[off] = __bfloat16_as_ushort(__float2bfloat16_rn((float)n1));
       t1[off] = __bfloat16_as_ushort(__float2bfloat16_rn((float)n2));
       t2[off] = __bfloat16_as_ushort(__float2bfloat16_rn((float)n3));
@@ -158,7 +163,7 @@ __global__ void __launch_bounds__(256) k_gram_pack(GramArgs a) {
 // row t (TMEM lane t); thread 0 also issues the bulk copies and the MMAs.
 __global__ void __launch_bounds__(128, 1) k_gram_mma(GramArgs a, int nct_cap) {
   extern __shared__ __align__(1024) unsigned char g_smem[];
-  __shared__ __align__(8) uint64_t bar_load[2], bar_mma[2], bar_acc;
+  __shared__ __align__(8) uint64_t bar_load[G_NS], bar_mma[G_NS], bar_acc;
   __shared__ uint32_t tmem_slot;
   __shared__ int s_abort;
   const int b = blockIdx.z;
@@ -181,10 +186,10 @@ __global__ void __launch_bounds__(128, 1) k_gram_mma(GramArgs a, int nct_cap) {
 
   const int tid = threadIdx.x, warp = tid >> 5;
   if (tid == 0) {
-    tc::mbar_init(&bar_load[0], 1);
-    tc::mbar_init(&bar_load[1], 1);
-    tc::mbar_init(&bar_mma[0], 1);
-    tc::mbar_init(&bar_mma[1], 1);
+    for (int i = 0; i < G_NS; ++i) {
+      tc::mbar_init(&bar_load[i], 1);
+      tc::mbar_init(&bar_mma[i], 1);
+    }
     tc::mbar_init(&bar_acc, 1);
     tc::mbar_fence_init();
     s_abort = 0;
@@ -194,43 +199,44 @@ __global__ void __launch_bounds__(128, 1) k_gram_mma(GramArgs a, int nct_cap) {
   __syncthreads();
   tc::tc_fence_after();
   const uint32_t tmem = tmem_slot;
+  const uint32_t lane_off = (uint32_t)(warp * 32) << 16;  // this warp's TMEM lane quarter
 
   const uint16_t* S = a.slices + (int64_t)b * a.sstride;
   auto srcA = [&](int s, int kt) { return S + ((int64_t)(s * NCT + ta) * NKT + kt) * G_TILE; };
   auto srcB = [&](int s, int kt) {
     return S + ((int64_t)(s * NCT + (tb >> 1)) * NKT + kt) * G_TILE + (tb & 1) * (G_TILE / 2);
   };
-  unsigned char* stage[2] = {g_smem, g_smem + G_STAGE};
+  auto stage = [&](int st) { return g_smem + st * G_STAGE; };
   auto issue_load = [&](int st, int kt) {
     tc::mbar_expect_tx(&bar_load[st], G_STAGE);
-    for (int s = 0; s < 3; ++s) tc::bulk_g2s(stage[st] + s * 16384, srcA(s, kt), 16384, &bar_load[st]);
+    for (int s = 0; s < 3; ++s) tc::bulk_g2s(stage(st) + s * G_TILE_B, srcA(s, kt), G_TILE_B, &bar_load[st]);
     for (int s = 0; s < 3; ++s)
-      tc::bulk_g2s(stage[st] + 3 * 16384 + s * 8192, srcB(s, kt), 8192, &bar_load[st]);
+      tc::bulk_g2s(stage(st) + 3 * G_TILE_B + s * (G_TILE_B / 2), srcB(s, kt), G_TILE_B / 2, &bar_load[st]);
   };
 
   const uint32_t idesc = tc::instr_desc(1, G_TA, G_TB);
-  // 64-bit fixed-point sums of this thread's row, column j at acc[j * 128 + tid]
-  long long* acc = reinterpret_cast<long long*>(g_smem + 2 * G_STAGE);
-  for (int j = 0; j < G_TB; ++j) acc[j * G_TA + tid] = 0;
   const int nk = kt1 - kt0;
-  int loads_issued = 0, mma_commits[2] = {0, 0};
-  if (tid == 0) {
-    issue_load(0, kt0);
-    loads_issued = 1;
-  }
+  int loads[G_NS], commits[G_NS];  // per stage: bulk loads issued, MMA commits (thread 0)
+  for (int i = 0; i < G_NS; ++i) loads[i] = commits[i] = 0;
+  if (tid == 0)
+    for (int i = 0; i < G_NS - 1 && i < nk; ++i) {
+      issue_load(i, kt0 + i);
+      loads[i]++;
+    }
   uint32_t acc_phase = 0;
+  bool first_chunk = true;
   bool first[5] = {true, true, true, true, true};
   for (int i = 0; i < nk; ++i) {
-    const int st = i & 1;
+    const int st = i % G_NS;
     const bool chunk_end = (i % G_CHUNK) == G_CHUNK - 1 || i == nk - 1;
     if (tid == 0 && !s_abort) {
-      if (!tc::mbar_wait(&bar_load[st], (uint32_t)((i >> 1) & 1), G_WAIT)) {
+      if (!tc::mbar_wait(&bar_load[st], (uint32_t)((i / G_NS) & 1), G_WAIT)) {
         s_abort = 1;
       } else {
         tc::tc_fence_after();
         if (i % G_CHUNK == 0)
           for (int g = 0; g < 5; ++g) first[g] = true;
-        const uint32_t sa = tc::smem_u32(stage[st]), sb = sa + 3 * 16384;
+        const uint32_t sa = tc::smem_u32(stage(st)), sb = sa + 3 * G_TILE_B;
 #pragma unroll
         for (int ks = 0; ks < G_KT / 16; ++ks) {
 #pragma unroll
@@ -238,26 +244,26 @@ __global__ void __launch_bounds__(128, 1) k_gram_mma(GramArgs a, int nct_cap) {
 #pragma unroll
             for (int s2 = 0; s2 < 3; ++s2) {
               const int g = s1 + s2;
-              const uint64_t ad = tc::smem_desc(sa + s1 * 16384 + ks * 256, 128, 1024);
-              const uint64_t bd = tc::smem_desc(sb + s2 * 8192 + ks * 256, 128, 1024);
+              const uint64_t ad = tc::smem_desc(sa + s1 * G_TILE_B + ks * 256, 128, G_SBO);
+              const uint64_t bd = tc::smem_desc(sb + s2 * (G_TILE_B / 2) + ks * 256, 128, G_SBO);
               tc::mma_bf16(tmem + g * G_TB, ad, bd, idesc, first[g] ? 0u : 1u);
               first[g] = false;
             }
           }
         }
         tc::mma_commit(&bar_mma[st]);
-        mma_commits[st]++;
-        // the next tile goes into the other stage once its MMAs are done
-        if (i + 1 < nk) {
-          const int so = st ^ 1;
+        commits[st]++;
+        // tile i + NS - 1 goes into the stage tile i - 1 used, once its MMAs are done
+        const int nx = i + G_NS - 1;
+        if (nx < nk) {
+          const int so = nx % G_NS;
           bool ok = true;
-          if (mma_commits[so] > 0)
-            ok = tc::mbar_wait(&bar_mma[so], (uint32_t)((mma_commits[so] - 1) & 1), G_WAIT);
+          if (commits[so] > 0) ok = tc::mbar_wait(&bar_mma[so], (uint32_t)((commits[so] - 1) & 1), G_WAIT);
           if (!ok) {
             s_abort = 1;
           } else {
-            issue_load(so, kt0 + i + 1);
-            loads_issued++;
+            issue_load(so, kt0 + nx);
+            loads[so]++;
           }
         }
         if (chunk_end) tc::mma_commit(&bar_acc);
@@ -283,15 +289,30 @@ __global__ void __launch_bounds__(128, 1) k_gram_mma(GramArgs a, int nct_cap) {
 #pragma unroll
         for (int g = 0; g < 5; ++g) {
           uint32_t r[32];
-          tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + g * G_TB + h * 32, r);
+          tc::tmem_ld32(tmem + lane_off + g * G_TB + h * 32, r);
           tc::tmem_ld_wait();
 #pragma unroll
           for (int j = 0; j < 32; ++j)
             part[j] += (long long)__float2int_rn(__uint_as_float(r[j])) << (8 * (4 - g));
         }
+        uint32_t lo[32], hi[32];
+        if (!first_chunk) {
+          tc::tmem_ld32(tmem + lane_off + G_TM_LO + h * 32, lo);
+          tc::tmem_ld32(tmem + lane_off + G_TM_HI + h * 32, hi);
+          tc::tmem_ld_wait();
 #pragma unroll
-        for (int j = 0; j < 32; ++j) acc[(h * 32 + j) * G_TA + tid] += part[j];
+          for (int j = 0; j < 32; ++j) part[j] += (long long)(((uint64_t)hi[j] << 32) | lo[j]);
+        }
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          lo[j] = (uint32_t)(uint64_t)part[j];
+          hi[j] = (uint32_t)((uint64_t)part[j] >> 32);
+        }
+        tc::tmem_st32(tmem + lane_off + G_TM_LO + h * 32, lo);
+        tc::tmem_st32(tmem + lane_off + G_TM_HI + h * 32, hi);
+        tc::tmem_st_wait();
       }
+      first_chunk = false;
       tc::tc_fence_before();
       __syncthreads();
     }
@@ -303,20 +324,25 @@ __global__ void __launch_bounds__(128, 1) k_gram_mma(GramArgs a, int nct_cap) {
     if (tid == 0) {
       tc::mma_commit(&bar_acc);
       tc::mbar_wait(&bar_acc, acc_phase, G_WAIT);
-      for (int st = 0; st < 2; ++st) {
-        const int uses = (loads_issued + 1 - st) / 2;  // loads into stage st
-        if (uses > 0) tc::mbar_wait(&bar_load[st], (uint32_t)((uses - 1) & 1), G_WAIT);
-      }
+      for (int st = 0; st < G_NS; ++st)
+        if (loads[st] > 0) tc::mbar_wait(&bar_load[st], (uint32_t)((loads[st] - 1) & 1), G_WAIT);
       g_flag(a, b, GRAM_ERR_TIMEOUT);
     }
   } else {
+    tc::tc_fence_after();
     const int arow = ta * G_TA + tid;
-    if (arow < nc) {
-      unsigned long long* F = a.gfix + (int64_t)b * a.gld * a.gld + (int64_t)arow * a.gld;
-      for (int j = 0; j < G_TB; ++j) {
-        const int c = tb * G_TB + j;
-        const long long v = acc[j * G_TA + tid];
-        if (c >= arow && c < nc && v != 0) atomicAdd(&F[c], (unsigned long long)v);
+    unsigned long long* F = a.gfix + (int64_t)b * a.gld * a.gld + (int64_t)arow * a.gld;
+    for (int h = 0; h < G_TB / 32; ++h) {
+      uint32_t lo[32], hi[32];
+      tc::tmem_ld32(tmem + lane_off + G_TM_LO + h * 32, lo);
+      tc::tmem_ld32(tmem + lane_off + G_TM_HI + h * 32, hi);
+      tc::tmem_ld_wait();
+      if (arow < nc) {
+        for (int j = 0; j < 32; ++j) {
+          const int c = tb * G_TB + h * 32 + j;
+          const unsigned long long v = ((unsigned long long)hi[j] << 32) | lo[j];
+          if (c >= arow && c < nc && v != 0ull) atomicAdd(&F[c], v);
+        }
       }
     }
   }
