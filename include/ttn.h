@@ -43,14 +43,18 @@ typedef enum {
  * (Sec. III.A, Fig. 1b-d).  SRX: exp(-i theta X) (Eq. 1).  AD: Kraus operators
  * of Eqs. 2-3, unravelled exactly.  *_PTA: Pauli-twirled channel (Sec. IV.C):
  * SRX -> X with prob. sin^2 theta; AD -> (I,X,Y,Z) with probabilities
- * ((1+sqrt(1-g))^2/4, g/4, g/4, (1-sqrt(1-g))^2/4).  SRX_AD: SRX then AD. */
+ * ((1+sqrt(1-g))^2/4, g/4, g/4, (1-sqrt(1-g))^2/4).  SRX_AD: SRX then AD.
+ * DEPOL: single-qubit depolarizing noise (Sec. III.A's Pauli benchmark model,
+ * applied at the same locations): X, Y, Z each with probability gamma / 3;
+ * gamma is its strength p. */
 typedef enum {
   TTN_NOISE_NONE = 0,
   TTN_NOISE_SRX = 1,
   TTN_NOISE_AD = 2,
   TTN_NOISE_SRX_PTA = 3,
   TTN_NOISE_AD_PTA = 4,
-  TTN_NOISE_SRX_AD = 5
+  TTN_NOISE_SRX_AD = 5,
+  TTN_NOISE_DEPOL = 6
 } ttn_noise;
 
 /* Arithmetic of the tree tensors.  FP64: complex128 throughout.  FP32:

@@ -20,13 +20,17 @@ reproduces the channel on random density matrices, the diagonal matches the
 closed forms, the channels are trace preserving, theta = 0 / gamma = 0 is the
 identity.
 
+  DEPOL (Sec. III.A, the Pauli benchmark model, single-qubit form at every
+       location): p = (1 - g, g/3, g/3, g/3).
+
 Noise-model numbering (shared vocabulary of the C-ABI):
 NONE=0, SRX=1, AD=2, SRX_PTA=3, AD_PTA=4, SRX_AD=5 (SRX then AD at each
-location).
+location), DEPOL=6.
 """
 import numpy as np
 
-NONE, SRX, AD, SRX_PTA, AD_PTA, SRX_AD = 0, 1, 2, 3, 4, 5
+NONE, SRX, AD, SRX_PTA, AD_PTA, SRX_AD, DEPOL = 0, 1, 2, 3, 4, 5, 6
+PAULI_MODELS = (SRX_PTA, AD_PTA, DEPOL)  # channels that are a Pauli mixture
 
 I2 = np.eye(2, dtype=np.complex128)
 X = np.array([[0, 1], [1, 0]], dtype=np.complex128)
@@ -79,4 +83,6 @@ def pta_probs(model: int, theta: float, gamma: float) -> np.ndarray:
     if model == AD_PTA:
         r = np.sqrt(1.0 - gamma)
         return np.array([(1 + r) ** 2 / 4, gamma / 4, gamma / 4, (1 - r) ** 2 / 4])
-    raise ValueError("not a twirled model")
+    if model == DEPOL:
+        return np.array([1.0 - gamma, gamma / 3, gamma / 3, gamma / 3])
+    raise ValueError("not a Pauli channel")

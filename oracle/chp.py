@@ -1,7 +1,8 @@
 """O3: stabilizer-tableau trajectories for Pauli-twirled noise.
 
 Oracle (test infrastructure only).  With Pauli noise (the Pauli-twirled
-channels of Sec. IV.C: SRX_PTA, AD_PTA) the extraction circuit is Clifford
+channels of Sec. IV.C, SRX_PTA and AD_PTA, and depolarizing noise, DEPOL)
+the extraction circuit is Clifford
 plus sampled Paulis, so every trajectory stays a stabilizer state and is
 simulated exactly at any code distance.  This is the repository's own
 version of the paper's comparison with a Clifford simulator (Sec. IV.C,
@@ -36,7 +37,7 @@ import math
 import numpy as np
 
 from . import philox
-from .channels import SRX_PTA, AD_PTA, NONE, pta_probs
+from .channels import SRX_PTA, AD_PTA, DEPOL, NONE, PAULI_MODELS, pta_probs
 from .circuit import PREP_Z, PREP_X, CNOT, MEAS_Z, MEAS_X, NOISE
 
 
@@ -129,10 +130,10 @@ class Tableau:
 
 
 def run_trajectory(circ, model, theta, gamma, seed, traj):
-    """One trajectory of a Pauli-noise model (NONE, SRX_PTA, AD_PTA).
+    """One trajectory of a Pauli-noise model (NONE, SRX_PTA, AD_PTA, DEPOL).
     Returns dict(rec, logp, margin, branch_p) as the state-vector oracle."""
-    if model not in (NONE, SRX_PTA, AD_PTA):
-        raise ValueError("the tableau oracle runs Pauli noise only (NONE, SRX_PTA, AD_PTA)")
+    if model != NONE and model not in PAULI_MODELS:
+        raise ValueError("the tableau oracle runs Pauli noise only (NONE, SRX_PTA, AD_PTA, DEPOL)")
     N = circ.n_qubits
     tb = Tableau(N)
     last = np.zeros(N, dtype=np.int64)

@@ -29,7 +29,7 @@ within 3 sigma; p_L from trajectories agrees with the exact p_L.
 import math
 import numpy as np
 from . import philox
-from .channels import (NONE, SRX, AD, SRX_PTA, AD_PTA, SRX_AD,
+from .channels import (NONE, SRX, AD, SRX_PTA, AD_PTA, SRX_AD, PAULI_MODELS,
                        srx_unitary, pta_probs, X, Y, Z, H)
 from .circuit import PREP_Z, PREP_X, CNOT, MEAS_Z, MEAS_X, NOISE
 
@@ -96,7 +96,7 @@ def apply_noise(sv, q, model, theta, gamma, u):
         v[:, 1, :] *= math.sqrt(1.0 - gamma) / math.sqrt(1.0 - p1)
         v[:, 0, :] /= math.sqrt(1.0 - p1)
         return math.log1p(-p1), abs(u - p1)
-    if model in (SRX_PTA, AD_PTA):
+    if model in PAULI_MODELS:
         p = pta_probs(model, theta, gamma)
         cum = np.cumsum(p)
         k = 3

@@ -42,7 +42,7 @@ import time
 import numpy as np
 
 from . import philox
-from .channels import (NONE, SRX, AD, SRX_PTA, AD_PTA, SRX_AD,
+from .channels import (NONE, SRX, AD, SRX_PTA, AD_PTA, SRX_AD, PAULI_MODELS,
                        srx_unitary, pta_probs, X, Y, Z, H)
 from .circuit import PREP_Z, PREP_X, CNOT, MEAS_Z, MEAS_X, NOISE
 
@@ -296,7 +296,7 @@ def apply_noise_ttn(tt, q, model, theta, gamma, u):
         K0 = np.array([[1, 0], [0, math.sqrt(1 - gamma)]], dtype=np.complex128)
         tt.apply1(q, K0 / math.sqrt(1.0 - p1))
         return math.log1p(-p1), abs(u - p1)
-    if model in (SRX_PTA, AD_PTA):
+    if model in PAULI_MODELS:
         p = pta_probs(model, theta, gamma)
         cum = np.cumsum(p)
         k = 3

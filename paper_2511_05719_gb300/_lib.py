@@ -7,7 +7,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB = None
 
-NOISE = {"none": 0, "srx": 1, "ad": 2, "srx_pta": 3, "ad_pta": 4, "srx_ad": 5}
+NOISE = {"none": 0, "srx": 1, "ad": 2, "srx_pta": 3, "ad_pta": 4, "srx_ad": 5, "depol": 6}
 PRECISION = {"fp64": 0, "fp32": 1, "mixed": 2}
 LAYOUT = {"default": 0, "optimized": 1, "explicit": 2, "search": 3}
 

@@ -150,7 +150,7 @@ ttn_status ttn_circuit_layout(const ttn_circuit* c, int32_t* leaf_of_qubit) {
 
 static ttn_status check_params(const ttn_circuit* c, const ttn_run_params* p) {
   if (!c || !p) return fail_with(TTN_EINVAL, "null argument");
-  if (p->noise < TTN_NOISE_NONE || p->noise > TTN_NOISE_SRX_AD) return fail_with(TTN_EINVAL, "unknown noise model");
+  if (p->noise < TTN_NOISE_NONE || p->noise > TTN_NOISE_DEPOL) return fail_with(TTN_EINVAL, "unknown noise model");
   if (p->precision != TTN_PREC_FP64 && p->precision != TTN_PREC_FP32 && p->precision != TTN_PREC_MIXED)
     return fail_with(TTN_EINVAL, "unknown precision");
   if (p->chi < 1 || p->chi > 4096) return fail_with(TTN_EINVAL, "chi must be in [1, 4096]");
@@ -361,7 +361,8 @@ ttn_status grad_run(const ttn_circuit* c, const ttn_run_params* p, uint64_t shot
   if (wrt == 1 && (p->gamma - h < 0.0 || p->gamma + h > 1.0))
     return fail_with(TTN_EINVAL, "gamma +- h must stay in [0, 1]");
   const bool srx_like = p->noise == TTN_NOISE_SRX || p->noise == TTN_NOISE_SRX_PTA || p->noise == TTN_NOISE_SRX_AD;
-  const bool ad_like = p->noise == TTN_NOISE_AD || p->noise == TTN_NOISE_AD_PTA || p->noise == TTN_NOISE_SRX_AD;
+  const bool ad_like = p->noise == TTN_NOISE_AD || p->noise == TTN_NOISE_AD_PTA || p->noise == TTN_NOISE_SRX_AD ||
+                       p->noise == TTN_NOISE_DEPOL;
   if ((wrt == 0 && !srx_like) || (wrt == 1 && !ad_like))
     return fail_with(TTN_EINVAL, "the noise model does not depend on that parameter");
   RunRequest rq = make_request(p, shots, nullptr);

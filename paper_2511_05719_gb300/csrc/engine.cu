@@ -2160,6 +2160,9 @@ __global__ void k_layer1q(Dev<R> d, const Op1* ops, const Group1* groups, int g0
       if (d.noise == TTN_NOISE_SRX_PTA) {
         double c = cos(d.theta[b]), s = sin(d.theta[b]);
         p[0] = c * c; p[1] = s * s; p[2] = 0.0; p[3] = 0.0;
+      } else if (d.noise == TTN_NOISE_DEPOL) {
+        const double g = d.gamma[b];
+        p[0] = 1.0 - g; p[1] = g / 3; p[2] = g / 3; p[3] = g / 3;
       } else {
         double g = d.gamma[b], r = sqrt(1.0 - g);
         p[0] = (1 + r) * (1 + r) / 4; p[1] = g / 4; p[2] = g / 4; p[3] = (1 - r) * (1 - r) / 4;

@@ -680,7 +680,7 @@ Program compile_program(const ttn_circuit& c, int noise, int last_layer) {
   Compiler cp(c);
   const bool ad = noise == TTN_NOISE_AD || noise == TTN_NOISE_SRX_AD;
   const bool srx = noise == TTN_NOISE_SRX || noise == TTN_NOISE_SRX_AD;
-  const bool pta = noise == TTN_NOISE_SRX_PTA || noise == TTN_NOISE_AD_PTA;
+  const bool pta = noise == TTN_NOISE_SRX_PTA || noise == TTN_NOISE_AD_PTA || noise == TTN_NOISE_DEPOL;
   int cur = 0;
   std::vector<int> ad_q, ad_e;
   auto end_layer = [&]() {

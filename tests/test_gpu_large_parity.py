@@ -1,7 +1,7 @@
 """Records of the MIXED route at d = 5 and d = 7 against oracles that reach
 those sizes exactly:
 
-* Pauli-twirled noise (SRX_PTA, AD_PTA) against the stabilizer-tableau oracle
+* Pauli noise (SRX_PTA, AD_PTA, DEPOL) against the stabilizer-tableau oracle
   (O3): a Pauli trajectory has the noise-free entanglement, so at chi >= the
   noise-free chi_exact (32 at d = 5, C = 5; 128 at d = 7, C = 1 on the
   optimized layout) the tree tensor network is exact and every record must
@@ -21,7 +21,7 @@ import pytest
 
 import workloads as W
 from oracle import chp, ttn as TT
-from oracle.channels import SRX_PTA, AD_PTA, AD
+from oracle.channels import SRX_PTA, AD_PTA, AD, DEPOL
 from oracle.circuit import build_circuit
 
 pytestmark = pytest.mark.gpu
@@ -39,7 +39,9 @@ def logp_tolerance(branch_p, e=2e-5):
     (5, 5, 64, "srx_pta", SRX_PTA, 0.12, 0.0),
     (5, 5, 64, "ad_pta", AD_PTA, 0.0, 0.06),
     (7, 1, 128, "srx_pta", SRX_PTA, 0.12, 0.0),
-    (7, 1, 128, "ad_pta", AD_PTA, 0.0, 0.06)])
+    (7, 1, 128, "ad_pta", AD_PTA, 0.0, 0.06),
+    (5, 5, 64, "depol", DEPOL, 0.0, 0.02),
+    (7, 1, 128, "depol", DEPOL, 0.0, 0.02)])
 def test_pta_records_equal_tableau_oracle(d, C, chi, noise, model, th, ga):
     circ = build_circuit(d, C)
     c = P.Circuit(d, C, layout="optimized")

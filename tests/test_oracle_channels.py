@@ -50,3 +50,19 @@ def test_identity_at_zero_strength():
     # theta convention: exp(-i theta X), so theta = pi/2 is a full bit flip
     U = ch.srx_unitary(np.pi / 2)
     assert abs(U[1, 0]) == pytest.approx(1.0)
+
+
+def test_depolarizing_closed_form():
+    """DEPOL's Pauli mixture (1 - g, g/3, g/3, g/3) is the depolarizing map
+    rho -> (1 - 4g/3) rho + (4g/3) Tr(rho) I / 2, and trace preserving."""
+    from oracle.channels import DEPOL, pta_probs, PAULIS, apply_channel
+    rng = np.random.default_rng(3)
+    for g in (0.0, 0.01, 0.2, 0.75):
+        p = pta_probs(DEPOL, 0.0, g)
+        assert np.isclose(p.sum(), 1.0)
+        kraus = [np.sqrt(pi) * P for pi, P in zip(p, PAULIS)]
+        A = rng.standard_normal((2, 2)) + 1j * rng.standard_normal((2, 2))
+        rho = A @ A.conj().T
+        rho /= np.trace(rho)
+        want = (1 - 4 * g / 3) * rho + (4 * g / 3) * np.trace(rho) * np.eye(2) / 2
+        assert np.allclose(apply_channel(kraus, rho), want, atol=1e-14)

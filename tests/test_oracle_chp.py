@@ -10,7 +10,7 @@ import pytest
 
 import workloads as W
 from oracle import chp, statevector as SV
-from oracle.channels import NONE, SRX_PTA, AD_PTA
+from oracle.channels import NONE, SRX_PTA, AD_PTA, DEPOL
 from oracle.circuit import build_circuit
 
 
@@ -40,7 +40,7 @@ def test_bell_and_ghz_closed_forms():
     assert y.measure_z(0, 0.3)[0] == 1
 
 
-@pytest.mark.parametrize("model,th,ga", [(SRX_PTA, 0.12, 0.0), (AD_PTA, 0.0, 0.08)])
+@pytest.mark.parametrize("model,th,ga", [(SRX_PTA, 0.12, 0.0), (AD_PTA, 0.0, 0.08), (DEPOL, 0.0, 0.03)])
 @pytest.mark.parametrize("C", [2, 3])
 def test_equals_statevector_oracle_d3(model, th, ga, C):
     circ = build_circuit(3, C)
