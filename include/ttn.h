@@ -386,6 +386,26 @@ void ttn_pipeline_free(ttn_pipeline* pipeline);
  * a bounded wait of the tensor-core kernel expires. */
 ttn_status ttn_gram_exact(const void* M, int64_t m, int32_t n, void* G, void* cuda_stream);
 
+/* Kept eigenpairs of a batch of Hermitian positive semi-definite Gram
+ * matrices: the centre move's FP64 eigensolver (Sec. III.B: the Schmidt
+ * decomposition of a bond matrix M, taken from G = M^H M = V S^2 V^H) run on
+ * its own.  G: DEVICE [batch][n][n] row-major complex128, 16-byte aligned,
+ * read only.  route 0: cyclic Jacobi in shared memory (n^2 <= 8192);
+ * 1: Householder tridiagonalisation, Sturm bisection, inverse iteration and
+ * a Rayleigh-Ritz step in one CTA per matrix (n <= 512); 2: as 1 with the
+ * back-transformation spread over CTAs and V_k rounded to complex64 (the
+ * MIXED runs' route).  Kept: the singular values above eps_keep times the
+ * largest (for routes 1 and 2 at least sqrt(2^-52) relative), at most kcap
+ * of them, at least one.  Outputs (DEVICE): V [batch][n][kcap] complex128,
+ * the k_b kept right singular vectors as columns in descending order,
+ * columns k_b.. zero; s [batch][n] all singular values descending; k [batch]
+ * the kept ranks.  1 <= kcap <= n <= 512, 0 <= eps_keep < 1 (EINVAL
+ * otherwise).  Allocates and frees its own scratch and synchronises
+ * cuda_stream; ENUMERIC if a matrix was zero or non-finite or the Jacobi
+ * sweeps did not converge. */
+ttn_status ttn_eig_gram(const void* G, int32_t batch, int32_t n, int32_t kcap, int32_t route, double eps_keep,
+                        void* V, double* s, int32_t* k, void* cuda_stream);
+
 /* Allocation-free variant of ttn_decode.  The paper has no counterpart: it
  * serves callers that cannot allocate device memory -- an application whose
  * memory pool or caching allocator already owns the GPU, or a framework whose

@@ -10,5 +10,5 @@ from ._lib import (  # noqa: F401
     NOISE, PRECISION, LAYOUT, TTNError, Circuit, run_trajectories, logical_error_rate,
     decode, debug_state, philox_uniforms, load_library, library_path,
     profile_begin, profile_end, KERNEL_CLASSES, grad, logical_error_rate_fn, decode_noalloc,
-    run_mixed, newton_crossing, crossing, threshold_fit, grad_sums, gram_exact, Pipeline,
+    run_mixed, newton_crossing, crossing, threshold_fit, grad_sums, gram_exact, eig_gram, Pipeline,
 )

@@ -41,7 +41,7 @@ EXPORTS = ["ttn_build_circuit", "ttn_free_circuit", "ttn_circuit_info", "ttn_cir
            "ttn_circuit_layout", "ttn_run_trajectories", "ttn_logical_error_rate", "ttn_decode",
            "ttn_debug_state", "ttn_philox_uniforms", "ttn_profile_begin", "ttn_profile_end",
            "ttn_grad", "ttn_decode_noalloc", "ttn_profile_class_ms", "ttn_profile_eig_phases",
-           "ttn_profile_move_hist", "ttn_gram_exact", "ttn_pipeline_create", "ttn_pipeline_step",
+           "ttn_profile_move_hist", "ttn_gram_exact", "ttn_eig_gram", "ttn_pipeline_create", "ttn_pipeline_step",
            "ttn_pipeline_group_size", "ttn_pipeline_free", "ttn_profile_kernels", "ttn_pipeline_segment_ms",
            "ttn_run_mixed", "ttn_newton_crossing", "ttn_crossing", "ttn_threshold_fit", "ttn_grad_sums",
            "ttn_slot_check", "ttn_layout_noise_free_chi",
@@ -93,6 +93,8 @@ def load_library():
     lib.ttn_decode.argtypes = [vp, ctypes.c_uint64, vp, vp, vp, vp, vp]
     lib.ttn_decode_noalloc.argtypes = [vp, ctypes.c_uint64, vp, vp, vp, vp, vp]
     lib.ttn_gram_exact.argtypes = [vp, ctypes.c_int64, ctypes.c_int32, vp, vp]
+    lib.ttn_eig_gram.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                 ctypes.c_double, vp, vp, vp, vp]
     lib.ttn_pipeline_create.argtypes = [vp, ctypes.POINTER(RunParams), ctypes.c_int32, ctypes.c_int32, vp,
                                         ctypes.c_int32, ctypes.c_uint64, vp, ctypes.POINTER(vp)]
     lib.ttn_pipeline_step.argtypes = [vp, vp, vp, vp, vp, ctypes.POINTER(ctypes.c_int32), ctypes.c_int32, vp]
@@ -458,6 +460,34 @@ def gram_exact(M, stream=None):
     st = ctypes.c_void_p(int(stream)) if stream else None
     _check(load_library().ttn_gram_exact(_ptr(M), int(m), int(n), _ptr(G), st))
     return G
+
+
+EIG_ROUTES = {"jacobi": 0, "tridiagonal": 1, "tridiagonal_split": 2}
+
+
+def eig_gram(G, kcap=None, route="tridiagonal", eps_keep=1e-7, stream=None):
+    """ttn_eig_gram: kept right singular vectors and singular values of a
+    batch of Hermitian PSD Gram matrices G (CUDA complex128, [batch, n, n] or
+    [n, n]).  Returns (V [batch, n, kcap] complex128, s [batch, n] float64
+    descending, k [batch] int32)."""
+    import torch
+    if not isinstance(G, torch.Tensor) or not G.is_cuda or G.dtype != torch.complex128 or G.dim() not in (2, 3):
+        raise ValueError("eig_gram: G must be a complex128 CUDA tensor [batch, n, n] or [n, n]")
+    if route not in EIG_ROUTES:
+        raise ValueError("eig_gram: route must be one of %s" % sorted(EIG_ROUTES))
+    squeeze = G.dim() == 2
+    G = (G[None] if squeeze else G).contiguous()
+    B, n, n2 = G.shape
+    if n != n2:
+        raise ValueError("eig_gram: G must be square")
+    kcap = n if kcap is None else int(kcap)
+    V = torch.empty((B, n, kcap), dtype=torch.complex128, device=G.device)
+    s = torch.empty((B, n), dtype=torch.float64, device=G.device)
+    k = torch.empty((B,), dtype=torch.int32, device=G.device)
+    st = ctypes.c_void_p(int(stream)) if stream else None
+    _check(load_library().ttn_eig_gram(_ptr(G), int(B), int(n), kcap, EIG_ROUTES[route], float(eps_keep),
+                                       _ptr(V), _ptr(s), _ptr(k), st))
+    return (V[0], s[0], k[0]) if squeeze else (V, s, k)
 
 
 def decode(circuit, records):

@@ -9,7 +9,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libttn.so")
-SOURCES = ["host.cpp", "capi.cpp", "engine.cu", "decoder.cu", "gram.cu"]
+SOURCES = ["host.cpp", "capi.cpp", "engine.cu", "decoder.cu", "gram.cu", "contract.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -159,6 +159,7 @@ static constexpr int EIG_JACOBI_N = 64;
 static constexpr int TRI_UNROLL = 16;  // loads in flight per thread in L2-resident sweeps
 static constexpr int TRI_NB = 8;       // reflectors per compact-WY block of the back-transformation
 static constexpr int TRI_INV_ITERS = 2;  // inverse-iteration / orthonormalisation rounds
+static constexpr int TRI_INV_EXTRA = 3;  // at most this many further rounds after restarted columns
 static constexpr double TRI_CLUSTER_TOL = 1e-3;  // eigenvalue cluster width (relative to |T|)
 // profiling ledger: flops and bytes per class, then SM cycles per phase of
 // the tridiagonal eigensolver (summed over trajectories, thread 0's clock)
@@ -1109,7 +1110,7 @@ __global__ void __launch_bounds__(512) k_eig_tri(Dev<R> d, int v, int w, int kca
   const int leg = (w == 2 * v) ? 0 : ((w == 2 * v + 1) ? 1 : 2);
   const int n = leg == 0 ? D[2 * v] : (leg == 1 ? D[2 * v + 1] : D[v]);
   if (d.eig_nsplit > 0 && n <= d.eig_nsplit) return;  // the Jacobi solver's share
-  if ((int64_t)n * n > d.vstride || n > d.nmax || n > nth || nth > 512) {
+  if ((int64_t)n * n > d.vstride || 2 * n > d.vstride || n > d.nmax || n > nth || nth > 512) {
     if (tid == 0) {
       flag_err(d, b, ERR_CAPACITY);
       d.knew[b] = 0;
@@ -1339,6 +1340,10 @@ __global__ void __launch_bounds__(512) k_eig_tri(Dev<R> d, int v, int w, int kca
   const R sturm_down = sizeof(R) == 8 ? R(0x1p-400) : R(0x1p-50);
   const R sturm_up = sizeof(R) == 8 ? R(0x1p400) : R(0x1p50);
   const R sturm_tiny = sizeof(R) == 8 ? R(0x1p-1000) : R(0x1p-120);
+  // rows between range checks: a minor shrinks by at most b^2 >= 4 eps^2 per
+  // two rows, so eight rows stay inside FP64's range (2^-408 below the
+  // window) but not FP32's (2^-176 below it): FP32 checks every row
+  constexpr int sturm_every = sizeof(R) == 8 ? 8 : 1;
   for (int j = tid; j < n; j += nth) {
     dg[j] = (R)(dg[j] / sc);
     if (j + 1 < n) {
@@ -1378,7 +1383,7 @@ __global__ void __launch_bounds__(512) k_eig_tri(Dev<R> d, int v, int w, int kca
       // pair is rescaled by exact powers of two to stay in range
       // (sign and zero tests on the bit patterns keep the FP64 pipe to the
       // three operations of the recurrence; |T| <= 1 bounds the growth of a
-      // minor to 3x per row, so the range is checked every 8 rows)
+      // minor to 3x per row, so FP64 checks the range every 8 rows)
       R pm2 = R(1), pm1 = dg[s0] - mid;
       if (fabs(pm1) < pivmin) pm1 = -pivmin;
       int cnt = pm1 < R(0);
@@ -1388,7 +1393,7 @@ __global__ void __launch_bounds__(512) k_eig_tri(Dev<R> d, int v, int w, int kca
         cnt += sign_differs(pc, pm1);
         pm2 = pm1;
         pm1 = pc;
-        if (((i - s0) & 7) == 0) {
+        if (((i - s0) & (sturm_every - 1)) == 0) {
           const R big = fmax(fabs(pm1), fabs(pm2));
           if (big > sturm_hi) {
             pm1 *= sturm_down;
@@ -1444,8 +1449,10 @@ __global__ void __launch_bounds__(512) k_eig_tri(Dev<R> d, int v, int w, int kca
   // further apart are orthogonal to about eps |T| / gap already, so
   // Gram-Schmidt and the Rayleigh-Ritz rotation act within clusters only (the
   // cluster rule of LAPACK's stein).
+  // (FP32 vectors are orthogonal across clusters only to eps_32 / 1e-3, too
+  // coarse: FP32 takes all kept columns as one cluster)
   if (tid == 0) {
-    const R tolc = TRI_CLUSTER_TOL * fmax(fabs(lam[perm[0]]), fabs(lam[perm[k - 1]]));
+    const R tolc = sizeof(R) == 8 ? TRI_CLUSTER_TOL * fmax(fabs(lam[perm[0]]), fabs(lam[perm[k - 1]])) : R(4);
     cst[0] = 0;
     for (int a = 1; a < k; ++a) cst[a] = (lam[perm[a - 1]] - lam[perm[a]] <= tolc) ? cst[a - 1] : (short)a;
     cen[k - 1] = (short)k;
@@ -1453,11 +1460,31 @@ __global__ void __launch_bounds__(512) k_eig_tri(Dev<R> d, int v, int w, int kca
   }
   __syncthreads();
   R* cf = reinterpret_cast<R*>(pp);  // Gram-Schmidt coefficients (k <= 512)
+  R* shift = reinterpret_cast<R*>(ek);  // inverse-iteration shifts (the sub-diagonal is no longer needed)
   const int warp_id = tid >> 5, lane_id = tid & 31, nwarp = nth >> 5;
-  for (int iter = 0; iter < TRI_INV_ITERS; ++iter) {
+  // Shifts: in descending order, a kept column's shift stays at least
+  // 10 eps |T| below the previous shift of its unreduced block, so columns
+  // of one block never share a shift (LAPACK's stein perturbs close
+  // eigenvalues the same way); the vectors of a cluster then start from
+  // distinct solves and Gram-Schmidt with Rayleigh-Ritz settles its subspace.
+  {
+    R* last = cf + 512;  // last shift of each block, by its first row
+    for (int i = tid; i < n; i += nth) last[i] = R(4);
+    __syncthreads();
+    if (tid == 0)
+      for (int c = 0; c < k; ++c) {
+        const int jj = perm[c], blk = bstart[jj];
+        const R sh = fmin(lam[jj], last[blk] - R(10) * epsR);
+        shift[c] = sh;
+        last[blk] = sh;
+      }
+    __syncthreads();
+  }
+  int iters = TRI_INV_ITERS;
+  for (int iter = 0; iter < iters; ++iter) {
     if (tid < k) {
       const int c = tid, jj = perm[c], s0 = bstart[jj], e0 = bend[jj];
-      const R l = lam[jj];
+      const R l = shift[c];
       // forward elimination with partial pivoting, right-hand side carried along
       R* zc = Z + (int64_t)c * n;  // this thread's column (column-major)
       R* u0 = U0 + (int64_t)c * n;
@@ -1524,6 +1551,7 @@ __global__ void __launch_bounds__(512) k_eig_tri(Dev<R> d, int v, int w, int kca
     }
     __syncthreads();
     // classical Gram-Schmidt, twice, columns in order
+    bool restarted = false;  // uniform: every thread sees the same sums
     for (int a = 0; a < k; ++a) {
       const int jj = perm[a];
       for (int rep = 0; rep < 2; ++rep) {
@@ -1555,10 +1583,14 @@ __global__ void __launch_bounds__(512) k_eig_tri(Dev<R> d, int v, int w, int kca
           }
           // dependent on the previous columns: restart from a fresh vector
           start_vec(a, 1 + iter * 4 + rep * 2 + attempt, bstart[jj], bend[jj]);
+          restarted = true;
           __syncthreads();
         }
       }
     }
+    // a restarted column holds a random vector until inverse iterations
+    // have acted on it: two more rounds follow every restart
+    if (restarted) iters = min(max(iters, iter + 3), TRI_INV_ITERS + TRI_INV_EXTRA);
   }
   phase_mark(3);
   // Rayleigh-Ritz: TZ into U0 (column-major), H = Z^T (TZ) into U1 (k x k),
@@ -1663,6 +1695,32 @@ __global__ void __launch_bounds__(512) k_eig_tri(Dev<R> d, int v, int w, int kca
   __syncthreads();
   for (int idx = tid; idx < n * k; idx += nth) Z[idx] = TZ[idx];
   __syncthreads();
+  // residual |T z - (z^T T z) z| of every kept vector (one warp per column):
+  // above 16 sqrt(eps) |T| the vectors did not converge (reported, not fatal)
+  for (int c = warp_id; c < k; c += nwarp) {
+    const R* zc = Z + (int64_t)c * n;
+    auto tz = [&](int i) {
+      R t = dg[i] * zc[i];
+      if (i > 0) t += bt[i - 1] * zc[i - 1];
+      if (i + 1 < n) t += bt[i] * zc[i + 1];
+      return t;
+    };
+    R zz = R(0), ztz = R(0);
+    for (int i = lane_id; i < n; i += 32) {
+      zz += zc[i] * zc[i];
+      ztz += zc[i] * tz(i);
+    }
+    zz = warp_sum(zz);
+    ztz = warp_sum(ztz);
+    const R mu = zz > R(0) ? ztz / zz : R(0);
+    R r2 = R(0);
+    for (int i = lane_id; i < n; i += 32) {
+      const R e = tz(i) - mu * zc[i];
+      r2 += e * e;
+    }
+    r2 = warp_sum(r2);
+    if (lane_id == 0 && (!(fabs(zz - R(1)) <= R(1e-3)) || !(r2 <= R(256) * epsR))) flag_err(d, b, ERR_NO_CONVERGE);
+  }
 
   phase_mark(4);
   if (d.defer_bt) {
@@ -3556,3 +3614,136 @@ int pipeline_segment_ms(const PipelineImpl* p, double* ms) { return p->segment_m
 void pipeline_free(PipelineImpl* p) { delete p; }
 
 }  // namespace ttn
+
+// ---------------------------------------------------------------- standalone Gram eigensolver
+namespace ttn {
+
+// Kept columns in descending order, zero-padded to kcap, and the descending
+// singular values (square roots of the eigenvalues).  V_k is complex128
+// (vin64) or complex64 (vin32, the multi-CTA back-transformation's output).
+__global__ void k_eig_collect(Dev<double> d, const cx<float>* vin32, cx<double>* Vout, double* s, int32_t* kout,
+                              int n, int kcap) {
+  const int b = blockIdx.x;
+  const int k = d.knew[b];
+  const cx<double>* v64 = d.G + (int64_t)b * d.vstride;
+  const cx<float>* v32 = vin32 ? vin32 + (int64_t)b * d.vstride : nullptr;
+  const double* sv = d.sv + (int64_t)b * d.nmax;
+  const int32_t* perm = d.perm + (int64_t)b * d.nmax;
+  for (int idx = threadIdx.x; idx < n * kcap; idx += blockDim.x) {
+    const int x = idx / kcap, c = idx - x * kcap;
+    cx<double> z = {0.0, 0.0};
+    if (c < k) {
+      if (v32) z = {(double)v32[(int64_t)x * k + c].x, (double)v32[(int64_t)x * k + c].y};
+      else z = v64[(int64_t)x * k + c];
+    }
+    Vout[(int64_t)b * n * kcap + idx] = z;
+  }
+  for (int c = threadIdx.x; c < n; c += blockDim.x) s[(int64_t)b * n + c] = k > 0 ? sv[perm[c]] : 0.0;
+  if (threadIdx.x == 0) kout[b] = k;
+}
+
+}  // namespace ttn
+
+extern "C" ttn_status ttn_eig_gram(const void* G, int32_t batch, int32_t n, int32_t kcap, int32_t route,
+                                   double eps_keep, void* V, double* s, int32_t* k, void* cuda_stream) {
+  using namespace ttn;
+  const int64_t jac_max = (int64_t)EIG_SMEM_MAX / (int64_t)sizeof(cx<double>);
+  if (!G || !V || !s || !k || batch < 1 || n < 1 || n > 512 || kcap < 1 || kcap > n || route < 0 ||
+      route > 2 || !(eps_keep >= 0.0 && eps_keep < 1.0) || (route == 0 && (int64_t)n * n > jac_max)) {
+    set_error("ttn_eig_gram: need device G [batch][n][n], V [batch][n][kcap], s [batch][n], k [batch]; "
+              "1 <= kcap <= n <= 512 (n^2 <= 8192 for route 0), route 0..2, 0 <= eps_keep < 1");
+    return TTN_EINVAL;
+  }
+  if ((reinterpret_cast<uintptr_t>(G) & 15) || (reinterpret_cast<uintptr_t>(V) & 15)) {
+    set_error("ttn_eig_gram: G and V must be 16-byte aligned");
+    return TTN_EINVAL;
+  }
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  // a slot holds n x n (and the deferred route's 2n phases and reflector scalars)
+  const int64_t vs = std::max<int64_t>((int64_t)n * n, 2 * (int64_t)n), B = batch;
+  Dev<double> d{};
+  Dev<float> df{};
+  d.ds = 4;
+  d.vstride = vs;
+  d.nmax = n;
+  d.eps_gram = eps_keep;
+  d.tol_gram = 1e-13;
+  d.tol_abs_gram = 1e-15;
+  d.max_sweeps = 40;
+  d.defer_bt = route == 2 ? 1 : 0;
+  d.eig_smem_bytes = route == 0 ? (int)(vs * (int64_t)sizeof(cx<double>)) : 0;
+  df.vstride = vs;
+  void* pool = nullptr;
+  const size_t b_cx = sizeof(cx<double>) * (size_t)(vs * B);
+  const size_t b_total = 4 * b_cx + sizeof(cx<float>) * (size_t)(vs * B) + (sizeof(double) + sizeof(int32_t)) * n * B +
+                         sizeof(int32_t) * (size_t)B * (d.ds + 6) + sizeof(double) * B + 4096;
+  cudaError_t e = cudaMalloc(&pool, b_total);
+  if (e == cudaSuccess) {
+    unsigned char* p = static_cast<unsigned char*>(pool);
+    auto take = [&](size_t bytes) {
+      unsigned char* q = p;
+      p += (bytes + 255) / 256 * 256;
+      return q;
+    };
+    d.G = reinterpret_cast<cx<double>*>(take(b_cx));
+    d.V = reinterpret_cast<cx<double>*>(take(b_cx));
+    d.Ts = reinterpret_cast<cx<double>*>(take(2 * b_cx));
+    df.G = reinterpret_cast<cx<float>*>(take(sizeof(cx<float>) * (size_t)(vs * B)));
+    d.sv = reinterpret_cast<double*>(take(sizeof(double) * n * B));
+    d.perm = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * n * B));
+    d.dims = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * d.ds * B));
+    d.knew = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * B));
+    d.nold = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * B));
+    d.trunc = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * B));
+    d.err = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * B));
+    d.err_step = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * 2 * B));
+    d.frob = reinterpret_cast<double*>(take(sizeof(double) * B));
+    // one move of node 1 towards its left child 2, whose bond has dimension n
+    std::vector<int32_t> dims((size_t)d.ds * B, 1);
+    for (int64_t b = 0; b < B; ++b) dims[(size_t)b * d.ds + 2] = n;
+    e = cudaMemcpyAsync(d.dims, dims.data(), sizeof(int32_t) * dims.size(), cudaMemcpyHostToDevice, st);
+    // matrix b at b * n^2 in G, at b * vs in the solver's slots
+    if (e == cudaSuccess)
+      e = cudaMemcpy2DAsync(d.G, sizeof(cx<double>) * (size_t)vs, G, sizeof(cx<double>) * (size_t)n * n,
+                            sizeof(cx<double>) * (size_t)n * n, (size_t)B, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d.err, 0, sizeof(int32_t) * B, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d.err_step, 0xFF, sizeof(int32_t) * 2 * B, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d.knew, 0, sizeof(int32_t) * B, st);
+    if (e == cudaSuccess && route == 0)
+      e = cudaFuncSetAttribute(k_eig<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, EIG_SMEM_MAX);
+    if (e == cudaSuccess && route > 0)
+      e = cudaFuncSetAttribute(k_eig_tri<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               tri_smem_bytes<double>());
+    if (e == cudaSuccess && route == 2)
+      e = cudaFuncSetAttribute(k_eig_bt, cudaFuncAttributeMaxDynamicSharedMemorySize, bt_smem_bytes());
+    if (e == cudaSuccess) {
+      if (route == 0) {
+        k_eig<double><<<batch, 512, d.eig_smem_bytes, st>>>(d, 1, 2, kcap);
+      } else {
+        k_eig_tri<double><<<batch, 512, route == 2 ? tri_smem_bytes_nobt<double>() : tri_smem_bytes<double>(), st>>>(
+            d, 1, 2, kcap);
+        if (route == 2)
+          k_eig_bt<<<dim3((unsigned)ceil_div(kcap, BT_COLS), batch), 256, bt_smem_bytes(), st>>>(df, d);
+      }
+      k_eig_collect<<<batch, 256, 0, st>>>(d, route == 2 ? df.G : nullptr, static_cast<cx<double>*>(V), s, k, n,
+                                           kcap);
+      e = cudaGetLastError();
+    }
+  }
+  std::vector<int32_t> herr(batch, 0);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(herr.data(), d.err, sizeof(int32_t) * B, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(pool);
+  if (e != cudaSuccess) {
+    set_error(std::string("CUDA: ttn_eig_gram: ") + cudaGetErrorString(e));
+    return TTN_ECUDA;
+  }
+  for (int b = 0; b < batch; ++b)
+    if (herr[b]) {
+      set_error("ttn_eig_gram: matrix " + std::to_string(b) + ": error flags " + std::to_string(herr[b]) +
+                " (1 zero matrix, 2 no convergence, 4 capacity, 8 non-finite)");
+      return TTN_ENUMERIC;
+    }
+  return TTN_OK;
+}

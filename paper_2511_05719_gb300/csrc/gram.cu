@@ -40,26 +40,12 @@
 
 #include "gram.h"
 #include "internal.h"
+#include "digit_gemm.cuh"
 #include "tc100.cuh"
 
 namespace ttn {
 
-static constexpr int G_KT = 32;                  // rows of M per K-tile
-static constexpr int G_TA = 128;                 // X-columns per A tile (MMA M)
-static constexpr int G_TB = 64;                  // X-columns per B tile (MMA N)
-static constexpr int G_TILE = G_TA * G_KT;       // bf16 elements of a packed 128 x 32 tile (8 KB)
-static constexpr int G_TILE_B = G_TILE * 2;      // its bytes
-static constexpr int G_SBO = G_KT / 8 * 128;     // bytes between 8-column groups of a tile
-static constexpr int G_CHUNK = 256 / G_KT;       // K-tiles per exact FP32 accumulation (256 rows)
 static constexpr int G_SPLIT = 4096 / G_KT;      // K-tiles per CTA (4096 rows)
-static constexpr int G_NS = 3;                   // pipeline stages
-static constexpr int G_STAGE = 3 * G_TILE_B + 3 * (G_TILE_B / 2);  // A digits (128 rows) + B digits (64)
-static constexpr int G_SMEM = G_NS * G_STAGE;    // dynamic shared memory of k_gram_mma
-static constexpr uint32_t G_WAIT = 1u << 22;     // polls of a bounded mbarrier wait
-// tensor memory: five 64-column FP32 accumulators (columns 0..319), then the
-// row's 64-bit fixed-point sums as low (320..383) and high (384..447) words
-static constexpr int G_TMEM_COLS = 512;
-static constexpr int G_TM_LO = 5 * G_TB, G_TM_HI = 6 * G_TB;
 
 __host__ __device__ inline int g_nct(int n) { return (2 * n + G_TA - 1) / G_TA; }
 __host__ __device__ inline int g_nkt(int64_t m) { return (int)((m + G_KT - 1) / G_KT); }
@@ -140,14 +126,10 @@ __global__ void __launch_bounds__(256) k_gram_pack(GramArgs a) {
         if (!isfinite(x)) {
           bad = true;
         } else {
-          const int N = __float2int_rn(ldexpf(x, 23 - E[c]));
-          n1 = (N + 32768) >> 16;
-          const int r1 = N - n1 * 65536;
-          n2 = (r1 + 128) >> 8;
-          n3 = r1 - n2 * 256;
+          digits3(x, E[c], n1, n2, n3);
         }
       }
-      const int off = (cc >> 3) * (G_SBO / 2) + (rr >> 3) * 64 + (cc & 7) * 8 + (rr & 7);
+      const int off = digit_offset(cc, rr);
       t0[off] = __bfloat16_as_ushort(__float2bfloat16_rn((float)n1));
       t1[off] = __bfloat16_as_ushort(__float2bfloat16_rn((float)n2));
       t2[off] = __bfloat16_as_ushort(__float2bfloat16_rn((float)n3));
@@ -159,13 +141,10 @@ __global__ void __launch_bounds__(256) k_gram_pack(GramArgs a) {
 // ---------------------------------------------------------------- 3. tensor-core products
 // CTA = (tile pair, row split, trajectory).  Tile pair: 128 X-columns ta (MMA
 // rows) x 64 X-columns tb (MMA columns), tb >= 2 ta (the upper triangle of
-// X^T X in 64-column blocks).  Thread t of the four warps owns accumulator
-// row t (TMEM lane t); thread 0 also issues the bulk copies and the MMAs.
+// X^T X in 64-column blocks).  The digit products and their exact integer
+// sums are digit_gemm's (digit_gemm.cuh); the epilogue adds each row's sums
+// into the trajectory's int64 matrix.
 __global__ void __launch_bounds__(128, 1) k_gram_mma(GramArgs a, int nct_cap) {
-  extern __shared__ __align__(1024) unsigned char g_smem[];
-  __shared__ __align__(8) uint64_t bar_load[G_NS], bar_mma[G_NS], bar_acc;
-  __shared__ uint32_t tmem_slot;
-  __shared__ int s_abort;
   const int b = blockIdx.z;
   const int2 sh = a.shape[b];
   const int64_t m = sh.x;
@@ -184,172 +163,21 @@ __global__ void __launch_bounds__(128, 1) k_gram_mma(GramArgs a, int nct_cap) {
   const int kt1 = min(NKT, kt0 + G_SPLIT);
   if (d_slice_elems(m, n) > a.sstride) return;  // flagged by the packing kernel
 
-  const int tid = threadIdx.x, warp = tid >> 5;
-  if (tid == 0) {
-    for (int i = 0; i < G_NS; ++i) {
-      tc::mbar_init(&bar_load[i], 1);
-      tc::mbar_init(&bar_mma[i], 1);
-    }
-    tc::mbar_init(&bar_acc, 1);
-    tc::mbar_fence_init();
-    s_abort = 0;
-  }
-  if (warp == 0) tc::tmem_alloc(&tmem_slot, G_TMEM_COLS);
-  tc::tc_fence_before();
-  __syncthreads();
-  tc::tc_fence_after();
-  const uint32_t tmem = tmem_slot;
-  const uint32_t lane_off = (uint32_t)(warp * 32) << 16;  // this warp's TMEM lane quarter
-
   const uint16_t* S = a.slices + (int64_t)b * a.sstride;
   auto srcA = [&](int s, int kt) { return S + ((int64_t)(s * NCT + ta) * NKT + kt) * G_TILE; };
   auto srcB = [&](int s, int kt) {
     return S + ((int64_t)(s * NCT + (tb >> 1)) * NKT + kt) * G_TILE + (tb & 1) * (G_TILE / 2);
   };
-  auto stage = [&](int st) { return g_smem + st * G_STAGE; };
-  auto issue_load = [&](int st, int kt) {
-    tc::mbar_expect_tx(&bar_load[st], G_STAGE);
-    for (int s = 0; s < 3; ++s) tc::bulk_g2s(stage(st) + s * G_TILE_B, srcA(s, kt), G_TILE_B, &bar_load[st]);
-    for (int s = 0; s < 3; ++s)
-      tc::bulk_g2s(stage(st) + 3 * G_TILE_B + s * (G_TILE_B / 2), srcB(s, kt), G_TILE_B / 2, &bar_load[st]);
+  const int arow = ta * G_TA + threadIdx.x;
+  unsigned long long* F = a.gfix + (int64_t)b * a.gld * a.gld + (int64_t)arow * a.gld;
+  auto epilogue = [&](int h, const unsigned long long (&v)[32]) {
+    if (arow >= nc) return;
+    for (int j = 0; j < 32; ++j) {
+      const int c = tb * G_TB + h * 32 + j;
+      if (c >= arow && c < nc && v[j] != 0ull) atomicAdd(&F[c], v[j]);
+    }
   };
-
-  const uint32_t idesc = tc::instr_desc(1, G_TA, G_TB);
-  const int nk = kt1 - kt0;
-  int loads[G_NS], commits[G_NS];  // per stage: bulk loads issued, MMA commits (thread 0)
-  for (int i = 0; i < G_NS; ++i) loads[i] = commits[i] = 0;
-  if (tid == 0)
-    for (int i = 0; i < G_NS - 1 && i < nk; ++i) {
-      issue_load(i, kt0 + i);
-      loads[i]++;
-    }
-  uint32_t acc_phase = 0;
-  bool first_chunk = true;
-  bool first[5] = {true, true, true, true, true};
-  for (int i = 0; i < nk; ++i) {
-    const int st = i % G_NS;
-    const bool chunk_end = (i % G_CHUNK) == G_CHUNK - 1 || i == nk - 1;
-    if (tid == 0 && !s_abort) {
-      if (!tc::mbar_wait(&bar_load[st], (uint32_t)((i / G_NS) & 1), G_WAIT)) {
-        s_abort = 1;
-      } else {
-        tc::tc_fence_after();
-        if (i % G_CHUNK == 0)
-          for (int g = 0; g < 5; ++g) first[g] = true;
-        const uint32_t sa = tc::smem_u32(stage(st)), sb = sa + 3 * G_TILE_B;
-#pragma unroll
-        for (int ks = 0; ks < G_KT / 16; ++ks) {
-#pragma unroll
-          for (int s1 = 0; s1 < 3; ++s1) {
-#pragma unroll
-            for (int s2 = 0; s2 < 3; ++s2) {
-              const int g = s1 + s2;
-              const uint64_t ad = tc::smem_desc(sa + s1 * G_TILE_B + ks * 256, 128, G_SBO);
-              const uint64_t bd = tc::smem_desc(sb + s2 * (G_TILE_B / 2) + ks * 256, 128, G_SBO);
-              tc::mma_bf16(tmem + g * G_TB, ad, bd, idesc, first[g] ? 0u : 1u);
-              first[g] = false;
-            }
-          }
-        }
-        tc::mma_commit(&bar_mma[st]);
-        commits[st]++;
-        // tile i + NS - 1 goes into the stage tile i - 1 used, once its MMAs are done
-        const int nx = i + G_NS - 1;
-        if (nx < nk) {
-          const int so = nx % G_NS;
-          bool ok = true;
-          if (commits[so] > 0) ok = tc::mbar_wait(&bar_mma[so], (uint32_t)((commits[so] - 1) & 1), G_WAIT);
-          if (!ok) {
-            s_abort = 1;
-          } else {
-            issue_load(so, kt0 + nx);
-            loads[so]++;
-          }
-        }
-        if (chunk_end) tc::mma_commit(&bar_acc);
-      }
-    }
-    if (chunk_end) {
-      __syncthreads();
-      if (s_abort) break;
-      // every thread polls; the block agrees on the outcome before the
-      // warp-collective TMEM loads
-      const int ok = __syncthreads_and(tc::mbar_wait(&bar_acc, acc_phase, G_WAIT) ? 1 : 0);
-      acc_phase ^= 1u;
-      if (!ok) {
-        if (tid == 0) s_abort = 1;
-        break;
-      }
-      tc::tc_fence_after();
-#pragma unroll
-      for (int h = 0; h < G_TB / 32; ++h) {
-        long long part[32];
-#pragma unroll
-        for (int j = 0; j < 32; ++j) part[j] = 0;
-#pragma unroll
-        for (int g = 0; g < 5; ++g) {
-          uint32_t r[32];
-          tc::tmem_ld32(tmem + lane_off + g * G_TB + h * 32, r);
-          tc::tmem_ld_wait();
-#pragma unroll
-          for (int j = 0; j < 32; ++j)
-            part[j] += (long long)__float2int_rn(__uint_as_float(r[j])) << (8 * (4 - g));
-        }
-        uint32_t lo[32], hi[32];
-        if (!first_chunk) {
-          tc::tmem_ld32(tmem + lane_off + G_TM_LO + h * 32, lo);
-          tc::tmem_ld32(tmem + lane_off + G_TM_HI + h * 32, hi);
-          tc::tmem_ld_wait();
-#pragma unroll
-          for (int j = 0; j < 32; ++j) part[j] += (long long)(((uint64_t)hi[j] << 32) | lo[j]);
-        }
-#pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          lo[j] = (uint32_t)(uint64_t)part[j];
-          hi[j] = (uint32_t)((uint64_t)part[j] >> 32);
-        }
-        tc::tmem_st32(tmem + lane_off + G_TM_LO + h * 32, lo);
-        tc::tmem_st32(tmem + lane_off + G_TM_HI + h * 32, hi);
-        tc::tmem_st_wait();
-      }
-      first_chunk = false;
-      tc::tc_fence_before();
-      __syncthreads();
-    }
-  }
-  __syncthreads();
-  if (s_abort) {
-    // let the copies and MMAs already issued finish (bounded) before the
-    // shared memory and tensor memory are released
-    if (tid == 0) {
-      tc::mma_commit(&bar_acc);
-      tc::mbar_wait(&bar_acc, acc_phase, G_WAIT);
-      for (int st = 0; st < G_NS; ++st)
-        if (loads[st] > 0) tc::mbar_wait(&bar_load[st], (uint32_t)((loads[st] - 1) & 1), G_WAIT);
-      g_flag(a, b, GRAM_ERR_TIMEOUT);
-    }
-  } else {
-    tc::tc_fence_after();
-    const int arow = ta * G_TA + tid;
-    unsigned long long* F = a.gfix + (int64_t)b * a.gld * a.gld + (int64_t)arow * a.gld;
-    for (int h = 0; h < G_TB / 32; ++h) {
-      uint32_t lo[32], hi[32];
-      tc::tmem_ld32(tmem + lane_off + G_TM_LO + h * 32, lo);
-      tc::tmem_ld32(tmem + lane_off + G_TM_HI + h * 32, hi);
-      tc::tmem_ld_wait();
-      if (arow < nc) {
-        for (int j = 0; j < 32; ++j) {
-          const int c = tb * G_TB + h * 32 + j;
-          const unsigned long long v = ((unsigned long long)hi[j] << 32) | lo[j];
-          if (c >= arow && c < nc && v != 0ull) atomicAdd(&F[c], v);
-        }
-      }
-    }
-  }
-  tc::tc_fence_before();
-  __syncthreads();
-  tc::tc_fence_after();
-  if (warp == 0) tc::tmem_dealloc(tmem, G_TMEM_COLS);
+  if (!digit_gemm(kt0, kt1 - kt0, srcA, srcB, epilogue) && threadIdx.x == 0) g_flag(a, b, GRAM_ERR_TIMEOUT);
 }
 
 // ---------------------------------------------------------------- 4. complex FP64 Gram
