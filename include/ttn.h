@@ -66,7 +66,9 @@ typedef enum {
  * (cyclic Jacobi for bonds up to 64, tridiagonal above), the kept rank and
  * the singular values in double -- and probabilities, log-probabilities and
  * discarded weights in double.  svd_mode is ignored in MIXED runs; their
- * contractions use the FP32 FMA units unless gemm_mode = 2. */
+ * contractions Y = M V_k and the neighbour absorb are exact digit products
+ * on the tcgen05 tensor cores as well (one final rounding to complex64)
+ * unless gemm_mode asks for the FMA units (1) or the 3xTF32 tile (2). */
 typedef enum { TTN_PREC_FP64 = 0, TTN_PREC_FP32 = 1, TTN_PREC_MIXED = 2 } ttn_precision;
 
 /* Qubit -> TTN leaf assignment (App. B).  DEFAULT: qubit i on leaf i.
@@ -135,7 +137,9 @@ typedef struct {
                                     on Gram-path moves), 1 FP32 FMA units,
                                     2 tensor cores for every move.  Tensor
                                     cores use TF32 with a 3-term split
-                                    (FP32-level accuracy).  FP64 runs ignore
+                                    (FP32-level accuracy).  MIXED runs: 0
+                                    exact tcgen05 digit products, 1 FMA, 2
+                                    the 3xTF32 tile.  FP64 runs ignore
                                     it.                                   */
 } ttn_run_params;
 
@@ -349,7 +353,9 @@ ttn_status ttn_decode(const ttn_circuit* circuit, uint64_t n, const uint8_t* rec
  * resident batch (0: 85 % of free memory; ENOMEM if it does not fit).
  * The groups' streams overlap only if the GPU has as many hardware work
  * queues: set CUDA_DEVICE_MAX_CONNECTIONS (up to 32) above n_segments before
- * the process starts CUDA.  *out: library-owned handle, released by
+ * the process starts CUDA.  The host enqueues the groups' launches
+ * interleaved, TTN_PIPELINE_CHUNK (environment, default 16) program steps of
+ * one group at a time.  *out: library-owned handle, released by
  * ttn_pipeline_free. */
 typedef struct ttn_pipeline ttn_pipeline;
 ttn_status ttn_pipeline_create(const ttn_circuit* circuit, const ttn_run_params* params, int32_t n_resident,
@@ -393,8 +399,9 @@ ttn_status ttn_gram_exact(const void* M, int64_t m, int32_t n, void* G, void* cu
  * read only.  route 0: cyclic Jacobi in shared memory (n^2 <= 8192);
  * 1: Householder tridiagonalisation, Sturm bisection, inverse iteration and
  * a Rayleigh-Ritz step in one CTA per matrix (n <= 512); 2: as 1 with the
- * back-transformation spread over CTAs and V_k rounded to complex64 (the
- * MIXED runs' route).  Kept: the singular values above eps_keep times the
+ * back-transformation spread over CTAs and V_k rounded to complex64; 3: the
+ * MIXED runs' combination -- route 2, with bonds up to 64 taken by the
+ * Jacobi body inside the same launch.  Kept: the singular values above eps_keep times the
  * largest (for routes 1 and 2 at least sqrt(2^-52) relative), at most kcap
  * of them, at least one.  Outputs (DEVICE): V [batch][n][kcap] complex128,
  * the k_b kept right singular vectors as columns in descending order,

@@ -462,7 +462,7 @@ def gram_exact(M, stream=None):
     return G
 
 
-EIG_ROUTES = {"jacobi": 0, "tridiagonal": 1, "tridiagonal_split": 2}
+EIG_ROUTES = {"jacobi": 0, "tridiagonal": 1, "tridiagonal_split": 2, "mixed": 3}
 
 
 def eig_gram(G, kcap=None, route="tridiagonal", eps_keep=1e-7, stream=None):

@@ -19,9 +19,11 @@
 // leave the sum), rounded to 23 bits below its largest entry and split into
 // bf16 digits; the tensor cores then sum the integer products exactly, and
 // one rounding (int64 -> double, then -> float) gives each entry.  So the
-// contraction is exact for its 23-bit-rounded inputs -- more accurate than
-// an FP32 FMA loop, and free of the truncating accumulation of the legacy
-// 3xTF32 mma.sync tile.
+// contraction is exact for its rounded inputs and free of the truncating
+// accumulation of the legacy 3xTF32 mma.sync tile; entries far below their
+// row's maximum keep fewer than FP32's 24 significant bits, so the result is
+// not more accurate than FP32 FMA sums in general (both hold the MIXED
+// amplitude bars).
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 

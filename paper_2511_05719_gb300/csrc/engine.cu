@@ -18,11 +18,13 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
 
 #include "engine.h"
+#include "contract.h"
 #include "gram.h"
 
 namespace ttn {
@@ -161,6 +163,10 @@ static constexpr int TRI_NB = 8;       // reflectors per compact-WY block of the
 static constexpr int TRI_INV_ITERS = 2;  // inverse-iteration / orthonormalisation rounds
 static constexpr int TRI_INV_EXTRA = 3;  // at most this many further rounds after restarted columns
 static constexpr double TRI_CLUSTER_TOL = 1e-3;  // eigenvalue cluster width (relative to |T|)
+// the same when V_k is rounded to complex64 afterwards (deferred
+// back-transformation): eps_64 / 1e-7 = 2.2e-9 of cross-cluster
+// non-orthogonality stays far below the 2^-24 rounding that follows
+static constexpr double TRI_CLUSTER_TOL_C64 = 1e-7;
 // profiling ledger: flops and bytes per class, then SM cycles per phase of
 // the tridiagonal eigensolver (summed over trajectories, thread 0's clock)
 static constexpr int LEDGER_WORDS = 2 * NCLASS + EIG_PHASES + MOVE_HIST_WORDS;
@@ -875,11 +881,12 @@ __device__ void eig_select_tail(Dev<R>& d, int b, int v, int w, int kcap, int n,
   }
 }
 
-// Eigen-decomposition of G by cyclic two-sided Jacobi; then the kept rank,
-// V_k S_k^-1 (into G) and R = S_k V_k^H (into Rm).
+// Eigen-decomposition of G by cyclic two-sided Jacobi; then the kept rank
+// and V_k (into G).  The body of k_eig, and of k_eig_tri for the bonds at or
+// below eig_nsplit (MIXED runs: one eigensolver launch per move); smem: the
+// launch's dynamic shared memory (d.eig_smem_bytes of it).
 template <typename R>
-__global__ void __launch_bounds__(512) k_eig(Dev<R> d, int v, int w, int kcap) {
-  const long long clk_entry = clock64();
+__device__ void eig_jacobi(Dev<R>& d, int v, int w, int kcap, unsigned char* eig_smem, long long clk_entry) {
   const int b = blockIdx.x;
   const int tid = threadIdx.x, nth = blockDim.x;
   int* D = d.dims + b * d.ds;
@@ -890,14 +897,12 @@ __global__ void __launch_bounds__(512) k_eig(Dev<R> d, int v, int w, int kcap) {
   cx<R>* V = d.V + (int64_t)b * d.vstride;
   double* sv = d.sv + (int64_t)b * d.nmax;
   // G lives in shared memory when the launch provides room for n x n
-  extern __shared__ __align__(16) unsigned char eig_smem[];
   const bool in_smem = (int64_t)n * n * sizeof(cx<R>) <= (int64_t)d.eig_smem_bytes;
   cx<R>* G = in_smem ? reinterpret_cast<cx<R>*>(eig_smem) : Gglob;
   __shared__ R pc[256], ps[256];
   __shared__ cx<R> pe[256];
   __shared__ int pp[256], pq[256];
   __shared__ double s_tr;
-  if (d.eig_nsplit > 0 && n > d.eig_nsplit) return;  // the tridiagonal solver's share
   if ((int64_t)n * n > d.vstride || n > d.nmax || n > 512) {
     if (tid == 0) {
       flag_err(d, b, ERR_CAPACITY);
@@ -998,6 +1003,17 @@ __global__ void __launch_bounds__(512) k_eig(Dev<R> d, int v, int w, int kcap) {
   for (int j = tid; j < n; j += nth) sv[j] = (double)G[(int64_t)j * n + j].x;  // eigenvalues
   __syncthreads();
   eig_select_tail(d, b, v, w, kcap, n, V, Gglob, s_tr, clk_entry);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(512) k_eig(Dev<R> d, int v, int w, int kcap) {
+  const long long clk_entry = clock64();
+  extern __shared__ __align__(16) unsigned char eig_smem[];
+  const int* D = d.dims + blockIdx.x * d.ds;
+  const int leg = (w == 2 * v) ? 0 : ((w == 2 * v + 1) ? 1 : 2);
+  const int n = leg == 0 ? D[2 * v] : (leg == 1 ? D[2 * v + 1] : D[v]);
+  if (d.eig_nsplit > 0 && n > d.eig_nsplit) return;  // the tridiagonal solver's share
+  eig_jacobi(d, v, w, kcap, eig_smem, clk_entry);
 }
 
 // Block-wide sums (blockDim.x a multiple of 32); red holds 64 doubles.
@@ -1109,7 +1125,11 @@ __global__ void __launch_bounds__(512) k_eig_tri(Dev<R> d, int v, int w, int kca
   const int* D = d.dims + b * d.ds;
   const int leg = (w == 2 * v) ? 0 : ((w == 2 * v + 1) ? 1 : 2);
   const int n = leg == 0 ? D[2 * v] : (leg == 1 ? D[2 * v + 1] : D[v]);
-  if (d.eig_nsplit > 0 && n <= d.eig_nsplit) return;  // the Jacobi solver's share
+  extern __shared__ __align__(16) unsigned char tri_smem[];
+  if (d.eig_nsplit > 0 && n <= d.eig_nsplit) {  // the Jacobi solver's share
+    if (d.eig_smem_bytes > 0) eig_jacobi(d, v, w, kcap, tri_smem, clk_entry);
+    return;
+  }
   if ((int64_t)n * n > d.vstride || 2 * n > d.vstride || n > d.nmax || n > nth || nth > 512) {
     if (tid == 0) {
       flag_err(d, b, ERR_CAPACITY);
@@ -1127,7 +1147,6 @@ __global__ void __launch_bounds__(512) k_eig_tri(Dev<R> d, int v, int w, int kca
   R* U2 = U1 + (int64_t)n * n;
   double* sv = d.sv + (int64_t)b * d.nmax;
   const int32_t* perm = d.perm + (int64_t)b * d.nmax;
-  extern __shared__ __align__(16) unsigned char tri_smem[];
   cx<R>* vk = reinterpret_cast<cx<R>*>(tri_smem);  // reflector of the current step
   cx<R>* wk = vk + 512;                             // w = p - K v; later the phases D
   cx<R>* vn = wk + 512;                             // next reflector; later b^2, lambda
@@ -1161,9 +1180,10 @@ __global__ void __launch_bounds__(512) k_eig_tri(Dev<R> d, int v, int w, int kca
     dg[1] = A[3].x;
   }
   if (n >= 3) {
-    // Five barriers per step: reductions (|x|^2 of the next reflector's
+    // Six barriers per step: reductions (|x|^2 of the next reflector's
     // column, v^H p) are per-warp partials written during the preceding
     // pass and summed in warp order after its barrier (deterministic).
+    // Only the lower triangle of the trailing block is kept current.
     const int wid = tid >> 5, lid = tid & 31, nw = nth >> 5;
     tri_reflector(A, n, 0, vk, tau, ek, red);
     {  // p_0 = tau_0 A[1:, 1:] v_0 and v_0^H p_0
@@ -1258,16 +1278,18 @@ __global__ void __launch_bounds__(512) k_eig_tri(Dev<R> d, int v, int w, int kca
       __syncthreads();  // B3: vn, tau[o] visible; x0 read by everyone
       if (has_next)  // v stored below the diagonal of column o
         for (int r = tid; r < m - 1; r += nth) A[(int64_t)(o + 1 + r) * n + o] = vn[r];
-      // (d) rank-2 update of rows/cols o+1.. fused with p_next = A' v_next
+      // (d) rank-2 update of the lower triangle of rows/cols o+1.. (the
+      // upper one is never read again: FP64 is the binding unit, so the
+      // Hermitian half is not recomputed), then p_next = A' v_next from the
+      // lower triangle read by columns (j >= col) and by rows (j < col)
       const int mp = m - 1;
       if (mp > 0) {
         const int G = nth / mp, col = tid % mp, g = tid / mp;
+        cx<R>* colp = A + (int64_t)(o + 1) * n + o + 1 + col;
         if (g < G) {
           const cx<R> cvi = {vk[1 + col].x, -vk[1 + col].y}, cwi = {wk[1 + col].x, -wk[1 + col].y};
-          cx<R> acc = {R(0), R(0)};
-          cx<R>* colp = A + (int64_t)(o + 1) * n + o + 1 + col;
           // TRI_UNROLL rows per batch: all loads issued before any store
-          for (int j0 = g; j0 < mp; j0 += G * TRI_UNROLL) {
+          for (int j0 = col + g; j0 < mp; j0 += G * TRI_UNROLL) {
             cx<R> a[TRI_UNROLL];
 #pragma unroll
             for (int u = 0; u < TRI_UNROLL; ++u) {
@@ -1281,11 +1303,31 @@ __global__ void __launch_bounds__(512) k_eig_tri(Dev<R> d, int v, int w, int kca
                 const cx<R> t1 = cmul(vk[1 + j], cwi), tt = cmul(wk[1 + j], cvi);
                 a[u] = {a[u].x - t1.x - tt.x, a[u].y - t1.y - tt.y};
                 colp[(int64_t)j * n] = a[u];
-                if (has_next) acc = cadd(acc, cmulc(a[u], vn[j]));
               }
             }
           }
-          if (has_next) pp[g * mp + col] = acc;
+        }
+        if (has_next) {
+          __syncthreads();  // B4a: the updated lower triangle is visible
+          if (g < G) {
+            const cx<R>* rowp = A + (int64_t)(o + 1 + col) * n + o + 1;  // row col, entries j < col
+            cx<R> acc = {R(0), R(0)};
+            for (int j0 = g; j0 < mp; j0 += G * TRI_UNROLL) {
+              cx<R> a[TRI_UNROLL];
+#pragma unroll
+              for (int u = 0; u < TRI_UNROLL; ++u) {
+                const int j = j0 + u * G;
+                if (j < mp) a[u] = j >= col ? colp[(int64_t)j * n] : rowp[j];
+              }
+#pragma unroll
+              for (int u = 0; u < TRI_UNROLL; ++u) {
+                const int j = j0 + u * G;
+                // A'[col][j] = conj(A'[j][col]) from the column, itself from the row
+                if (j < mp) acc = cadd(acc, j >= col ? cmulc(a[u], vn[j]) : cmul(a[u], vn[j]));
+              }
+            }
+            pp[g * mp + col] = acc;
+          }
         }
         __syncthreads();  // B4
         if (has_next) {
@@ -1445,14 +1487,16 @@ __global__ void __launch_bounds__(512) k_eig_tri(Dev<R> d, int v, int w, int kca
     start_vec(c, 0, bstart[jj], bend[jj]);
   }
   // clusters of kept eigenvalues (descending order): neighbours closer than
-  // TRI_CLUSTER_TOL |T| share one.  Inverse-iteration vectors of eigenvalues
-  // further apart are orthogonal to about eps |T| / gap already, so
-  // Gram-Schmidt and the Rayleigh-Ritz rotation act within clusters only (the
-  // cluster rule of LAPACK's stein).
+  // TRI_CLUSTER_TOL |T| (TRI_CLUSTER_TOL_C64 when V_k is rounded to
+  // complex64) share one.  Inverse-iteration vectors of eigenvalues further
+  // apart are orthogonal to about eps |T| / gap already, so Gram-Schmidt and
+  // the Rayleigh-Ritz rotation act within clusters only (the cluster rule of
+  // LAPACK's stein); their cost grows with the square of a cluster's size.
   // (FP32 vectors are orthogonal across clusters only to eps_32 / 1e-3, too
   // coarse: FP32 takes all kept columns as one cluster)
   if (tid == 0) {
-    const R tolc = sizeof(R) == 8 ? TRI_CLUSTER_TOL * fmax(fabs(lam[perm[0]]), fabs(lam[perm[k - 1]])) : R(4);
+    const double crel = d.defer_bt ? TRI_CLUSTER_TOL_C64 : TRI_CLUSTER_TOL;
+    const R tolc = sizeof(R) == 8 ? (R)crel * fmax(fabs(lam[perm[0]]), fabs(lam[perm[k - 1]])) : R(4);
     cst[0] = 0;
     for (int a = 1; a < k; ++a) cst[a] = (lam[perm[a - 1]] - lam[perm[a]] <= tolc) ? cst[a - 1] : (short)a;
     cen[k - 1] = (short)k;
@@ -1944,10 +1988,20 @@ __global__ void __launch_bounds__(256) k_unorm_apply(Dev<R> d, int v, int w) {
 // CTA of k_eig_tri would apply them to all k columns itself; here the k
 // columns take k / BT_COLS SMs at once.
 static constexpr int BT_COLS = 16;
+// dynamic shared memory of k_eig_bt for bonds up to nm (the launch's capacity)
+__host__ __device__ constexpr int bt_smem_bytes(int nm = 512) {
+  return (nm * BT_COLS + nm + 16 * BT_COLS) * (int)sizeof(cx<double>);
+}
 __global__ void __launch_bounds__(256) k_eig_bt(Dev<float> df, Dev<double> dv) {
   const int b = blockIdx.y;
   const int n = dv.nold[b], k = dv.knew[b];
   if (n <= dv.eig_nsplit || k <= 0 || n > 512 || (int64_t)n * k > dv.vstride) return;
+  unsigned dyn = 0;
+  asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn));
+  if ((int64_t)bt_smem_bytes(n) > (int64_t)dyn) {  // launched for smaller bonds
+    if (threadIdx.x == 0 && blockIdx.x == 0) flag_err(dv, b, ERR_CAPACITY);
+    return;
+  }
   const int c0 = blockIdx.x * BT_COLS;
   if (c0 >= k) return;
   const int nc = min(BT_COLS, k - c0);
@@ -1993,7 +2047,6 @@ __global__ void __launch_bounds__(256) k_eig_bt(Dev<float> df, Dev<double> dv) {
   }
 }
 
-static constexpr int bt_smem_bytes() { return (512 * BT_COLS + 512 + 16 * BT_COLS) * (int)sizeof(cx<double>); }
 
 // MIXED runs: the FP64 eigensolver leaves V_k (n x k, row-major, complex128)
 // in its Gram buffer; the tensor-core contraction Y = M V_k takes it in
@@ -2518,7 +2571,9 @@ struct Engine {
   cx<double>* dG64 = nullptr;
   cx<double>* dV64 = nullptr;
   cx<double>* dTs64 = nullptr;
+  int* dCExpo = nullptr;           // row exponents of the exact contractions
   int64_t sstride = 0;             // bf16 digit tiles per trajectory (largest move)
+  int crows = 0;                   // row exponents per trajectory
   GramArgs gargs, gbase;
   Dev<R> base{};                   // the whole batch (dev = a group of it, see select_group)
   int64_t b0 = 0;                  // first trajectory of the selected group
@@ -2629,8 +2684,23 @@ struct Engine {
       for (int t = 0; t < 3; ++t)
         if (t != lv) mm *= c3[t];
       mm = std::min<int64_t>(mm, ncap[v]);
-      sstride = std::max<int64_t>(sstride, gram_slice_elems(mm, (int)(2 * bcap[bond])));
+      const int nb2 = (int)(2 * bcap[bond]);
+      sstride = std::max<int64_t>(sstride, gram_slice_elems(mm, nb2));
+      // the exact contractions Y = M V_k (m x n times n x k) and R T_w
+      // (k x n times n x J, J the product of w's other two legs)
+      const int kc = std::min<int>(nb2, st.c ? bcap[bond] : 2 * bcap[bond]);
+      const int lw = (v == 2 * w) ? 0 : ((v == 2 * w + 1) ? 1 : 2);
+      const int64_t w3[3] = {2 * (int64_t)bcap[2 * w], 2 * (int64_t)bcap[2 * w + 1],
+                             w == 1 ? 1 : 2 * (int64_t)bcap[w]};
+      int64_t J = 1;
+      for (int t = 0; t < 3; ++t)
+        if (t != lw) J *= w3[t];
+      J = std::min<int64_t>(J, ncap[w]);
+      sstride = std::max<int64_t>(sstride, contract_form_elems(mm, nb2, kc));
+      sstride = std::max<int64_t>(sstride, contract_absorb_elems(nb2, kc, J));
+      crows = (int)std::max<int64_t>(crows, std::max<int64_t>(mm, J) + 512);
     }
+    sstride = (sstride + 63) / 64 * 64;  // 128-byte aligned digit tiles
   }
 
   size_t bytes_per_traj() const {
@@ -2639,7 +2709,8 @@ struct Engine {
                c.n_events + 64;
     if (mixed)
       b += sizeof(uint16_t) * (size_t)sstride + sizeof(unsigned long long) * (size_t)(2 * nmax) * (2 * nmax) +
-           sizeof(cx<double>) * (size_t)(4 * vstride) + (sizeof(unsigned) + sizeof(int)) * 2 * nmax + 64;
+           sizeof(cx<double>) * (size_t)(4 * vstride) + (sizeof(unsigned) + sizeof(int)) * 2 * nmax +
+           sizeof(int) * (size_t)crows + 64;
     return b;
   }
 
@@ -2734,6 +2805,7 @@ struct Engine {
       CK(cudaMalloc(&dAmax, sizeof(unsigned) * cs * B));
       CK(cudaMalloc(&dExpo, sizeof(int) * cs * B));
       CK(cudaMalloc(&dSlices, sizeof(uint16_t) * (size_t)sstride * B));
+      CK(cudaMalloc(&dCExpo, sizeof(int) * (size_t)crows * B));
       CK(cudaMalloc(&dGfix, sizeof(unsigned long long) * cs * cs * B));
       CK(cudaMalloc(&dG64, sizeof(cx<double>) * (size_t)vstride * B));
       CK(cudaMalloc(&dV64, sizeof(cx<double>) * (size_t)vstride * B));
@@ -2810,7 +2882,7 @@ struct Engine {
   void release() {
     void* ptrs[] = {dT, dW, dV, dR, dG, dTs, dOff, dDims, dSv, dPerm, dK, dN, dLogp, dDisc, dTies, dRec,
                     dLast, dTheta, dGamma, dTraj, dErr, dErrStep, dFrob, dTrunc, dLeafdim, dOp1, dGroups,
-                    dLedger, dChoice, dShape, dAmax, dExpo, dSlices, dGfix, dG64, dV64, dTs64};
+                    dLedger, dChoice, dShape, dAmax, dExpo, dSlices, dGfix, dG64, dV64, dTs64, dCExpo};
     for (void* p : ptrs)
       if (p) cudaFree(p);
   }
@@ -2865,6 +2937,40 @@ struct Engine {
     }
   }
 
+  // Operands of the exact tensor-core contractions of the move v -> w for
+  // the selected group (MIXED runs).
+  ContractArgs contract_args(int v, int w) const {
+    ContractArgs a{};
+    a.dims = dev.dims;
+    a.ds = dev.ds;
+    a.v = v;
+    a.w = w;
+    a.leg_v = (w == 2 * v) ? 0 : ((w == 2 * v + 1) ? 1 : 2);
+    a.leg_w = (v == 2 * w) ? 0 : ((v == 2 * w + 1) ? 1 : 2);
+    a.nold = dev.nold;
+    a.knew = dev.knew;
+    a.M = reinterpret_cast<const float2*>(dev.W);
+    a.mstride = dev.wstride;
+    a.V = reinterpret_cast<const float2*>(dev.G);
+    a.Rm = reinterpret_cast<const float2*>(dev.Rm);
+    a.vstride = dev.vstride;
+    a.T = reinterpret_cast<float2*>(dev.T);
+    a.tstride = dev.tstride;
+    a.off_v = off[v];
+    a.off_w = off[w];
+    a.W = reinterpret_cast<float2*>(dev.W);
+    a.wstride = dev.wstride;
+    a.slices = dSlices + b0 * sstride;
+    a.sstride = sstride;
+    a.expo = dCExpo + b0 * crows;
+    a.rows_cap = crows;
+    a.err = dev.err;
+    a.ledger = dev.ledger;
+    a.ledger_form = KC_FORMU;
+    a.ledger_absorb = KC_ABSORB;
+    return a;
+  }
+
   // Steps [s0, s1) of the program for the selected group's first nb
   // trajectories; s0 == 0 starts them from |0...0>.
   ttn_status launch_range(int nb, int s0, int s1) {
@@ -2904,10 +3010,12 @@ struct Engine {
             if (t != lv0) mcap *= cc3[t];
           const bool big = c.N > BIG_CIRCUIT_QUBITS || mcap * nmv >= BIG_MOVE;
           const bool gram = mixed || dev.svd_mode >= 2 || (dev.svd_mode == 0 && sizeof(R) == 4 && (nmv > 64 || big));
-          // contractions of this move on the tensor cores (FP32 only)
-          // MIXED: the FMA units unless tensor cores are asked for (the
-          // mma.sync 3xTF32 tile's truncating FP32 accumulation costs ~1e-5
-          // of amplitude accuracy over a syndrome round)
+          // contractions of this move on the tensor cores (FP32 only).
+          // MIXED: by default the exact digit products on tcgen05
+          // (contract.cu); gemm_mode 1 the FMA units, 2 the mma.sync 3xTF32
+          // tile (whose truncating FP32 accumulation costs ~1e-5 of
+          // amplitude accuracy over a syndrome round)
+          const bool exact_c = mixed && gemm_mode == 0;
           const bool tc = sizeof(R) == 4 && (gemm_mode == 2 || (gemm_mode == 0 && gram && !mixed));
           if (gram) {
             const int lv = (w == 2 * v) ? 0 : ((w == 2 * v + 1) ? 1 : 2);
@@ -2925,24 +3033,29 @@ struct Engine {
               // dimension: cyclic Jacobi in shared memory up to EIG_JACOBI_N,
               // the tridiagonal solver above (each kernel skips the others)
               const bool both = nmv > EIG_JACOBI_N;
-              timed(KC_EIG, (sizeof(R) == 4 ? 2 : 1) + (both ? 2 : 0), [&] {
+              timed(KC_EIG, (sizeof(R) == 4 ? 1 : 0) + (both ? 2 : 1), [&] {
                 Dev<double> dv = view64();
                 dv.eig_nsplit = EIG_JACOBI_N;
                 dv.eig_smem_bytes = EIG_JACOBI_N * EIG_JACOBI_N * (int)sizeof(cx<double>);
                 dv.defer_bt = sizeof(R) == 4 ? 1 : 0;
-                k_eig<double><<<nb, 512, dv.eig_smem_bytes, st>>>(dv, v, w, kcap);
-                // a bond up to 256 fits 256 threads (one per eigenvalue); half
-                // the SM's registers and a quarter of its shared memory then
-                // leave room for other streams' kernels beside it
-                if (both)
-                  k_eig_tri<double><<<nb, nmv <= 256 ? 256 : 512,
-                                      dv.defer_bt ? tri_smem_bytes_nobt<double>() : tri_smem_bytes<double>(), st>>>(
-                      dv, v, w, kcap);
+                if (!both) {
+                  k_eig<double><<<nb, 512, dv.eig_smem_bytes, st>>>(dv, v, w, kcap);
+                } else {
+                  // one launch per move: the tridiagonal kernel runs the
+                  // Jacobi body itself for the trajectories whose bond is at
+                  // most EIG_JACOBI_N (an idle second launch would still wait
+                  // for a slot on a busy SM).  A bond up to 256 fits 256
+                  // threads (one per eigenvalue), leaving room for a second
+                  // CTA on the SM.
+                  const int smem = std::max(dv.eig_smem_bytes, dv.defer_bt ? tri_smem_bytes_nobt<double>()
+                                                                             : tri_smem_bytes<double>());
+                  k_eig_tri<double><<<nb, nmv <= 256 ? 256 : 512, smem, st>>>(dv, v, w, kcap);
+                }
                 if constexpr (sizeof(R) == 4) {
                   k_vk_to_float<<<nb, 256, 0, st>>>(dev, dG64 + b0 * vstride, EIG_JACOBI_N);
                   if (both)
                     k_eig_bt<<<dim3((unsigned)ceil_div(std::min<int64_t>(kcap, nmv), BT_COLS), nb), 256,
-                               bt_smem_bytes(), st>>>(dev, dv);
+                               bt_smem_bytes((int)std::min<int64_t>(nmv, 512)), st>>>(dev, dv);
                 }
               });
             } else {
@@ -2960,11 +3073,18 @@ struct Engine {
             } else {
               timed(KC_EIG, [&] { k_eig_tri<R><<<nb, 512, tri_smem_bytes<R>(), st>>>(dev, v, w, kcap); });
             }
+            if (exact_c) {
+              timed(KC_FORMU, 3, [&] {
+                (void)contract_form_launch(contract_args(v, w), nb, mmax, (int)nmv,
+                                           (int)std::min<int64_t>(kcap, nmv), st);
+              });
+            } else {
             timed(KC_FORMU, [&] {
               const dim3 gf(std::max(1, ceil_div(mmax, 64)), tn, nb);
               if (tc) k_form_u<R, true><<<gf, 256, 0, st>>>(dev, v, w);
               else k_form_u<R, false><<<gf, 256, 0, st>>>(dev, v, w);
             });
+            }
             timed(KC_OTHER, 4, [&] {
               const int gx = (int)std::min<int64_t>(std::max<int64_t>(1, mmax * nmv / 4096), 512);
               k_unorm_zero<R><<<nb, 256, 0, st>>>(dev, nb);
@@ -2983,10 +3103,17 @@ struct Engine {
           int64_t Jmax = ncap[w] * 2 / std::max<int64_t>(1, kmax);
           Jmax = std::min<int64_t>(Jmax, (lw == 0 ? cr * cu : (lw == 1 ? cl * cu : cl * cr)));
           dim3 ga(std::max(1, ceil_div(Jmax, 64)), std::max(1, ceil_div(kmax, 64)), nb);
+          if (exact_c && gram) {
+            timed(KC_ABSORB, 3, [&] {
+              (void)contract_absorb_launch(contract_args(v, w), nb, (int)nmv, (int)std::min<int64_t>(kcap, nmv),
+                                           Jmax, st);
+            });
+          } else {
           timed(KC_ABSORB, [&] {
             if (tc) k_absorb<R, true><<<ga, 256, 0, st>>>(dev, w, v);
             else k_absorb<R, false><<<ga, 256, 0, st>>>(dev, w, v);
           });
+          }
           timed(KC_COPY, [&] { k_copy_back<R><<<dim3(std::max(1, ceil_div(ncap[w], 256 * 4)), nb), 256, 0, st>>>(dev, w); });
           break;
         }
@@ -3347,6 +3474,9 @@ struct PipelineT : PipelineImpl {
   RunRequest rq;
   Engine<R> eng;
   int B = 0, S = 0, G = 0;
+  // program steps each group gets per turn of the interleaved launches
+  // (TTN_PIPELINE_CHUNK, default 16)
+  int chunk = 16;
   std::vector<int> seg;             // S + 1 step boundaries
   std::vector<int> phase;           // next segment of each group
   std::vector<uint64_t> first;      // first trajectory index of each group's trajectories
@@ -3362,7 +3492,9 @@ struct PipelineT : PipelineImpl {
   uint64_t* h_traj = nullptr;
 
   PipelineT(const ttn_circuit& cc, const RunRequest& r)
-      : c(cc), prog(compile_program(cc, r.noise, -1)), rq(r), eng(cc, prog, r.chi, r.noise, nullptr) {}
+      : c(cc), prog(compile_program(cc, r.noise, -1)), rq(r), eng(cc, prog, r.chi, r.noise, nullptr) {
+    if (const char* e = std::getenv("TTN_PIPELINE_CHUNK")) chunk = std::max(1, std::min(1 << 20, std::atoi(e)));
+  }
 
   ~PipelineT() override {
     for (cudaStream_t x : streams) cudaStreamDestroy(x);
@@ -3496,7 +3628,7 @@ struct PipelineT : PipelineImpl {
       timed_seg[g] = phase[g];
       CK(cudaEventRecord(ev_a[g], streams[g]));
     }
-    static constexpr int CHUNK = 16;  // program steps per group per turn
+    const int CHUNK = chunk;  // program steps per group per turn
     for (bool more = true; more;) {
       more = false;
       for (size_t i = 0; i < gs.size(); ++i) {
@@ -3649,9 +3781,9 @@ extern "C" ttn_status ttn_eig_gram(const void* G, int32_t batch, int32_t n, int3
   using namespace ttn;
   const int64_t jac_max = (int64_t)EIG_SMEM_MAX / (int64_t)sizeof(cx<double>);
   if (!G || !V || !s || !k || batch < 1 || n < 1 || n > 512 || kcap < 1 || kcap > n || route < 0 ||
-      route > 2 || !(eps_keep >= 0.0 && eps_keep < 1.0) || (route == 0 && (int64_t)n * n > jac_max)) {
+      route > 3 || !(eps_keep >= 0.0 && eps_keep < 1.0) || (route == 0 && (int64_t)n * n > jac_max)) {
     set_error("ttn_eig_gram: need device G [batch][n][n], V [batch][n][kcap], s [batch][n], k [batch]; "
-              "1 <= kcap <= n <= 512 (n^2 <= 8192 for route 0), route 0..2, 0 <= eps_keep < 1");
+              "1 <= kcap <= n <= 512 (n^2 <= 8192 for route 0), route 0..3, 0 <= eps_keep < 1");
     return TTN_EINVAL;
   }
   if ((reinterpret_cast<uintptr_t>(G) & 15) || (reinterpret_cast<uintptr_t>(V) & 15)) {
@@ -3670,8 +3802,12 @@ extern "C" ttn_status ttn_eig_gram(const void* G, int32_t batch, int32_t n, int3
   d.tol_gram = 1e-13;
   d.tol_abs_gram = 1e-15;
   d.max_sweeps = 40;
-  d.defer_bt = route == 2 ? 1 : 0;
-  d.eig_smem_bytes = route == 0 ? (int)(vs * (int64_t)sizeof(cx<double>)) : 0;
+  d.defer_bt = route >= 2 ? 1 : 0;
+  // route 3: bonds up to EIG_JACOBI_N by the Jacobi body inside the tridiagonal kernel
+  d.eig_nsplit = route == 3 ? EIG_JACOBI_N : 0;
+  d.eig_smem_bytes = route == 0   ? (int)(vs * (int64_t)sizeof(cx<double>))
+                     : route == 3 ? EIG_JACOBI_N * EIG_JACOBI_N * (int)sizeof(cx<double>)
+                                  : 0;
   df.vstride = vs;
   void* pool = nullptr;
   const size_t b_cx = sizeof(cx<double>) * (size_t)(vs * B);
@@ -3714,18 +3850,25 @@ extern "C" ttn_status ttn_eig_gram(const void* G, int32_t batch, int32_t n, int3
     if (e == cudaSuccess && route > 0)
       e = cudaFuncSetAttribute(k_eig_tri<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                tri_smem_bytes<double>());
-    if (e == cudaSuccess && route == 2)
+    if (e == cudaSuccess && route >= 2)
       e = cudaFuncSetAttribute(k_eig_bt, cudaFuncAttributeMaxDynamicSharedMemorySize, bt_smem_bytes());
     if (e == cudaSuccess) {
       if (route == 0) {
         k_eig<double><<<batch, 512, d.eig_smem_bytes, st>>>(d, 1, 2, kcap);
       } else {
-        k_eig_tri<double><<<batch, 512, route == 2 ? tri_smem_bytes_nobt<double>() : tri_smem_bytes<double>(), st>>>(
-            d, 1, 2, kcap);
-        if (route == 2)
-          k_eig_bt<<<dim3((unsigned)ceil_div(kcap, BT_COLS), batch), 256, bt_smem_bytes(), st>>>(df, d);
+        const int smem = std::max(d.eig_smem_bytes, route >= 2 ? tri_smem_bytes_nobt<double>() : tri_smem_bytes<double>());
+        // the MIXED runs' launch shape: 256 threads up to n = 256
+        k_eig_tri<double><<<batch, route == 3 && n <= 256 ? 256 : 512, smem, st>>>(d, 1, 2, kcap);
+        if (route >= 2)
+          k_eig_bt<<<dim3((unsigned)ceil_div(kcap, BT_COLS), batch), 256, bt_smem_bytes(n), st>>>(df, d);
       }
-      k_eig_collect<<<batch, 256, 0, st>>>(d, route == 2 ? df.G : nullptr, static_cast<cx<double>*>(V), s, k, n,
+      if (route == 3) {  // the Jacobi share's V_k in complex64, as k_vk_to_float leaves it
+        Dev<float> dfv = df;
+        dfv.nold = d.nold;
+        dfv.knew = d.knew;
+        k_vk_to_float<<<batch, 256, 0, st>>>(dfv, d.G, EIG_JACOBI_N);
+      }
+      k_eig_collect<<<batch, 256, 0, st>>>(d, route >= 2 ? df.G : nullptr, static_cast<cx<double>*>(V), s, k, n,
                                            kcap);
       e = cudaGetLastError();
     }

@@ -18,7 +18,7 @@ P = pytest.importorskip("paper_2511_05719_gb300")
 
 pytestmark = pytest.mark.gpu
 
-ROUTES = ["jacobi", "tridiagonal", "tridiagonal_split"]
+ROUTES = ["jacobi", "tridiagonal", "tridiagonal_split", "mixed"]
 
 
 def _unitary(rng, n):
@@ -80,8 +80,8 @@ def _run(Gs, route, kcap=None, eps_keep=1e-7):
 
 
 def _tol(route, fp64=1e-10):
-    """The split route rounds V_k to complex64 (2^-24 per entry)."""
-    return 1e-6 if route == "tridiagonal_split" else fp64
+    """The split and MIXED routes round V_k to complex64 (2^-24 per entry)."""
+    return 1e-6 if route in ("tridiagonal_split", "mixed") else fp64
 
 
 def _routes_for(n):
@@ -164,7 +164,8 @@ def test_kcap_and_threshold():
 
 def test_trajectory_gram_matrices():
     """Every bond Gram matrix of a d = 3 SRX trajectory of the CPU tree
-    tensor network, through both tridiagonal routes."""
+    tensor network, through the tridiagonal routes and the MIXED runs'
+    combination."""
     from oracle import ttn as OT
     from oracle.layout import optimized_layout
     from oracle.channels import SRX
@@ -193,7 +194,7 @@ def test_trajectory_gram_matrices():
     for G in mats:
         by_n.setdefault(G.shape[0], []).append(G)
     for n, Gs in sorted(by_n.items()):
-        for route in ("tridiagonal", "tridiagonal_split"):
+        for route in ("tridiagonal", "tridiagonal_split", "mixed"):
             V, s, k = _run(Gs, route)
             for b, G in enumerate(Gs):
                 _check(G, V[b], s[b], k[b], 1e-7, _tol(route), route=route)

@@ -1,6 +1,7 @@
-"""The MIXED precision route -- complex64 tensors, 3xTF32 tensor-core
-contractions, every isometry-centre factorisation in FP64 (exact Gram matrix
-on the tensor cores + FP64 Hermitian eigensolver) -- against the CPU oracle.
+"""The MIXED precision route -- complex64 tensors, exact digit-product
+contractions on the tcgen05 tensor cores, every isometry-centre factorisation
+in FP64 (exact Gram matrix on the tensor cores + FP64 Hermitian eigensolver)
+-- against the CPU oracle.
 
 This is the route of the d = 7, chi = 128 benchmark workload, and it is the
 same at every circuit size (no size-dependent switch), so the d = 3 circuits
@@ -94,3 +95,26 @@ def test_mixed_large_circuits_complete(d, C, chi, noise, th, ga):
     assert np.all(out["fail"] <= 1)
     assert np.all(np.isfinite(out["log_prob"])) and np.all(out["log_prob"] <= 1e-9)
     assert np.all(out["discarded"] >= 0) and np.all(np.isfinite(out["discarded"]))
+
+
+@pytest.mark.parametrize("noise", ["srx", "srx_ad"])
+def test_mixed_contraction_routes(noise):
+    """The tcgen05 digit-product contractions (default) and the FMA
+    contractions (gemm_mode "fma") both hold the amplitude bars.  (The digit
+    route sums exactly but rounds its inputs to 23 bits below each row's
+    largest entry, so it is not more accurate than FMA sums in general.)"""
+    circ = build_circuit(3, 2)
+    th, ga = STRENGTH[noise]
+    c = P.Circuit(3, 2, layout="optimized")
+    layers = [13, circ.n_layers - 1]
+    for traj in (1, 2):
+        ref = SV.run_trajectory(circ, MODELS[noise], th, ga, W.BASE_SEED, traj, snapshot_layers=layers)
+        errs = {}
+        for mode in ("auto", "fma"):
+            for L in layers:
+                amp = P.debug_state(c, traj, L, noise=noise, theta=th, gamma=ga, chi=64,
+                                    precision="mixed", seed=W.BASE_SEED, gemm_mode=mode)
+                want = ref["states"][L]
+                err = np.linalg.norm(amp - want) / np.linalg.norm(want)
+                assert err < (TOL_ROUND1 if L <= 13 else TOL_ROUND2), (noise, mode, traj, L, err)
+                errs[mode, L] = err
