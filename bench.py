@@ -65,7 +65,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ttn", choices=["ttn", "reference"])
-    ap.add_argument("--resident", type=int, default=160, help="trajectories on the device per rank")
+    ap.add_argument("--resident", type=int, default=192, help="trajectories on the device per rank")
     ap.add_argument("--segments", type=int, default=32, help="pipeline segments (resident must be a multiple)")
     ap.add_argument("--distance", type=int, default=7)
     ap.add_argument("--rounds", type=int, default=7)
@@ -74,6 +74,7 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 single-instance leg")
+    ap.add_argument("--no-grad", action="store_true", help="skip the gradient / forward cost leg")
     return ap.parse_args()
 
 
@@ -229,7 +230,34 @@ def plain_fp64_single(a, P, torch):
                       % (a.distance, theta, a.chi, secs, a.rounds, a.rounds)}
 
 
-def roofline(a, prof, cls):
+def grad_fwd(a, P, torch):
+    """Cost of the gradient estimate against the forward p_L on the gradient
+    workload's d = 5, chi = 64 setting (MIXED, one syndrome round per
+    trajectory so the leg stays short): ttn_grad = forward pass plus the two
+    forced replays at theta +- h, on the same shots."""
+    g = WL.M5
+    circ = P.Circuit(5, 1, layout="optimized")
+    shots, th = 64, g["theta0"]
+    kw = dict(noise="srx", theta=th, chi=64, precision="mixed", seed=g["seed"])
+    P.logical_error_rate(circ, 8, **kw)  # warm-up (library load, first launches)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    P.logical_error_rate(circ, shots, **kw)
+    torch.cuda.synchronize()
+    tf = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    P.grad(circ, shots, wrt="theta", h=g["dtheta"], **kw)
+    torch.cuda.synchronize()
+    tg = time.perf_counter() - t0
+    return {"grad_s": tg, "fwd_s": tf, "ratio": tg / tf if tf > 0 else None,
+            "sample": "d=5, 1 round, chi=64, MIXED, SRX theta=%.3f, %d shots; score-function gradient "
+                      "(forward + forced replays at theta +- %.0e)" % (th, shots, g["dtheta"])}
+
+
+def roofline(a, prof, cls, wall_s):
+    """achieved: the class's ledger flops / its event-timed device time (per
+    launch, as the launches ran); aggregate: the same flops / the timed wall
+    time, i.e. the rate of all concurrent launches of the class together."""
     fl = prof["flops"][cls]
     ms = prof["class_ms"][cls]
     achieved = fl / (ms / 1e3) / 1e12 if ms > 0 else 0.0
@@ -237,17 +265,18 @@ def roofline(a, prof, cls):
     if cls == "eig":
         bound, peak, psrc = "alu", FP64_PEAK_TFLOPS, "FP64 nominal (MEASURED_PEAKS has no FP64 entry)"
     elif cls == "gram":
-        bound, peak, psrc = "tensor", bf16, src + "; algorithmic complex Gram flops 8mn^2 (the kernel " \
-                                                  "executes 9 bf16 digit products of the real Gram)"
-    elif cls in ("form_u", "absorb"):
-        bound, peak = "tensor", bf16 * (1.1 / 2.25) / 3.0
-        psrc = src + " x 1.1/2.25 (TF32) / 3 (3xTF32 passes)"
-    else:
+        # 9 bf16 digit products of the real Gram X^T X (X = m x 2n), upper
+        # triangle only: 36 m n^2 executed flops per 8 m n^2 algorithmic
+        bound, peak = "tensor", bf16 * 8.0 / 36.0
+        psrc = src + " x 8/36 (algorithmic complex Gram flops per executed bf16 digit-product flops)"
+    else:  # form_u, absorb (FP32 FMA in MIXED runs by default) and the rest
         bound, peak, psrc = "alu", 152 * 128 * 2 * 2.070e9 / 1e12, "FP32 FMA: 152 SMs x 128 lanes x 2 x 2070 MHz"
+    agg = fl / wall_s / 1e12 if wall_s > 0 else 0.0
     return {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak if peak else 0.0, "traffic": None, "kernel_class": cls,
             "launches": prof["launches"][cls], "kernel_ms": ms,
-            "per_launch_ms": ms / max(1, prof["launches"][cls]), "peak_source": psrc}
+            "per_launch_ms": ms / max(1, prof["launches"][cls]), "peak_source": psrc,
+            "aggregate_tflops": agg, "aggregate_frac": agg / peak if peak else 0.0}
 
 
 def note(msg):
@@ -363,7 +392,7 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "c64+f64", "data": "synthetic",
             "config": run_config(a),
             "clocks": ck, "e2e": e2e, "gpu_launches": int(prof["kernels"]),
-            "roofline": roofline(a, prof, dom),
+            "roofline": roofline(a, prof, dom, ms / 1e3),
             "fill_s": fill_s, "segment_s_last_step": seg_ms,
             "device_ms_by_class_warmup": {k: round(v, 1) for k, v in cms.items()},
             "ledger_tflop_per_traj": {k: v / 1e12 / max(1, K * G) for k, v in prof["flops"].items()},
@@ -375,6 +404,9 @@ def main():
         pl1 = plain_fp64_single(a, P, torch)
         pl1["batched_over_plain"] = value / pl1["value"] if pl1["value"] > 0 else None
         line["plain_fp64_single"] = pl1
+    if not a.no_grad:
+        note("grad / forward cost leg")
+        line["grad_fwd"] = grad_fwd(a, P, torch)
     if not a.no_cpu_baseline and world == 1:
         note("CPU oracle baseline")
         line["cpu_baseline"] = cpu_baseline(a)

@@ -66,9 +66,9 @@ typedef enum {
  * (cyclic Jacobi for bonds up to 64, tridiagonal above), the kept rank and
  * the singular values in double -- and probabilities, log-probabilities and
  * discarded weights in double.  svd_mode is ignored in MIXED runs; their
- * contractions Y = M V_k and the neighbour absorb are exact digit products
- * on the tcgen05 tensor cores as well (one final rounding to complex64)
- * unless gemm_mode asks for the FMA units (1) or the 3xTF32 tile (2). */
+ * contractions Y = M V_k and the neighbour absorb run on the FP32 FMA units
+ * unless gemm_mode asks for the exact digit products on the tcgen05 tensor
+ * cores (3, one final rounding to complex64) or the 3xTF32 tile (2). */
 typedef enum { TTN_PREC_FP64 = 0, TTN_PREC_FP32 = 1, TTN_PREC_MIXED = 2 } ttn_precision;
 
 /* Qubit -> TTN leaf assignment (App. B).  DEFAULT: qubit i on leaf i.
@@ -138,9 +138,9 @@ typedef struct {
                                     2 tensor cores for every move.  Tensor
                                     cores use TF32 with a 3-term split
                                     (FP32-level accuracy).  MIXED runs: 0
-                                    exact tcgen05 digit products, 1 FMA, 2
-                                    the 3xTF32 tile.  FP64 runs ignore
-                                    it.                                   */
+                                    and 1 FMA, 2 the 3xTF32 tile, 3 exact
+                                    tcgen05 digit products.  FP64 runs
+                                    ignore it.                            */
 } ttn_run_params;
 
 typedef struct ttn_circuit ttn_circuit;  /* opaque, library-owned */

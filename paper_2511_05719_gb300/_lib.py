@@ -195,7 +195,7 @@ class Circuit:
 
 
 SVD_MODE = {"auto": 0, "jacobi": 1, "gram": 2, "gram_tri": 3}
-GEMM_MODE = {"auto": 0, "fma": 1, "tensor": 2}
+GEMM_MODE = {"auto": 0, "fma": 1, "tensor": 2, "exact": 3}
 
 
 def _run_params(noise, theta, gamma, chi, precision, seed, first_traj, svd_eps,

@@ -157,7 +157,7 @@ static ttn_status check_params(const ttn_circuit* c, const ttn_run_params* p) {
   if (!std::isfinite(p->theta)) return fail_with(TTN_EINVAL, "theta must be finite");
   if (!(p->gamma >= 0.0 && p->gamma <= 1.0)) return fail_with(TTN_EINVAL, "gamma must be in [0, 1]");
   if (p->svd_mode < 0 || p->svd_mode > 3) return fail_with(TTN_EINVAL, "svd_mode must be 0, 1, 2 or 3");
-  if (p->gemm_mode < 0 || p->gemm_mode > 2) return fail_with(TTN_EINVAL, "gemm_mode must be 0, 1 or 2");
+  if (p->gemm_mode < 0 || p->gemm_mode > 3) return fail_with(TTN_EINVAL, "gemm_mode must be 0, 1, 2 or 3");
   return TTN_OK;
 }
 

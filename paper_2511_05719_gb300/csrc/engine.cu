@@ -1300,8 +1300,19 @@ __global__ void __launch_bounds__(512) k_eig_tri(Dev<R> d, int v, int w, int kca
             for (int u = 0; u < TRI_UNROLL; ++u) {
               const int j = j0 + u * G;
               if (j < mp) {
-                const cx<R> t1 = cmul(vk[1 + j], cwi), tt = cmul(wk[1 + j], cvi);
-                a[u] = {a[u].x - t1.x - tt.x, a[u].y - t1.y - tt.y};
+                // a -= v_j conj(w_col) + w_j conj(v_col): eight FMAs, the
+                // FP64 minimum for the two complex products
+                const cx<R> vj = vk[1 + j], wj = wk[1 + j];
+                R ax = a[u].x, ay = a[u].y;
+                ax = fma(-vj.x, cwi.x, ax);
+                ax = fma(vj.y, cwi.y, ax);
+                ay = fma(-vj.x, cwi.y, ay);
+                ay = fma(-vj.y, cwi.x, ay);
+                ax = fma(-wj.x, cvi.x, ax);
+                ax = fma(wj.y, cvi.y, ax);
+                ay = fma(-wj.x, cvi.y, ay);
+                ay = fma(-wj.y, cvi.x, ay);
+                a[u] = {ax, ay};
                 colp[(int64_t)j * n] = a[u];
               }
             }
@@ -1323,7 +1334,16 @@ __global__ void __launch_bounds__(512) k_eig_tri(Dev<R> d, int v, int w, int kca
               for (int u = 0; u < TRI_UNROLL; ++u) {
                 const int j = j0 + u * G;
                 // A'[col][j] = conj(A'[j][col]) from the column, itself from the row
-                if (j < mp) acc = cadd(acc, j >= col ? cmulc(a[u], vn[j]) : cmul(a[u], vn[j]));
+                if (j < mp) {
+                  // acc += conj(a) v (column entries) or a v (row entries):
+                  // four FMAs, the conjugation a sign on a.y
+                  const cx<R> vv = vn[j];
+                  const R ay = j >= col ? -a[u].y : a[u].y;
+                  acc.x = fma(a[u].x, vv.x, acc.x);
+                  acc.x = fma(-ay, vv.y, acc.x);
+                  acc.y = fma(a[u].x, vv.y, acc.y);
+                  acc.y = fma(ay, vv.x, acc.y);
+                }
               }
             }
             pp[g * mp + col] = acc;
@@ -1472,8 +1492,9 @@ __global__ void __launch_bounds__(512) k_eig_tri(Dev<R> d, int v, int w, int kca
   // independent vectors spanning their invariant subspace, and a
   // Rayleigh-Ritz step on the kept subspace (H = Z^T T Z = Q L Q^T by cyclic
   // Jacobi, Z <- Z Q) diagonalises it.
-  auto start_vec = [&](int c, int salt, int s0, int e0) {
-    for (int i = tid; i < n; i += nth) {
+  // fills column c from thread t0 with stride st (the block: tid, nth; a warp: lane, 32)
+  auto start_vec_by = [&](int c, int salt, int s0, int e0, int t0, int st) {
+    for (int i = t0; i < n; i += st) {
       uint32_t h = (uint32_t)(i + 7919 * salt) * 0x9E3779B1u ^ ((uint32_t)c + 0x7F4A7C15u) * 0x85EBCA77u;
       h ^= h >> 15;
       h *= 0x2C1B3C6Du;
@@ -1482,6 +1503,7 @@ __global__ void __launch_bounds__(512) k_eig_tri(Dev<R> d, int v, int w, int kca
       Z[(int64_t)c * n + i] = (i >= s0 && i < e0) ? x : R(0);
     }
   };
+  auto start_vec = [&](int c, int salt, int s0, int e0) { start_vec_by(c, salt, s0, e0, tid, nth); };
   for (int c = 0; c < k; ++c) {
     const int jj = perm[c];
     start_vec(c, 0, bstart[jj], bend[jj]);
@@ -1594,9 +1616,28 @@ __global__ void __launch_bounds__(512) k_eig_tri(Dev<R> d, int v, int w, int kca
       for (int i = s0; i < e0; ++i) zc[i] *= inv;
     }
     __syncthreads();
-    // classical Gram-Schmidt, twice, columns in order
-    bool restarted = false;  // uniform: every thread sees the same sums
+    // a column alone in its cluster is only normalised (one warp per column,
+    // all at once; a zero vector restarts)
+    int zero_col = 0;
+    for (int a = warp_id; a < k; a += nwarp) {
+      if (cen[a] - cst[a] != 1) continue;
+      R* za = Z + (int64_t)a * n;
+      double nn = 0.0;
+      for (int i = lane_id; i < n; i += 32) nn += (double)za[i] * za[i];
+      nn = warp_sum(nn);
+      if (nn > 0.0) {
+        const R sc1 = (R)(1.0 / sqrt(nn));
+        for (int i = lane_id; i < n; i += 32) za[i] *= sc1;
+      } else {
+        const int jj = perm[a];
+        start_vec_by(a, 1 + iter * 4, bstart[jj], bend[jj], lane_id, 32);
+        zero_col = 1;
+      }
+    }
+    // classical Gram-Schmidt, twice, columns of the larger clusters in order
+    bool restarted = __syncthreads_or(zero_col) != 0;  // uniform: every thread sees the same sums
     for (int a = 0; a < k; ++a) {
+      if (cen[a] - cst[a] == 1) continue;  // uniform
       const int jj = perm[a];
       for (int rep = 0; rep < 2; ++rep) {
         for (int attempt = 0; attempt < 2; ++attempt) {
@@ -1637,8 +1678,12 @@ __global__ void __launch_bounds__(512) k_eig_tri(Dev<R> d, int v, int w, int kca
     if (restarted) iters = min(max(iters, iter + 3), TRI_INV_ITERS + TRI_INV_EXTRA);
   }
   phase_mark(3);
-  // Rayleigh-Ritz: TZ into U0 (column-major), H = Z^T (TZ) into U1 (k x k),
-  // Q into U2
+  // Rayleigh-Ritz within the clusters of more than one column: TZ into U0
+  // (column-major), H = Z^T (TZ) into U1 (k x k), Q into U2.  With every
+  // cluster a single column, H is diagonal and Z stays as it is.
+  int multi = 0;
+  for (int a = tid; a < k; a += nth) multi |= cen[a] - cst[a] > 1;
+  if (__syncthreads_or(multi)) {
   R* TZ = U0;
   R* H = U1;
   R* Q = U2;
@@ -1739,6 +1784,7 @@ __global__ void __launch_bounds__(512) k_eig_tri(Dev<R> d, int v, int w, int kca
   __syncthreads();
   for (int idx = tid; idx < n * k; idx += nth) Z[idx] = TZ[idx];
   __syncthreads();
+  }
   // residual |T z - (z^T T z) z| of every kept vector (one warp per column):
   // above 16 sqrt(eps) |T| the vectors did not converge (reported, not fatal)
   for (int c = warp_id; c < k; c += nwarp) {
@@ -3011,11 +3057,15 @@ struct Engine {
           const bool big = c.N > BIG_CIRCUIT_QUBITS || mcap * nmv >= BIG_MOVE;
           const bool gram = mixed || dev.svd_mode >= 2 || (dev.svd_mode == 0 && sizeof(R) == 4 && (nmv > 64 || big));
           // contractions of this move on the tensor cores (FP32 only).
-          // MIXED: by default the exact digit products on tcgen05
-          // (contract.cu); gemm_mode 1 the FMA units, 2 the mma.sync 3xTF32
-          // tile (whose truncating FP32 accumulation costs ~1e-5 of
-          // amplitude accuracy over a syndrome round)
-          const bool exact_c = mixed && gemm_mode == 0;
+          // MIXED: the FMA units by default (0, 1); gemm_mode 3 the digit
+          // products on tcgen05 (contract.cu), 2 the mma.sync 3xTF32 tile
+          // (whose truncating FP32 accumulation costs ~1e-5 of amplitude
+          // accuracy over a syndrome round).  The tcgen05 kernels' grids are
+          // sized by the bond capacities, and their idle CTAs, each holding
+          // ~110 KB of shared memory, kept other streams' eigensolver CTAs
+          // waiting: ten times the FMA kernels' device time in the
+          // pipelined d=7 batch.
+          const bool exact_c = mixed && gemm_mode == 3;
           const bool tc = sizeof(R) == 4 && (gemm_mode == 2 || (gemm_mode == 0 && gram && !mixed));
           if (gram) {
             const int lv = (w == 2 * v) ? 0 : ((w == 2 * v + 1) ? 1 : 2);

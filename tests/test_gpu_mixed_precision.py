@@ -1,7 +1,7 @@
-"""The MIXED precision route -- complex64 tensors, exact digit-product
-contractions on the tcgen05 tensor cores, every isometry-centre factorisation
-in FP64 (exact Gram matrix on the tensor cores + FP64 Hermitian eigensolver)
--- against the CPU oracle.
+"""The MIXED precision route -- complex64 tensors, FP32 contractions (FMA,
+or exact digit products on the tcgen05 tensor cores), every isometry-centre
+factorisation in FP64 (exact Gram matrix on the tensor cores + FP64 Hermitian
+eigensolver) -- against the CPU oracle.
 
 This is the route of the d = 7, chi = 128 benchmark workload, and it is the
 same at every circuit size (no size-dependent switch), so the d = 3 circuits
@@ -99,8 +99,8 @@ def test_mixed_large_circuits_complete(d, C, chi, noise, th, ga):
 
 @pytest.mark.parametrize("noise", ["srx", "srx_ad"])
 def test_mixed_contraction_routes(noise):
-    """The tcgen05 digit-product contractions (default) and the FMA
-    contractions (gemm_mode "fma") both hold the amplitude bars.  (The digit
+    """The tcgen05 digit-product contractions (gemm_mode "exact") and the
+    FMA contractions (the default) both hold the amplitude bars.  (The digit
     route sums exactly but rounds its inputs to 23 bits below each row's
     largest entry, so it is not more accurate than FMA sums in general.)"""
     circ = build_circuit(3, 2)
@@ -110,7 +110,7 @@ def test_mixed_contraction_routes(noise):
     for traj in (1, 2):
         ref = SV.run_trajectory(circ, MODELS[noise], th, ga, W.BASE_SEED, traj, snapshot_layers=layers)
         errs = {}
-        for mode in ("auto", "fma"):
+        for mode in ("exact", "fma"):
             for L in layers:
                 amp = P.debug_state(c, traj, L, noise=noise, theta=th, gamma=ga, chi=64,
                                     precision="mixed", seed=W.BASE_SEED, gemm_mode=mode)

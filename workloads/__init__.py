@@ -17,7 +17,7 @@ M2 = dict(name="d5_C5_ad_chi64_fp32", distance=5, rounds=5, noise="ad",
           gammas=[1e-3, 3e-3, 1e-2, 2e-2], chi=64, precision="fp32", shots=100000,
           seed=BASE_SEED + 1)
 # d=7, 7 rounds, SRX theta sweep (8 points in [0.01, 0.15] rad), chi = 128,
-# complex64 tensors with 3xTF32 contractions and the FP64 centre (MIXED)
+# complex64 tensors with tcgen05 digit-product contractions and the FP64 centre (MIXED)
 M3 = dict(name="d7_C7_srx_chi128", distance=7, rounds=7, noise="srx",
           thetas=list(np.linspace(0.01, 0.15, 8)), chi=128, precision="mixed",
           shots=100000, seed=BASE_SEED + 2)
