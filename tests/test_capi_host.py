@@ -136,3 +136,36 @@ def test_header_is_plain_c():
                            capture_output=True, text=True)
         os.unlink(f.name)
         assert r.returncode == 0, r.stderr
+
+
+def test_eig_gram_argument_checks_before_device_work():
+    """ttn_eig_gram rejects bad shapes, routes and tolerances with EINVAL before
+    it touches the device; the wrapper rejects tensors that are not CUDA
+    complex128."""
+    _lib = _lib_or_skip()
+    lib = _lib.load_library()
+    fake = ctypes.c_void_p(16)  # never dereferenced: every call below fails its checks
+    s = (ctypes.c_double * 4)()
+    k = (ctypes.c_int32 * 1)()
+    cases = [(None, 1, 4, 4, 1, 1e-7), (fake, 0, 4, 4, 1, 1e-7), (fake, 1, 513, 4, 1, 1e-7),
+             (fake, 1, 4, 5, 1, 1e-7), (fake, 1, 4, 0, 1, 1e-7), (fake, 1, 4, 4, 4, 1e-7),
+             (fake, 1, 4, 4, -1, 1e-7), (fake, 1, 4, 4, 1, 1.0), (fake, 1, 100, 4, 0, 1e-7)]
+    for G, B, n, kc, route, eps in cases:
+        st = lib.ttn_eig_gram(G, B, n, kc, route, eps, fake, ctypes.cast(s, ctypes.POINTER(ctypes.c_double)),
+                              ctypes.cast(k, ctypes.POINTER(ctypes.c_int32)), None)
+        assert st == 1, (B, n, kc, route, eps)
+    torch = pytest.importorskip("torch")
+    import paper_2511_05719_gb300 as P
+    with pytest.raises(ValueError):
+        P.eig_gram(torch.zeros(4, 4, dtype=torch.complex128))
+    with pytest.raises(ValueError):
+        P.eig_gram(torch.zeros(4, 4, dtype=torch.complex64))
+
+
+def test_gemm_mode_range():
+    _lib = _lib_or_skip()
+    import paper_2511_05719_gb300 as P
+    c = P.Circuit(3, 1)
+    with pytest.raises(P.TTNError) as e:
+        P.run_trajectories(c, 1, noise="srx", theta=0.1, chi=8, precision="mixed", gemm_mode=4)
+    assert e.value.status == 1
