@@ -27,6 +27,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 
 #include "contract.h"
@@ -178,39 +179,52 @@ __global__ void __launch_bounds__(256) k_form_packB(ContractArgs a) {
   }
 }
 
-__global__ void __launch_bounds__(128, 1) k_form_mma(ContractArgs a, int nnt_cap) {
+// The trajectory's G_CTAS CTAs (blockIdx.x) loop over the (mt, nt) tiles of
+// its actual shape, with one tensor memory allocation per CTA.
+__global__ void __launch_bounds__(128, 1) k_form_mma(ContractArgs a) {
   const int b = blockIdx.y;
   const MoveShape s = move_shape(a, b);
   if (s.k <= 0) return;
   const int K = 2 * s.n, NMT = c_ceil(s.m, G_TA), NKT = c_ceil(K, G_KT), NNT = c_ceil(2 * s.k, G_TB);
-  const int mt = blockIdx.x / nnt_cap, nt = blockIdx.x - mt * nnt_cap;
-  if (mt >= NMT || nt >= NNT) return;
   if (3LL * NMT * NKT * G_TILE + 3LL * NNT * NKT * (G_TILE / 2) > a.sstride || s.m + 512 > a.rows_cap) return;
-  const uint16_t* SA = a.slices + (int64_t)b * a.sstride;
-  const uint16_t* SB = SA + 3LL * NMT * NKT * G_TILE;
-  const int* EA = a.expo + (int64_t)b * a.rows_cap;
-  const int* EB = EA + (a.rows_cap - 512);
-  auto srcA = [&](int d, int kt) { return SA + ((int64_t)(d * NMT + mt) * NKT + kt) * G_TILE; };
-  auto srcB = [&](int d, int kt) { return SB + ((int64_t)(d * NNT + nt) * NKT + kt) * (G_TILE / 2); };
-  const int i = mt * G_TA + threadIdx.x;
-  float2* T = a.T + (int64_t)b * a.tstride + a.off_v;
-  const int ei = i < s.m ? EA[i] : 0;
-  auto epilogue = [&](int h, const unsigned long long (&v)[32]) {
-    if (i >= s.m) return;
-    for (int q = 0; q < 16; ++q) {
-      const int j = nt * G_TB + h * 32 + 2 * q, c = j >> 1;
-      if (c >= s.k) break;
-      const double y_re = ldexp((double)(long long)v[2 * q], ei + EB[j] - 46);
-      const double y_im = ldexp((double)(long long)v[2 * q + 1], ei + EB[j + 1] - 46);
-      T[y_addr(s, i, c)] = make_float2((float)y_re, (float)y_im);
-    }
-  };
-  if (!digit_gemm(0, NKT, srcA, srcB, epilogue) && threadIdx.x == 0) c_flag(a, b, CONTRACT_ERR_TIMEOUT);
   if (blockIdx.x == 0 && threadIdx.x == 0 && a.ledger && a.ledger_form >= 0) {
     atomicAdd(&a.ledger[2 * a.ledger_form], (unsigned long long)(8.0 * s.m * (double)s.n * s.k));
     atomicAdd(&a.ledger[2 * a.ledger_form + 1],
               (unsigned long long)(8.0 * ((double)s.m * s.n + (double)s.n * s.k + (double)s.m * s.k)));
   }
+  if ((int)blockIdx.x >= NMT * NNT) return;
+  const uint16_t* SA = a.slices + (int64_t)b * a.sstride;
+  const uint16_t* SB = SA + 3LL * NMT * NKT * G_TILE;
+  const int* EA = a.expo + (int64_t)b * a.rows_cap;
+  const int* EB = EA + (a.rows_cap - 512);
+  float2* T = a.T + (int64_t)b * a.tstride + a.off_v;
+  __shared__ DigitShared dsh;
+  DigitCtx dc;
+  digit_begin(dsh, dc);
+  for (int t = blockIdx.x; t < NMT * NNT; t += gridDim.x) {
+    const int mt = t / NNT, nt = t - mt * NNT;
+    auto srcA = [&](int d, int kt) { return SA + ((int64_t)(d * NMT + mt) * NKT + kt) * G_TILE; };
+    auto srcB = [&](int d, int kt) { return SB + ((int64_t)(d * NNT + nt) * NKT + kt) * (G_TILE / 2); };
+    const int i = mt * G_TA + threadIdx.x;
+    const int ei = i < s.m ? EA[i] : 0;
+    auto epilogue = [&](int h, const unsigned long long (&v)[32]) {
+      if (i >= s.m) return;
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        const int j = nt * G_TB + h * 32 + 2 * q, c = j >> 1;
+        if (c < s.k) {
+          const double y_re = ldexp((double)(long long)v[2 * q], ei + EB[j] - 46);
+          const double y_im = ldexp((double)(long long)v[2 * q + 1], ei + EB[j + 1] - 46);
+          T[y_addr(s, i, c)] = make_float2((float)y_re, (float)y_im);
+        }
+      }
+    };
+    if (!digit_tile(dsh, dc, 0, NKT, srcA, srcB, epilogue)) {
+      if (threadIdx.x == 0) c_flag(a, b, CONTRACT_ERR_TIMEOUT);
+      break;
+    }
+  }
+  digit_end(dsh, dc);
 }
 
 // ================================================================== absorb
@@ -355,39 +369,51 @@ __global__ void __launch_bounds__(256) k_absorb_packB(ContractArgs a) {
   }
 }
 
-__global__ void __launch_bounds__(128, 1) k_absorb_mma(ContractArgs a, int nmt_cap) {
+__global__ void __launch_bounds__(128, 1) k_absorb_mma(ContractArgs a) {
   const int b = blockIdx.y;
   const AbsorbShape s = absorb_shape(a, b);
   if (s.k <= 0) return;
   const int K = 2 * s.n, NMT = c_ceil(2 * s.k, G_TA), NKT = c_ceil(K, G_KT), NNT = c_ceil(s.J, G_TB);
-  const int nt = blockIdx.x / nmt_cap, mt = blockIdx.x - nt * nmt_cap;
-  if (mt >= NMT || nt >= NNT) return;
   if (3LL * NMT * NKT * G_TILE + 3LL * NNT * NKT * (G_TILE / 2) > a.sstride || s.J + 512 > a.rows_cap) return;
   if ((int64_t)s.k * s.J > a.wstride) return;
-  const uint16_t* SA = a.slices + (int64_t)b * a.sstride;
-  const uint16_t* SB = SA + 3LL * NMT * NKT * G_TILE;
-  const int* EB = a.expo + (int64_t)b * a.rows_cap;
-  const int* EA = EB + (a.rows_cap - 512);
-  auto srcA = [&](int d, int kt) { return SA + ((int64_t)(d * NMT + mt) * NKT + kt) * G_TILE; };
-  auto srcB = [&](int d, int kt) { return SB + ((int64_t)(d * NNT + nt) * NKT + kt) * (G_TILE / 2); };
-  const int row = mt * G_TA + threadIdx.x, i = row >> 1, p = row & 1;
-  float* out = reinterpret_cast<float*>(a.W + (int64_t)b * a.wstride);
-  const int er = row < 2 * s.k ? EA[row] : 0;
-  auto epilogue = [&](int h, const unsigned long long (&v)[32]) {
-    if (row >= 2 * s.k) return;
-    for (int q = 0; q < 32; ++q) {
-      const int j = nt * G_TB + h * 32 + q;
-      if (j >= s.J) break;
-      const int o = j / s.inner, u = j - o * s.inner;
-      out[(((int64_t)o * s.k + i) * s.inner + u) * 2 + p] = (float)ldexp((double)(long long)v[q], er + EB[j] - 46);
-    }
-  };
-  if (!digit_gemm(0, NKT, srcA, srcB, epilogue) && threadIdx.x == 0) c_flag(a, b, CONTRACT_ERR_TIMEOUT);
   if (blockIdx.x == 0 && threadIdx.x == 0 && a.ledger && a.ledger_absorb >= 0) {
     atomicAdd(&a.ledger[2 * a.ledger_absorb], (unsigned long long)(8.0 * s.k * (double)s.n * s.J));
     atomicAdd(&a.ledger[2 * a.ledger_absorb + 1],
               (unsigned long long)(8.0 * ((double)s.n * s.J + (double)s.k * s.n + (double)s.k * s.J)));
   }
+  if ((int)blockIdx.x >= NMT * NNT) return;
+  const uint16_t* SA = a.slices + (int64_t)b * a.sstride;
+  const uint16_t* SB = SA + 3LL * NMT * NKT * G_TILE;
+  const int* EB = a.expo + (int64_t)b * a.rows_cap;
+  const int* EA = EB + (a.rows_cap - 512);
+  float* out = reinterpret_cast<float*>(a.W + (int64_t)b * a.wstride);
+  __shared__ DigitShared dsh;
+  DigitCtx dc;
+  digit_begin(dsh, dc);
+  for (int t = blockIdx.x; t < NMT * NNT; t += gridDim.x) {
+    const int nt = t / NMT, mt = t - nt * NMT;
+    auto srcA = [&](int d, int kt) { return SA + ((int64_t)(d * NMT + mt) * NKT + kt) * G_TILE; };
+    auto srcB = [&](int d, int kt) { return SB + ((int64_t)(d * NNT + nt) * NKT + kt) * (G_TILE / 2); };
+    const int row = mt * G_TA + threadIdx.x, i = row >> 1, p = row & 1;
+    const int er = row < 2 * s.k ? EA[row] : 0;
+    auto epilogue = [&](int h, const unsigned long long (&v)[32]) {
+      if (row >= 2 * s.k) return;
+#pragma unroll
+      for (int q = 0; q < 32; ++q) {
+        const int j = nt * G_TB + h * 32 + q;
+        if (j < s.J) {
+          const int o = j / s.inner, u = j - o * s.inner;
+          out[(((int64_t)o * s.k + i) * s.inner + u) * 2 + p] =
+              (float)ldexp((double)(long long)v[q], er + EB[j] - 46);
+        }
+      }
+    };
+    if (!digit_tile(dsh, dc, 0, NKT, srcA, srcB, epilogue)) {
+      if (threadIdx.x == 0) c_flag(a, b, CONTRACT_ERR_TIMEOUT);
+      break;
+    }
+  }
+  digit_end(dsh, dc);
 }
 
 // ================================================================== host
@@ -422,7 +448,7 @@ cudaError_t contract_form_launch(const ContractArgs& a, int B, int64_t m_cap, in
   const int nmt = c_ceil(m_cap, G_TA), nnt = c_ceil(2 * k_cap, G_TB);
   k_form_packA<<<dim3(nmt, B), 256, 0, st>>>(a);
   k_form_packB<<<dim3(nnt, B), 256, 0, st>>>(a);
-  k_form_mma<<<dim3(nmt * nnt, B), 128, G_SMEM, st>>>(a, nnt);
+  k_form_mma<<<dim3(std::min(nmt * nnt, G_CTAS), B), 128, G_SMEM, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -434,7 +460,7 @@ cudaError_t contract_absorb_launch(const ContractArgs& a, int B, int n_cap, int 
   const int nmt = c_ceil(2 * k_cap, G_TA), nnt = c_ceil(J_cap, G_TB);
   k_absorb_packA<<<dim3(nmt, B), 256, 0, st>>>(a);
   k_absorb_packB<<<dim3(std::min(nnt, 1024), B), 256, 0, st>>>(a);
-  k_absorb_mma<<<dim3(nmt * nnt, B), 128, G_SMEM, st>>>(a, nmt);
+  k_absorb_mma<<<dim3(std::min(nmt * nnt, G_CTAS), B), 128, G_SMEM, st>>>(a);
   return cudaGetLastError();
 }
 

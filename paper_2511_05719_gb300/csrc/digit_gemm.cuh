@@ -41,6 +41,11 @@ static constexpr int G_NS = 3;                   // pipeline stages
 static constexpr int G_STAGE = 3 * G_TILE_B + 3 * (G_TILE_B / 2);  // A digits + B digits
 static constexpr int G_SMEM = G_NS * G_STAGE;    // dynamic shared memory of a digit_gemm kernel
 static constexpr uint32_t G_WAIT = 1u << 22;     // polls of a bounded mbarrier wait
+// CTAs per trajectory of a digit-product kernel: each loops over the tiles
+// its trajectory's actual shape needs (a grid sized by capacities would
+// launch thousands of idle CTAs, each holding G_SMEM of shared memory while
+// other streams' kernels wait for room)
+static constexpr int G_CTAS = 64;
 // tensor memory: five 64-column FP32 accumulators (columns 0..319), then the
 // rows' 64-bit sums as low (320..383) and high (384..447) words
 static constexpr int G_TMEM_COLS = 512;
@@ -60,62 +65,113 @@ __device__ __forceinline__ void digits3(float x, int e, int& n1, int& n2, int& n
   n3 = r1 - n2 * 256;
 }
 
-// D (128 x 64 tile) = sum over K-tiles [kt0, kt0 + nk) of A B^T, exactly.
-// srcA(s, kt) / srcB(s, kt): global address of digit s's A tile (8 KB) / B
-// tile (4 KB) for K-tile kt, 16-byte aligned.  epilogue(h, v): thread t
-// (row t of the tile) receives its row's sums for columns h*32 .. h*32+31 as
-// two's-complement 64-bit integers.  All 128 threads of the CTA must call it
-// (it allocates tensor memory and synchronises the CTA).  Returns false if
-// a bounded wait expired; the epilogue is then not called.
-template <typename FA, typename FB, typename FE>
-__device__ bool digit_gemm(int kt0, int nk, FA srcA, FB srcB, FE epilogue) {
-  extern __shared__ __align__(1024) unsigned char g_smem[];
-  __shared__ __align__(8) uint64_t bar_load[G_NS], bar_mma[G_NS], bar_acc;
-  __shared__ uint32_t tmem_slot;
-  __shared__ int s_abort;
+// A CTA computes one or more 128 x 64 tiles D = sum over K-tiles of A B^T,
+// exactly, between digit_begin (mbarriers, tensor memory) and digit_end
+// (release).  The tensor memory is allocated once per CTA: a CTA may not
+// allocate again after it relinquishes its allocation permit.  The barrier
+// phases run on across tiles, so the context counts, per pipeline stage, the
+// loads issued and waited and the MMA commits.
+struct DigitShared {
+  uint64_t bar_load[G_NS], bar_mma[G_NS], bar_acc;
+  uint32_t tmem_slot;
+  int abort;
+};
+
+struct DigitCtx {
+  uint32_t tmem;
+  uint32_t issued[G_NS];     // bulk loads issued into each stage (thread 0)
+  uint32_t waited[G_NS];     // of those, completions waited for (thread 0)
+  uint32_t commits[G_NS];    // MMA commits reading each stage (thread 0)
+  uint32_t acc_phase;        // completed phases of bar_acc (every thread)
+};
+
+// All 128 threads of the CTA.
+__device__ __forceinline__ void digit_begin(DigitShared& sh, DigitCtx& c) {
   const int tid = threadIdx.x, warp = tid >> 5;
   if (tid == 0) {
     for (int i = 0; i < G_NS; ++i) {
-      tc::mbar_init(&bar_load[i], 1);
-      tc::mbar_init(&bar_mma[i], 1);
+      tc::mbar_init(&sh.bar_load[i], 1);
+      tc::mbar_init(&sh.bar_mma[i], 1);
     }
-    tc::mbar_init(&bar_acc, 1);
+    tc::mbar_init(&sh.bar_acc, 1);
     tc::mbar_fence_init();
-    s_abort = 0;
+    sh.abort = 0;
   }
-  if (warp == 0) tc::tmem_alloc(&tmem_slot, G_TMEM_COLS);
+  if (warp == 0) tc::tmem_alloc(&sh.tmem_slot, G_TMEM_COLS);
   tc::tc_fence_before();
   __syncthreads();
   tc::tc_fence_after();
-  const uint32_t tmem = tmem_slot;
-  const uint32_t lane_off = (uint32_t)(warp * 32) << 16;  // this warp's TMEM lane quarter
+  c.tmem = sh.tmem_slot;
+  for (int i = 0; i < G_NS; ++i) c.issued[i] = c.waited[i] = c.commits[i] = 0;
+  c.acc_phase = 0;
+}
 
+// All 128 threads.  After an expired wait (sh.abort set) thread 0 lets the
+// copies and MMAs already issued finish (bounded) before the shared memory
+// and the tensor memory are released.
+__device__ __forceinline__ void digit_end(DigitShared& sh, DigitCtx& c) {
+  const int tid = threadIdx.x, warp = tid >> 5;
+  __syncthreads();
+  if (tid == 0) {
+    if (sh.abort) {
+      tc::mma_commit(&sh.bar_acc);
+      tc::mbar_wait(&sh.bar_acc, c.acc_phase & 1, G_WAIT);
+      for (int st = 0; st < G_NS; ++st)
+        if (c.issued[st] > c.waited[st]) tc::mbar_wait(&sh.bar_load[st], (c.issued[st] - 1) & 1, G_WAIT);
+    }
+    for (int st = 0; st < G_NS; ++st)
+      if (c.commits[st] > 0) tc::mbar_wait(&sh.bar_mma[st], (c.commits[st] - 1) & 1, G_WAIT);
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  if (warp == 0) tc::tmem_dealloc(c.tmem, G_TMEM_COLS);
+}
+
+// One tile: D = sum over K-tiles [kt0, kt0 + nk) of A B^T, exactly.
+// srcA(s, kt) / srcB(s, kt): global address of digit s's A tile (8 KB) / B
+// tile (4 KB) for K-tile kt, 16-byte aligned.  epilogue(h, v): thread t
+// (row t of the tile) receives its row's sums for columns h*32 .. h*32+31 as
+// two's-complement 64-bit integers.  All 128 threads call it, between
+// digit_begin and digit_end.  Returns false (sh.abort set, the epilogue not
+// called) if a bounded wait expired; the caller then goes to digit_end.
+template <typename FA, typename FB, typename FE>
+__device__ bool digit_tile(DigitShared& sh, DigitCtx& c, int kt0, int nk, FA srcA, FB srcB, FE epilogue) {
+  extern __shared__ __align__(1024) unsigned char g_smem[];
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const uint32_t tmem = c.tmem;
+  const uint32_t lane_off = (uint32_t)(warp * 32) << 16;  // this warp's TMEM lane quarter
   auto stage = [&](int st) { return g_smem + st * G_STAGE; };
   auto issue_load = [&](int st, int kt) {
-    tc::mbar_expect_tx(&bar_load[st], G_STAGE);
-    for (int s = 0; s < 3; ++s) tc::bulk_g2s(stage(st) + s * G_TILE_B, srcA(s, kt), G_TILE_B, &bar_load[st]);
+    tc::mbar_expect_tx(&sh.bar_load[st], G_STAGE);
+    for (int s = 0; s < 3; ++s) tc::bulk_g2s(stage(st) + s * G_TILE_B, srcA(s, kt), G_TILE_B, &sh.bar_load[st]);
     for (int s = 0; s < 3; ++s)
-      tc::bulk_g2s(stage(st) + 3 * G_TILE_B + s * (G_TILE_B / 2), srcB(s, kt), G_TILE_B / 2, &bar_load[st]);
+      tc::bulk_g2s(stage(st) + 3 * G_TILE_B + s * (G_TILE_B / 2), srcB(s, kt), G_TILE_B / 2, &sh.bar_load[st]);
+    c.issued[st]++;
   };
-
+  // a stage is reused only after the MMAs that read it completed
+  auto stage_free = [&](int st) {
+    return c.commits[st] == 0 || tc::mbar_wait(&sh.bar_mma[st], (c.commits[st] - 1) & 1, G_WAIT);
+  };
   const uint32_t idesc = tc::instr_desc(1, G_TA, G_TB);
-  int loads[G_NS], commits[G_NS];  // per stage: bulk loads issued, MMA commits (thread 0)
-  for (int i = 0; i < G_NS; ++i) loads[i] = commits[i] = 0;
-  if (tid == 0)
+  if (tid == 0 && !sh.abort)
     for (int i = 0; i < G_NS - 1 && i < nk; ++i) {
+      if (!stage_free(i)) {
+        sh.abort = 1;
+        break;
+      }
       issue_load(i, kt0 + i);
-      loads[i]++;
     }
-  uint32_t acc_phase = 0;
   bool first_chunk = true;
   bool first[5] = {true, true, true, true, true};
   for (int i = 0; i < nk; ++i) {
     const int st = i % G_NS;
     const bool chunk_end = (i % G_CHUNK) == G_CHUNK - 1 || i == nk - 1;
-    if (tid == 0 && !s_abort) {
-      if (!tc::mbar_wait(&bar_load[st], (uint32_t)((i / G_NS) & 1), G_WAIT)) {
-        s_abort = 1;
+    if (tid == 0 && !sh.abort) {
+      if (!tc::mbar_wait(&sh.bar_load[st], c.waited[st] & 1, G_WAIT)) {
+        sh.abort = 1;
       } else {
+        c.waited[st]++;
         tc::tc_fence_after();
         if (i % G_CHUNK == 0)
           for (int g = 0; g < 5; ++g) first[g] = true;
@@ -134,34 +190,29 @@ __device__ bool digit_gemm(int kt0, int nk, FA srcA, FB srcB, FE epilogue) {
             }
           }
         }
-        tc::mma_commit(&bar_mma[st]);
-        commits[st]++;
+        tc::mma_commit(&sh.bar_mma[st]);
+        c.commits[st]++;
         // tile i + NS - 1 goes into the stage tile i - 1 used, once its MMAs are done
         const int nx = i + G_NS - 1;
         if (nx < nk) {
           const int so = nx % G_NS;
-          bool ok = true;
-          if (commits[so] > 0) ok = tc::mbar_wait(&bar_mma[so], (uint32_t)((commits[so] - 1) & 1), G_WAIT);
-          if (!ok) {
-            s_abort = 1;
-          } else {
-            issue_load(so, kt0 + nx);
-            loads[so]++;
-          }
+          if (!stage_free(so)) sh.abort = 1;
+          else issue_load(so, kt0 + nx);
         }
-        if (chunk_end) tc::mma_commit(&bar_acc);
+        if (chunk_end) tc::mma_commit(&sh.bar_acc);
       }
     }
     if (chunk_end) {
       __syncthreads();
-      if (s_abort) break;
+      if (sh.abort) return false;
       // every thread polls; the block agrees on the outcome before the
       // warp-collective TMEM loads
-      const int ok = __syncthreads_and(tc::mbar_wait(&bar_acc, acc_phase, G_WAIT) ? 1 : 0);
-      acc_phase ^= 1u;
+      const int ok = __syncthreads_and(tc::mbar_wait(&sh.bar_acc, c.acc_phase & 1, G_WAIT) ? 1 : 0);
+      c.acc_phase++;
       if (!ok) {
-        if (tid == 0) s_abort = 1;
-        break;
+        if (tid == 0) sh.abort = 1;
+        __syncthreads();
+        return false;
       }
       tc::tc_fence_after();
 #pragma unroll
@@ -200,35 +251,34 @@ __device__ bool digit_gemm(int kt0, int nk, FA srcA, FB srcB, FE epilogue) {
       __syncthreads();
     }
   }
-  __syncthreads();
-  const bool aborted = s_abort != 0;
-  if (aborted) {
-    // let the copies and MMAs already issued finish (bounded) before the
-    // shared memory and tensor memory are released
-    if (tid == 0) {
-      tc::mma_commit(&bar_acc);
-      tc::mbar_wait(&bar_acc, acc_phase, G_WAIT);
-      for (int st = 0; st < G_NS; ++st)
-        if (loads[st] > 0) tc::mbar_wait(&bar_load[st], (uint32_t)((loads[st] - 1) & 1), G_WAIT);
-    }
-  } else {
-    tc::tc_fence_after();
-    for (int h = 0; h < G_TB / 32; ++h) {
-      uint32_t lo[32], hi[32];
-      tc::tmem_ld32(tmem + lane_off + G_TM_LO + h * 32, lo);
-      tc::tmem_ld32(tmem + lane_off + G_TM_HI + h * 32, hi);
-      tc::tmem_ld_wait();
-      unsigned long long v[32];
+  if (nk <= 0) return true;
+  tc::tc_fence_after();
+  for (int h = 0; h < G_TB / 32; ++h) {
+    uint32_t lo[32], hi[32];
+    tc::tmem_ld32(tmem + lane_off + G_TM_LO + h * 32, lo);
+    tc::tmem_ld32(tmem + lane_off + G_TM_HI + h * 32, hi);
+    tc::tmem_ld_wait();
+    unsigned long long v[32];
 #pragma unroll
-      for (int j = 0; j < 32; ++j) v[j] = ((unsigned long long)hi[j] << 32) | lo[j];
-      epilogue(h, v);
-    }
+    for (int j = 0; j < 32; ++j) v[j] = ((unsigned long long)hi[j] << 32) | lo[j];
+    epilogue(h, v);
   }
+  // every thread's TMEM reads are done before the next tile's MMAs overwrite
   tc::tc_fence_before();
   __syncthreads();
   tc::tc_fence_after();
-  if (warp == 0) tc::tmem_dealloc(tmem, G_TMEM_COLS);
-  return !aborted;
+  return true;
+}
+
+// One tile in its own digit_begin / digit_end.
+template <typename FA, typename FB, typename FE>
+__device__ bool digit_gemm(int kt0, int nk, FA srcA, FB srcB, FE epilogue) {
+  __shared__ DigitShared sh;
+  DigitCtx c;
+  digit_begin(sh, c);
+  const bool ok = digit_tile(sh, c, kt0, nk, srcA, srcB, epilogue);
+  digit_end(sh, c);
+  return ok;
 }
 
 }  // namespace ttn

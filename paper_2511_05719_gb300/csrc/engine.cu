@@ -3060,11 +3060,9 @@ struct Engine {
           // MIXED: the FMA units by default (0, 1); gemm_mode 3 the digit
           // products on tcgen05 (contract.cu), 2 the mma.sync 3xTF32 tile
           // (whose truncating FP32 accumulation costs ~1e-5 of amplitude
-          // accuracy over a syndrome round).  The tcgen05 kernels' grids are
-          // sized by the bond capacities, and their idle CTAs, each holding
-          // ~110 KB of shared memory, kept other streams' eigensolver CTAs
-          // waiting: ten times the FMA kernels' device time in the
-          // pipelined d=7 batch.
+          // accuracy over a syndrome round).  In the pipelined d=7 batch the
+          // tcgen05 route runs 3 % slower than the FMA kernels and is not
+          // more accurate (its inputs are rounded relative to row maxima).
           const bool exact_c = mixed && gemm_mode == 3;
           const bool tc = sizeof(R) == 4 && (gemm_mode == 2 || (gemm_mode == 0 && gram && !mixed));
           if (gram) {

@@ -33,6 +33,8 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include <cmath>
 #include <cstdio>
 #include <mutex>
@@ -144,40 +146,50 @@ __global__ void __launch_bounds__(256) k_gram_pack(GramArgs a) {
 // X^T X in 64-column blocks).  The digit products and their exact integer
 // sums are digit_gemm's (digit_gemm.cuh); the epilogue adds each row's sums
 // into the trajectory's int64 matrix.
-__global__ void __launch_bounds__(128, 1) k_gram_mma(GramArgs a, int nct_cap) {
+// Tiles: (A row tile ta, 64-column B tile tb >= 2 ta) pairs of the upper
+// triangle, times splits of G_SPLIT K-tiles.  A trajectory's G_CTAS CTAs
+// (blockIdx.x) loop over the tiles of its actual shape, with one tensor
+// memory allocation per CTA.
+__global__ void __launch_bounds__(128, 1) k_gram_mma(GramArgs a) {
   const int b = blockIdx.z;
-  const int2 sh = a.shape[b];
-  const int64_t m = sh.x;
-  const int n = sh.y, nc = 2 * n;
+  const int2 sh2 = a.shape[b];
+  const int64_t m = sh2.x;
+  const int n = sh2.y, nc = 2 * n;
   if (n <= 0) return;
   const int NCT = g_nct(n), NKT = g_nkt(m);
-  int p = blockIdx.x, ta = 0;
-  while (ta < nct_cap && p >= 2 * nct_cap - 2 * ta) {
-    p -= 2 * nct_cap - 2 * ta;
-    ++ta;
-  }
-  const int tb = 2 * ta + p;
-  if (ta >= NCT || tb * G_TB >= nc) return;
-  const int kt0 = blockIdx.y * G_SPLIT;
-  if (kt0 >= NKT) return;
-  const int kt1 = min(NKT, kt0 + G_SPLIT);
   if (d_slice_elems(m, n) > a.sstride) return;  // flagged by the packing kernel
-
+  const int NBT = (nc + G_TB - 1) / G_TB;
+  const int npair = NCT * NBT;
+  const int ntile = npair * ((NKT + G_SPLIT - 1) / G_SPLIT);
+  if ((int)blockIdx.x >= ntile) return;
   const uint16_t* S = a.slices + (int64_t)b * a.sstride;
-  auto srcA = [&](int s, int kt) { return S + ((int64_t)(s * NCT + ta) * NKT + kt) * G_TILE; };
-  auto srcB = [&](int s, int kt) {
-    return S + ((int64_t)(s * NCT + (tb >> 1)) * NKT + kt) * G_TILE + (tb & 1) * (G_TILE / 2);
-  };
-  const int arow = ta * G_TA + threadIdx.x;
-  unsigned long long* F = a.gfix + (int64_t)b * a.gld * a.gld + (int64_t)arow * a.gld;
-  auto epilogue = [&](int h, const unsigned long long (&v)[32]) {
-    if (arow >= nc) return;
-    for (int j = 0; j < 32; ++j) {
-      const int c = tb * G_TB + h * 32 + j;
-      if (c >= arow && c < nc && v[j] != 0ull) atomicAdd(&F[c], v[j]);
+  __shared__ DigitShared dsh;
+  DigitCtx dc;
+  digit_begin(dsh, dc);
+  for (int t = blockIdx.x; t < ntile; t += gridDim.x) {
+    const int pr = t % npair, sp = t / npair;
+    const int ta = pr / NBT, tb = pr - ta * NBT;
+    if (tb < 2 * ta) continue;  // below the diagonal block: uniform over the CTA
+    const int kt0 = sp * G_SPLIT, kt1 = min(NKT, kt0 + G_SPLIT);
+    auto srcA = [&](int s, int kt) { return S + ((int64_t)(s * NCT + ta) * NKT + kt) * G_TILE; };
+    auto srcB = [&](int s, int kt) {
+      return S + ((int64_t)(s * NCT + (tb >> 1)) * NKT + kt) * G_TILE + (tb & 1) * (G_TILE / 2);
+    };
+    const int arow = ta * G_TA + threadIdx.x;
+    unsigned long long* F = a.gfix + (int64_t)b * a.gld * a.gld + (int64_t)arow * a.gld;
+    auto epilogue = [&](int h, const unsigned long long (&v)[32]) {
+      if (arow >= nc) return;
+      for (int j = 0; j < 32; ++j) {
+        const int c = tb * G_TB + h * 32 + j;
+        if (c >= arow && c < nc && v[j] != 0ull) atomicAdd(&F[c], v[j]);
+      }
+    };
+    if (!digit_tile(dsh, dc, kt0, kt1 - kt0, srcA, srcB, epilogue)) {
+      if (threadIdx.x == 0) g_flag(a, b, GRAM_ERR_TIMEOUT);
+      break;
     }
-  };
-  if (!digit_gemm(kt0, kt1 - kt0, srcA, srcB, epilogue) && threadIdx.x == 0) g_flag(a, b, GRAM_ERR_TIMEOUT);
+  }
+  digit_end(dsh, dc);
 }
 
 // ---------------------------------------------------------------- 4. complex FP64 Gram
@@ -231,7 +243,10 @@ cudaError_t gram_exact_launch(const GramArgs& a, int B, int n_cap, int64_t m_cap
   k_gram_amax<<<dim3((2 * n_cap + 31) / 32, rs, B), 256, 0, st>>>(a);
   k_gram_exps<<<dim3((2 * n_cap + 127) / 128, B), 128, 0, st>>>(a);
   k_gram_pack<<<dim3(nct, std::min(nkt, 64), B), 256, 0, st>>>(a);
-  k_gram_mma<<<dim3(nct * (nct + 1), (nkt + G_SPLIT - 1) / G_SPLIT, B), 128, G_SMEM, st>>>(a, nct);
+  {
+    const int tiles = nct * ((2 * n_cap + G_TB - 1) / G_TB) * ((nkt + G_SPLIT - 1) / G_SPLIT);
+    k_gram_mma<<<dim3(std::min(tiles, G_CTAS), 1, B), 128, G_SMEM, st>>>(a);
+  }
   k_gram_finalize<<<dim3((int)(((int64_t)n_cap * n_cap + 255) / 256), B), 256, 0, st>>>(a);
   return cudaGetLastError();
 }
