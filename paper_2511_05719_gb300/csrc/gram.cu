@@ -147,7 +147,7 @@ __global__ void __launch_bounds__(256) k_gram_pack(GramArgs a) {
 // sums are digit_gemm's (digit_gemm.cuh); the epilogue adds each row's sums
 // into the trajectory's int64 matrix.
 // Tiles: (A row tile ta, 64-column B tile tb >= 2 ta) pairs of the upper
-// triangle, times splits of G_SPLIT K-tiles.  A trajectory's G_CTAS CTAs
+// triangle, enumerated row by row, times splits of G_SPLIT K-tiles.  A trajectory's G_CTAS CTAs
 // (blockIdx.x) loop over the tiles of its actual shape, with one tensor
 // memory allocation per CTA.
 __global__ void __launch_bounds__(128, 1) k_gram_mma(GramArgs a) {
@@ -158,8 +158,7 @@ __global__ void __launch_bounds__(128, 1) k_gram_mma(GramArgs a) {
   if (n <= 0) return;
   const int NCT = g_nct(n), NKT = g_nkt(m);
   if (d_slice_elems(m, n) > a.sstride) return;  // flagged by the packing kernel
-  const int NBT = (nc + G_TB - 1) / G_TB;
-  const int npair = NCT * NBT;
+  const int npair = NCT * (NCT + 1);  // (ta, tb) with 2 ta <= tb < 2 NCT, row by row
   const int ntile = npair * ((NKT + G_SPLIT - 1) / G_SPLIT);
   if ((int)blockIdx.x >= ntile) return;
   const uint16_t* S = a.slices + (int64_t)b * a.sstride;
@@ -167,9 +166,14 @@ __global__ void __launch_bounds__(128, 1) k_gram_mma(GramArgs a) {
   DigitCtx dc;
   digit_begin(dsh, dc);
   for (int t = blockIdx.x; t < ntile; t += gridDim.x) {
-    const int pr = t % npair, sp = t / npair;
-    const int ta = pr / NBT, tb = pr - ta * NBT;
-    if (tb < 2 * ta) continue;  // below the diagonal block: uniform over the CTA
+    const int sp = t / npair;
+    int p = t - sp * npair, ta = 0;
+    while (p >= 2 * NCT - 2 * ta) {
+      p -= 2 * NCT - 2 * ta;
+      ++ta;
+    }
+    const int tb = 2 * ta + p;
+    if (tb * G_TB >= nc) continue;  // past the last column (2n an odd multiple of 64): uniform
     const int kt0 = sp * G_SPLIT, kt1 = min(NKT, kt0 + G_SPLIT);
     auto srcA = [&](int s, int kt) { return S + ((int64_t)(s * NCT + ta) * NKT + kt) * G_TILE; };
     auto srcB = [&](int s, int kt) {
@@ -244,7 +248,7 @@ cudaError_t gram_exact_launch(const GramArgs& a, int B, int n_cap, int64_t m_cap
   k_gram_exps<<<dim3((2 * n_cap + 127) / 128, B), 128, 0, st>>>(a);
   k_gram_pack<<<dim3(nct, std::min(nkt, 64), B), 256, 0, st>>>(a);
   {
-    const int tiles = nct * ((2 * n_cap + G_TB - 1) / G_TB) * ((nkt + G_SPLIT - 1) / G_SPLIT);
+    const int tiles = nct * (nct + 1) * ((nkt + G_SPLIT - 1) / G_SPLIT);
     k_gram_mma<<<dim3(std::min(tiles, G_CTAS), 1, B), 128, G_SMEM, st>>>(a);
   }
   k_gram_finalize<<<dim3((int)(((int64_t)n_cap * n_cap + 255) / 256), B), 256, 0, st>>>(a);
