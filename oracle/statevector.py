@@ -168,6 +168,45 @@ def run_trajectory(circ, model, theta, gamma, seed, traj, snapshot_layers=()):
     return dict(rec=rec, logp=logp, margin=margin, states=states, sv=sv, branch_p=branch_p)
 
 
+def record_log_prob(circ, model, theta, gamma, rec):
+    """log p(record; theta, gamma) of a given measurement record for a noise
+    model whose only random branches are the measurements (NONE, SRX): the
+    circuit run with every measurement forced to its recorded outcome, the
+    log-probabilities of those outcomes summed (-inf if one is impossible).
+    Its central difference in theta is the per-trajectory score
+    d log p / d theta of the score-function gradient (Sec. IV.A, the slopes
+    of the crossing search)."""
+    if model not in (NONE, SRX):
+        raise ValueError("record_log_prob: the record fixes every branch only for NONE and SRX")
+    N = circ.n_qubits
+    sv = StateVector(N)
+    last = np.zeros(N, dtype=np.int64)
+    logp = 0.0
+    for (kind, a, b, e, r, layer) in circ.ops:
+        if kind in (PREP_Z, PREP_X):
+            if last[a]:
+                sv.apply1(a, X)
+                last[a] = 0
+            if kind == PREP_X:
+                sv.apply1(a, H)
+        elif kind == CNOT:
+            sv.cnot(a, b)
+        elif kind in (MEAS_Z, MEAS_X):
+            if kind == MEAS_X:
+                sv.apply1(a, H)
+            p1 = sv.prob1(a)
+            m = int(rec[r])
+            pm = p1 if m else 1.0 - p1
+            if pm <= 0.0:
+                return -math.inf
+            sv.project(a, m, pm)
+            logp += math.log(pm)
+            last[a] = m
+        elif kind == NOISE:
+            apply_noise(sv, a, model, theta, gamma, 0.0)
+    return logp
+
+
 def run_trajectories(circ, model, theta, gamma, seed, trajs):
     recs = np.zeros((len(trajs), circ.n_record_bits), dtype=np.uint8)
     logps = np.zeros(len(trajs))

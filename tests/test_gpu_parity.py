@@ -232,6 +232,23 @@ def test_grad_matches_exact_derivative_d3_c1():
     assert abs(score.mean()) < 3 * score.std() / np.sqrt(shots)
 
 
+def test_grad_scores_match_oracle_per_trajectory():
+    """Each trajectory's score (the central difference of its forced replays at
+    theta +- h) against the state-vector oracle's log p of the same record at
+    theta +- h, same h: FP64, d = 3, untruncated (chi = 64)."""
+    theta, h, shots = 0.12, 1e-4, 16
+    c = P.Circuit(3, 1)
+    circ = build_circuit(3, 1)
+    kw = dict(noise="srx", theta=theta, chi=64, precision="fp64", seed=W.BASE_SEED + 5)
+    out = P.run_trajectories(c, shots, **kw)
+    pl, g, sg, score = P.grad(c, shots, wrt="theta", h=h, return_score=True, **kw)
+    for i in range(shots):
+        rec = out["records"][i]
+        want = (SV.record_log_prob(circ, SRX, theta + h, 0.0, rec)
+                - SV.record_log_prob(circ, SRX, theta - h, 0.0, rec)) / (2 * h)
+        assert abs(score[i] - want) <= 1e-6 * (1.0 + abs(want)), (i, score[i], want)
+
+
 def test_grad_ad_and_argument_checks():
     c = P.Circuit(3, 1)
     pl, g, sg = P.grad(c, 2000, wrt="gamma", noise="ad", gamma=0.05, chi=64, precision="fp32",

@@ -121,3 +121,36 @@ def test_exact_pl_vs_trajectories_d3_c1_srx():
     est = fails.mean()
     assert pl > 0.01
     assert abs(est - pl) < 3 * math.sqrt(pl * (1 - pl) / n) + 1e-9
+
+
+@pytest.mark.parametrize("k,theta", [(1, 0.3), (5, 0.07), (12, 0.02)])
+def test_record_log_prob_closed_form(k, theta):
+    """k SRX locations then a Z measurement: log p(1) = log sin^2(k theta), its
+    theta-derivative 2 k cot(k theta); log p(0) = log cos^2(k theta), derivative
+    -2 k tan(k theta)."""
+    circ = custom_circuit(1, [[(NOISE, 0, None)] for _ in range(k)] + [[(MEAS_Z, 0, None)]])
+    one, zero = np.array([1], np.uint8), np.array([0], np.uint8)
+    assert SV.record_log_prob(circ, SRX, theta, 0.0, one) == pytest.approx(
+        math.log(math.sin(k * theta) ** 2), abs=1e-12)
+    assert SV.record_log_prob(circ, SRX, theta, 0.0, zero) == pytest.approx(
+        math.log(math.cos(k * theta) ** 2), abs=1e-12)
+    h = 1e-5
+    fd1 = (SV.record_log_prob(circ, SRX, theta + h, 0.0, one)
+           - SV.record_log_prob(circ, SRX, theta - h, 0.0, one)) / (2 * h)
+    fd0 = (SV.record_log_prob(circ, SRX, theta + h, 0.0, zero)
+           - SV.record_log_prob(circ, SRX, theta - h, 0.0, zero)) / (2 * h)
+    assert fd1 == pytest.approx(2 * k / math.tan(k * theta), rel=1e-6)
+    assert fd0 == pytest.approx(-2 * k * math.tan(k * theta), rel=1e-6)
+    # noise off: the measurement of |0> cannot give 1
+    assert SV.record_log_prob(circ, NONE, 0.0, 0.0, one) == -math.inf
+
+
+def test_record_log_prob_equals_sampled_log_prob():
+    """Forcing a d = 3 trajectory's own record reproduces its log-probability."""
+    circ = build_circuit(3, 1)
+    for traj in range(4):
+        out = SV.run_trajectory(circ, SRX, 0.12, 0.0, 17, traj)
+        lp = SV.record_log_prob(circ, SRX, 0.12, 0.0, out["rec"])
+        assert lp == pytest.approx(out["logp"], abs=1e-10)
+    with pytest.raises(ValueError):
+        SV.record_log_prob(circ, AD, 0.0, 0.05, out["rec"])
