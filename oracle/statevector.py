@@ -24,7 +24,10 @@ Pinned (tests/test_oracle_statevector.py): unit norm; noise-off invariants;
 an idle qubit under k SRX locations has P(1) = sin^2(k theta) exactly, and
 (1 - (1 - 2 sin^2 theta)^k)/2 under SRX-PTA; |1> after one AD location has
 P(1) = 1 - gamma; trajectory averages agree with the density-matrix oracle
-within 3 sigma; p_L from trajectories agrees with the exact p_L.
+within 3 sigma; p_L from trajectories agrees with the exact p_L;
+record_log_prob gives log sin^2(k theta) / log cos^2(k theta) and their
+theta-derivatives for k SRX locations and one measurement, and reproduces a
+sampled trajectory's log p from its record.
 """
 import math
 import numpy as np
